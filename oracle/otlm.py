@@ -1,0 +1,418 @@
+"""Plain FP64 oracle of the Scaling Algorithm for OTLM (Algorithm 1) and its objective.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and bench.py's CPU legs,
+never by the product path.  Slow and direct on purpose: every step is the paper's formula with
+numpy/scipy primitives (matmul, exp/log, logsumexp, Lambert W) and no blocking or fusion.
+
+Notation (paper, Sec. 3): X [N, M] non-negative dictionary, w [M] weights, y [N] target,
+C [N, N] cost, K = exp(-C/eps) (Sec. 2.2), u1 target-side scaling (starts at 1), u2 source-side
+scaling.  The plan is Q_ij = u2_i K_ij u1_j, so Q 1 = u2 * (K u1) and Q^T 1 = u1 * (K^T u2).
+
+Readings of passages the paper leaves garbled or open (the same list stands in the design doc):
+  A1  objective: eps KL(Q||K) + lam L(Q^T 1 | y) + alpha R(w) with Q 1 = X w (the <C,Q> term
+      printed beside eps KL(Q||K) would count the cost twice; Sec. 2.3 / Eq. OTLM).
+  A2  Q_ij = u2_i K_ij u1_j (u2 scales the source rows; Sec. 2.3 updates, Algorithm 1).
+  A3  Table 2, no penalty: the sum over i is restored inside the exponent.
+  A4  Table 2, l1: the shift is alpha/(eps x_j), as derived in App. A (equal to alpha/eps when
+      columns have unit mass).
+  A5  Table 2, squared l2: w_j = W0(c_j e^{nu_j}) / c_j, c_j = alpha/(eps x_j), from App. A
+      (ln w_j + c_j w_j = nu_j); R(w) = (alpha/2)||w||^2.
+  A8  "not converged" (Algorithm 1): source-marginal violation
+      e = ||u2 * (K u1) - X w||_1 / ||X w||_1, measured with the u1 of the next iteration.
+  A11 zeros: rows with (X w)_i = 0 contribute nothing to the MM sum (0 log 0 = 0), y_j = 0
+      gives u1_j = 0 under the KL datafit.
+Poisson (Table 1, last row) and elastic net (Table 2, last row) are not implemented.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import lambertw, logsumexp, wrightomega
+
+DATAFITS = ("balanced", "kl", "tv", "l2")
+PENALTIES = ("none", "l1", "l2sq")
+
+
+# ---------------------------------------------------------------------------------------------
+# Building blocks (Sec. 2.2, Table 1, Table 2)
+# ---------------------------------------------------------------------------------------------
+
+def gibbs_kernel(C, eps):
+    """K = exp(-C / eps), the Gibbs kernel of the entropic OT problem (Sec. 2.2)."""
+    return np.exp(-np.asarray(C, dtype=np.float64) / eps)
+
+
+def generalized_kl(P, R):
+    """Generalised KL divergence, Eq. (generalized_kl): sum P log(P/R) - P + R, 0 log 0 = 0."""
+    P = np.asarray(P, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        plogp = np.where(P > 0, P * np.log(P / R), 0.0)
+    return float(np.sum(plogp - P + R))
+
+
+def lambert_w0(z):
+    """Principal branch W0 of the Lambert W function (library primitive: scipy)."""
+    return np.real(lambertw(np.asarray(z, dtype=np.float64), 0))
+
+
+def wright_omega(z):
+    """Wright omega: omega(z) = W0(e^z) for real z (library primitive: scipy)."""
+    return np.real(wrightomega(np.asarray(z, dtype=np.float64)))
+
+
+def datafit_loss(datafit, t, y):
+    """L(t | y) without the weight lam (Sec. 1 notation; Table 1 rows)."""
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if datafit == "balanced":
+        return 0.0 if np.allclose(t, y, rtol=1e-12, atol=0) else np.inf
+    if datafit == "kl":
+        return generalized_kl(t, y)
+    if datafit == "tv":
+        return float(np.sum(np.abs(t - y)))
+    if datafit == "l2":
+        return 0.5 * float(np.sum((t - y) ** 2))
+    raise ValueError(datafit)
+
+
+def penalty_value(penalty, w):
+    """R(w): none -> 0, l1 -> sum w, l2sq -> (1/2)||w||^2 (Table 2 rows; w >= 0)."""
+    w = np.asarray(w, dtype=np.float64)
+    if penalty == "none":
+        return 0.0
+    if penalty == "l1":
+        return float(np.sum(np.abs(w)))
+    if penalty == "l2sq":
+        return 0.5 * float(np.sum(w * w))
+    raise ValueError(penalty)
+
+
+def prox_datafit(datafit, s, y, eps, lam):
+    """prox^KL_{lam L}(s | y), Table 1, linear form."""
+    s = np.asarray(s, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if datafit == "balanced":
+        return y.copy()
+    if datafit == "kl":
+        return s ** (eps / (eps + lam)) * y ** (lam / (eps + lam))
+    if datafit == "tv":
+        return np.minimum(s * np.exp(lam / eps), np.maximum(s * np.exp(-lam / eps), y))
+    if datafit == "l2":
+        return (eps / lam) * lambert_w0((lam / eps) * s * np.exp((lam / eps) * y))
+    raise ValueError(datafit)
+
+
+def _Z(X, w_prev):
+    """Z_ij = X_ij w'_j / sum_k X_ik w'_k (Table 2 caption); 0 where X_ij w'_j = 0."""
+    num = X * w_prev[None, :]
+    den = num.sum(axis=1, keepdims=True)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(num > 0, num / den, 0.0)
+
+
+def mm_step(penalty, a, w_prev, X, eps, alpha):
+    """One MM step wMMstep^KL_P(a, Z | X), Table 2 with the App. A readings A3-A5.
+
+    `a` takes the place of y in Table 2 (Algorithm 1 calls it with K u1).  With
+    L_j = sum_i X_ij log(Z_ij a_i / X_ij) (terms with X_ij = 0 dropped, 0 log 0 = 0) and the
+    column mass x_j = sum_i X_ij:
+        none : w_j = exp(L_j / x_j)
+        l1   : w_j = exp(L_j / x_j - alpha / (eps x_j))
+        l2sq : w_j = W0(c_j exp(L_j / x_j)) / c_j,   c_j = alpha / (eps x_j)
+    """
+    X = np.asarray(X, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    w_prev = np.asarray(w_prev, dtype=np.float64)
+    Z = _Z(X, w_prev)
+    x = X.sum(axis=0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        terms = np.where(X > 0, X * np.log(Z * a[:, None] / X), 0.0)
+    nu = terms.sum(axis=0) / x
+    if penalty == "none":
+        return np.exp(nu)
+    if penalty == "l1":
+        return np.exp(nu - alpha / (eps * x))
+    if penalty == "l2sq":
+        c = alpha / (eps * x)
+        return lambert_w0(c * np.exp(nu)) / c
+    raise ValueError(penalty)
+
+
+def mm_step_log(penalty, log_a, w_prev, X, eps, alpha):
+    """The same MM step written with log a instead of a (for kernels that underflow).
+
+    Since Z_ij a_i / X_ij = w'_j a_i / s_i with s = X w' (wherever X_ij > 0), Table 2's
+    exponent becomes nu_j = log w'_j + (1/x_j) sum_{i: s_i > 0} X_ij (log a_i - log s_i).
+    The squared-l2 update is evaluated as omega(log c_j + nu_j) / c_j, which equals
+    W0(c_j e^{nu_j}) / c_j but never overflows.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    w_prev = np.asarray(w_prev, dtype=np.float64)
+    s = X @ w_prev
+    x = X.sum(axis=0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(s > 0, log_a - np.log(np.where(s > 0, s, 1.0)), 0.0)
+        nu = np.log(w_prev) + (X.T @ r) / x
+    if penalty == "none":
+        return np.exp(nu)
+    if penalty == "l1":
+        return np.exp(nu - alpha / (eps * x))
+    if penalty == "l2sq":
+        c = alpha / (eps * x)
+        out = wright_omega(np.log(c) + nu) / c
+        return np.where(np.isneginf(nu), 0.0, out)
+    raise ValueError(penalty)
+
+
+def majorizer_G(w, w_prev, a, X, eps, alpha, penalty):
+    """G(w, w') of Eq. (obj_nnsx_majorized), with a in place of y.
+
+    G = eps sum_ij Z_ij ( (X_ij w_j / Z_ij) log(X_ij w_j / (Z_ij a_i)) - X_ij w_j / Z_ij + a_i )
+        + alpha R(w),   summed over the pairs with Z_ij > 0.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    Z = _Z(X, np.asarray(w_prev, dtype=np.float64))
+    total = 0.0
+    for i in range(X.shape[0]):
+        for j in range(X.shape[1]):
+            if Z[i, j] <= 0:
+                continue
+            q = X[i, j] * w[j] / Z[i, j]
+            term = (q * np.log(q / a[i]) if q > 0 else 0.0) - q + a[i]
+            total += Z[i, j] * term
+    return eps * total + alpha * penalty_value(penalty, w)
+
+
+def prox_objective_V(w, a, X, eps, alpha, penalty):
+    """V(w) = alpha R(w) + eps KL(X w || a), the objective of Eq. (ProxP) (Sec. 4.1)."""
+    return alpha * penalty_value(penalty, w) + eps * generalized_kl(np.asarray(X) @ np.asarray(w), a)
+
+
+# ---------------------------------------------------------------------------------------------
+# Algorithm 1, linear and log domain
+# ---------------------------------------------------------------------------------------------
+
+def marginal_violation(s, u2, a):
+    """e = || u2 * a - s ||_1 / || s ||_1 with a = K u1 (reading A8)."""
+    return float(np.sum(np.abs(u2 * a - s)) / np.sum(s))
+
+
+def solve(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0):
+    """Algorithm 1 (Scaling Algorithm for OTLM) in the linear domain, FP64.
+
+    Per iteration, in the paper's order: a = K u1; Z from the previous w; w <- wMMstep(a, Z|X);
+    u2 = X w / a; b = K^T u2; v2 = prox_L(b | y); u1 = v2 / b.
+    Before every iteration after the first, the source-marginal violation of the current plan
+    (reading A8) is measured with the new a = K u1; when tol > 0 and it is <= tol the loop
+    stops and the state of the last completed iteration is returned (tol <= 0: run n_iter).
+
+    Returns dict(w, u1, u2, Q, iters, err, err_hist, t=Q^T 1, s=Q 1).
+    """
+    C = np.asarray(C, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    K = gibbs_kernel(C, eps)
+    u1 = np.ones(C.shape[1])
+    u2 = None
+    w = np.asarray(w0, dtype=np.float64).copy()
+    s = None
+    err = np.nan
+    hist = []
+    it = 0
+    for it in range(n_iter + 1):
+        a = K @ u1
+        if it > 0:
+            err = marginal_violation(s, u2, a)
+            hist.append(err)
+            if tol > 0 and err <= tol:
+                break
+        if it == n_iter:
+            break
+        w = mm_step(penalty, a, w, X, eps, alpha)
+        s = X @ w
+        u2 = s / a
+        b = K.T @ u2
+        v2 = prox_datafit(datafit, b, y, eps, lam)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u1 = np.where(b > 0, v2 / b, 0.0)
+    Q = u2[:, None] * K * u1[None, :]
+    return dict(w=w, u1=u1, u2=u2, Q=Q, iters=it, err=err, err_hist=np.array(hist),
+                t=Q.sum(axis=0), s=Q.sum(axis=1))
+
+
+def _log_datafit_potential(datafit, log_b, y, eps, lam):
+    """g = eps log(v2 / b) for v2 = prox_L(b | y), Table 1 rewritten with log b.
+
+    balanced: g = eps (log y - log b)
+    kl      : g = (eps lam / (eps + lam)) (log y - log b)
+    tv      : g = clip(eps (log y - log b), -lam, lam)
+    l2      : log v2 = log(eps/lam) + log omega(log(lam/eps) + log b + (lam/eps) y)
+              (W0(e^z) = omega(z)), g = eps (log v2 - log b)
+    """
+    with np.errstate(divide="ignore"):
+        log_y = np.log(y)
+    if datafit == "balanced":
+        return eps * (log_y - log_b)
+    if datafit == "kl":
+        return (eps * lam / (eps + lam)) * (log_y - log_b)
+    if datafit == "tv":
+        return np.clip(eps * (log_y - log_b), -lam, lam)
+    if datafit == "l2":
+        z = np.log(lam / eps) + log_b + (lam / eps) * y
+        log_v = np.log(eps / lam) + np.log(wright_omega(z))
+        return eps * (log_v - log_b)
+    raise ValueError(datafit)
+
+
+def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g0=None):
+    """Algorithm 1 with the scalings carried as potentials g = eps log u1, f = eps log u2.
+
+    log (K u1)_i = LSE_j((g_j - C_ij)/eps), log (K^T u2)_j = LSE_i((f_i - C_ij)/eps); the MM step
+    is `mm_step_log`; f = eps (log X w - log K u1) (-inf where X w = 0); g from
+    `_log_datafit_potential`.  Same stopping rule and outputs as `solve`, plus f, g, log_a.
+    """
+    C = np.asarray(C, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    g = np.zeros(C.shape[1]) if g0 is None else np.asarray(g0, dtype=np.float64).copy()
+    f = None
+    w = np.asarray(w0, dtype=np.float64).copy()
+    s = None
+    err = np.nan
+    hist = []
+    it = 0
+    log_a = None
+    for it in range(n_iter + 1):
+        log_a = logsumexp((g[None, :] - C) / eps, axis=1)
+        if it > 0:
+            # u2 * K u1 = s * exp(log a_new - log a_old)
+            err = float(np.sum(np.abs(s * np.expm1(log_a - log_a_old))) / np.sum(s))
+            hist.append(err)
+            if tol > 0 and err <= tol:
+                break
+        if it == n_iter:
+            break
+        w = mm_step_log(penalty, log_a, w, X, eps, alpha)
+        s = X @ w
+        with np.errstate(divide="ignore"):
+            f = eps * (np.log(s) - log_a)
+        log_a_old = log_a
+        log_b = logsumexp((f[:, None] - C) / eps, axis=0)
+        g = _log_datafit_potential(datafit, log_b, y, eps, lam)
+    # plan of the returned state: u2 from the last source step, u1 from the last target step
+    with np.errstate(invalid="ignore"):
+        logQ = (f[:, None] + g[None, :] - C) / eps
+    Q = np.exp(logQ)
+    return dict(w=w, f=f, g=g, Q=Q, iters=it, err=err, err_hist=np.array(hist),
+                t=Q.sum(axis=0), s=Q.sum(axis=1), log_a=log_a)
+
+
+# ---------------------------------------------------------------------------------------------
+# Objective (reading A1) and a Fenchel dual lower bound
+# ---------------------------------------------------------------------------------------------
+
+def primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty):
+    """eps KL(Q || K) + lam L(Q^T 1 | y) + alpha R(w) (Eq. OTLM, reading A1).
+
+    The caller guarantees Q 1 = X w (the constraint of the second form of Eq. OTLM).
+    """
+    K = gibbs_kernel(C, eps)
+    t = np.asarray(Q).sum(axis=0)
+    lt = datafit_loss(datafit, t, y)
+    return eps * generalized_kl(Q, K) + (lam * lt if datafit != "balanced" else lt) + alpha * penalty_value(penalty, w)
+
+
+def _F2_conj_neg(datafit, g, y, lam):
+    """F2*(-g) for F2 = lam L(. | y) on t >= 0 (convex conjugate, per datafit)."""
+    y = np.asarray(y, dtype=np.float64)
+    if datafit == "balanced":
+        return -float(np.dot(g, y))
+    if datafit == "kl":
+        # lam sum y (e^{-g/lam} - 1); a bin with y = 0 contributes 0 whatever g is
+        with np.errstate(over="ignore", invalid="ignore"):
+            v = np.where(y > 0, y * np.expm1(-g / lam), 0.0)
+        return lam * float(np.sum(v))
+    if datafit == "tv":
+        if np.any(g < -lam * (1 + 1e-12)):
+            return np.inf
+        return -float(np.sum(y * np.minimum(g, lam)))
+    if datafit == "l2":
+        inside = y - g / lam >= 0
+        return float(np.sum(np.where(inside, -g * y + g * g / (2 * lam), -lam * y * y / 2)))
+    raise ValueError(datafit)
+
+
+def _F1_conj_neg(penalty, f, X, alpha):
+    """F1*(-f) = (alpha R + indicator(w >= 0))^*(-X^T f), F1(s) = alpha P_R(s | X) (Eq. P).
+
+    Rows of X that are entirely zero do not enter X^T f (0 * (-inf) taken as 0).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    with np.errstate(invalid="ignore"):
+        prod = np.where(X > 0, X * f[:, None], 0.0)
+    v = -prod.sum(axis=0)  # v = -X^T f
+    # the feasibility tests allow a rounding slack of 1e-12 relative to the column mass
+    slack = 1e-12 * (np.abs(prod).sum(axis=0) + alpha)
+    if penalty == "none":
+        return 0.0 if np.all(v <= slack) else np.inf
+    if penalty == "l1":
+        return 0.0 if np.all(v <= alpha + slack) else np.inf
+    if penalty == "l2sq":
+        return float(np.sum(np.maximum(v, 0.0) ** 2) / (2 * alpha))
+    raise ValueError(penalty)
+
+
+def dual_objective(f, g, C, X, y, eps, lam, alpha, datafit, penalty):
+    """D(f, g) = -F1*(-f) - F2*(-g) - eps sum_ij K_ij (e^{(f_i + g_j)/eps} - 1).
+
+    For the l1 / unpenalised cases a constant shift f <- f + c 1 (c >= 0, the smallest that makes
+    X^T f >= -alpha, resp. >= 0) restores dual feasibility; D stays a valid lower bound.
+    """
+    C = np.asarray(C, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    # A row whose source mass underflowed to 0 carries f = -inf; if the dictionary is non-zero
+    # there, -inf would make X^T f infinite.  Any finite f is admissible in the dual, so such
+    # rows take the smallest finite f instead (rows where X is entirely zero keep -inf).
+    bad = np.isneginf(f) & (X.sum(axis=1) > 0)
+    if np.any(bad):
+        f = np.where(bad, np.min(f[np.isfinite(f)]), f)
+    if penalty in ("l1", "none"):
+        bound = alpha if penalty == "l1" else 0.0
+        with np.errstate(invalid="ignore"):
+            xtf = np.where(X > 0, X * f[:, None], 0.0).sum(axis=0)
+        x = X.sum(axis=0)
+        c = float(np.max(np.maximum(0.0, (-bound - xtf) / x)))
+        f = f + c
+    K = gibbs_kernel(C, eps)
+    with np.errstate(invalid="ignore", over="ignore"):
+        E = np.exp((f[:, None] + g[None, :]) / eps)
+    ent = eps * float(np.sum(K * E) - np.sum(K))
+    return -_F1_conj_neg(penalty, f, X, alpha) - _F2_conj_neg(datafit, g, y, lam) - ent
+
+
+def objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty):
+    """Primal value, dual value and their plan, evaluated from a solver state (w, g).
+
+    From (w, g): a = K u1 (u1 = e^{g/eps}), s = X w, f = eps log(s / a); the plan
+    Q = diag(e^{f/eps}) K diag(e^{g/eps}) has Q 1 = X w exactly, so (Q, w) is feasible and gives
+    the primal value.  The dual is evaluated at (f, g') with g' the datafit step from
+    b = K^T u2, i.e. the g the next iteration would use.
+    """
+    C = np.asarray(C, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    log_a = logsumexp((g[None, :] - C) / eps, axis=1)
+    s = X @ w
+    with np.errstate(divide="ignore"):
+        f = eps * (np.log(s) - log_a)
+    Q = np.exp((f[:, None] + g[None, :] - C) / eps)
+    P = primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty)
+    log_b = logsumexp((f[:, None] - C) / eps, axis=0)
+    g_next = _log_datafit_potential(datafit, log_b, y, eps, lam)
+    Dv = dual_objective(f, g_next, C, X, y, eps, lam, alpha, datafit, penalty)
+    return P, Dv, Q

@@ -1,0 +1,141 @@
+"""Seeded synthetic spectra: the one input source shared by the FP64 oracle and the CUDA path.
+
+This module draws problem instances and nothing else; it holds none of the solver's arithmetic.
+Shapes and value distributions stand in for the paper's workloads (App. D, scaling test:
+Gaussian basis functions on a 1-D grid, a sum of shifted peaks plus non-negative noise as the
+target).  The paper's own spectra (muonic X-ray, Sec. 6.1 / App. E; infrared filters,
+Sec. 6.2 / App. F) are not available; these draws stand in for them.
+
+Recipe (every instance):
+  * grid        x_i = i / (n - 1), i = 0..n-1, on [0, 1]
+  * cost        C_ij = (x_i - x_j)^2        (squared distance on the grid)
+  * dictionary  k Gaussian peaks, centres U[0.1, 0.9], widths exp(N(ln 0.02, 0.3)),
+                each column normalised to unit mass (sum over bins = 1)
+  * weights     w_true has `nnz` non-zeros at random atoms, values Gamma(shape 2, scale 1)
+  * target      y = sum_j w_true_j * peak_j shifted by delta ~ N(0, 0.01) (std) in position
+                and renormalised to unit mass, then y <- max(0, y * (1 + 0.01 xi)), xi ~ N(0, 1)
+
+Seeds: numpy SeedSequence(2504_04609, spawn_key=(workload_id, ...)), one child stream for the
+shared dictionary and one per target, so that a sub-batch of a workload reproduces exactly the
+same problems as the full batch.
+
+Every array is produced in float64 and then rounded to the precision the solver is given
+(`dtype`), so both sides see bit-identical input values.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+ROOT_SEED = 2504_04609
+
+
+def _rng(*key: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.SeedSequence(ROOT_SEED, spawn_key=tuple(int(v) for v in key)))
+
+
+def grid(n: int) -> np.ndarray:
+    """x_i = i/(n-1) on [0, 1]."""
+    if n < 2:
+        raise ValueError("grid needs n >= 2")
+    return np.arange(n, dtype=np.float64) / (n - 1)
+
+
+def squared_cost(x: np.ndarray) -> np.ndarray:
+    """Dense C_ij = (x_i - x_j)^2 for tests that want the cost as a matrix."""
+    return (x[:, None] - x[None, :]) ** 2
+
+
+def _unit_peaks(x: np.ndarray, mu: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    g = np.exp(-0.5 * ((x[:, None] - mu[None, :]) / sigma[None, :]) ** 2)
+    return g / g.sum(axis=0, keepdims=True)
+
+
+def peak_parameters(rng: np.random.Generator, k: int):
+    mu = rng.uniform(0.1, 0.9, size=k)
+    sigma = np.exp(rng.normal(np.log(0.02), 0.3, size=k))
+    return mu, sigma
+
+
+def dictionary(x: np.ndarray, k: int, rng: np.random.Generator):
+    """D [n, k] of unit-mass Gaussian peaks plus their (centre, width) parameters."""
+    mu, sigma = peak_parameters(rng, k)
+    return _unit_peaks(x, mu, sigma), mu, sigma
+
+
+def target(x: np.ndarray, mu: np.ndarray, sigma: np.ndarray, nnz: int, rng: np.random.Generator):
+    """One target spectrum y [n] and its generating weights w_true [k]."""
+    k = mu.shape[0]
+    nnz = min(nnz, k)
+    idx = rng.choice(k, size=nnz, replace=False)
+    w_true = np.zeros(k)
+    w_true[idx] = rng.gamma(2.0, 1.0, size=nnz)
+    shift = rng.normal(0.0, 0.01, size=nnz)
+    peaks = _unit_peaks(x, mu[idx] + shift, sigma[idx])
+    y = peaks @ w_true[idx]
+    y = np.maximum(0.0, y * (1.0 + 0.01 * rng.normal(size=x.shape[0])))
+    return y, w_true
+
+
+def batch(workload: int, B: int, n: int, k: int, nnz: int, dtype=np.float32, first: int = 0):
+    """A batch of B targets sharing one grid and one dictionary.
+
+    Returns dict(x [n], D [n,k], y [B,n], w_true [B,k]) with x, D, y rounded to `dtype`
+    (w_true stays float64; it is only a generator record).  Problem p of the batch is drawn
+    from child stream (workload, 1, first + p), so problems are reproducible one by one.
+    """
+    x = grid(n)
+    D, mu, sigma = dictionary(x, k, _rng(workload, 0))
+    Y = np.empty((B, n))
+    W = np.empty((B, k))
+    for p in range(B):
+        Y[p], W[p] = target(x, mu, sigma, nnz, _rng(workload, 1, first + p))
+    return dict(x=x.astype(dtype), D=D.astype(dtype), y=Y.astype(dtype), w_true=W)
+
+
+def ragged(workload: int, count: int, n_range=(256, 4096), k_range=(8, 128), eps_range=(2e-3, 5e-2),
+           nnz: int = 5, dtype=np.float32, first: int = 0):
+    """Uneven batch: each problem draws its own n ~ U{n_range}, k ~ U{k_range},
+    eps ~ logU[eps_range], its own grid and dictionary and one target.
+
+    Returns a list of dicts(x, D, y, eps, n, k).
+    """
+    out = []
+    for p in range(count):
+        rng = _rng(workload, 2, first + p)
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        eps = float(np.exp(rng.uniform(np.log(eps_range[0]), np.log(eps_range[1]))))
+        x = grid(n)
+        D, mu, sigma = dictionary(x, k, rng)
+        y, _ = target(x, mu, sigma, nnz, rng)
+        out.append(dict(x=x.astype(dtype), D=D.astype(dtype), y=y.astype(dtype), eps=eps, n=n, k=k))
+    return out
+
+
+def initial_weights(y: np.ndarray, D: np.ndarray) -> np.ndarray:
+    """Cold-start weights w0_j = sum(y) / (k * x_j), x_j the column mass of D.
+
+    The paper leaves the initial w to the caller (Algorithm 1 takes it as input); every w0_j
+    must be > 0 because zero weights stay zero under multiplicative updates.  Shapes:
+    y [..., n], D [n, k] -> w0 [..., k] in float64.
+    """
+    y = np.asarray(y, dtype=np.float64)
+    D = np.asarray(D, dtype=np.float64)
+    k = D.shape[1]
+    col = D.sum(axis=0)
+    return (y.sum(axis=-1)[..., None] / (k * col)) * np.ones(y.shape[:-1] + (k,))
+
+
+# Workload catalogue: the five configurations the solver is measured on, by what they are.
+WORKLOADS = {
+    "single_fp64_n200": dict(id=1, B=1, n=200, k=10, nnz=3, eps=1e-2, datafit="kl", lam=1.0,
+                             penalty="l2sq", alpha=1e-3, iters=500, dtype=np.float64),
+    "batch1024_n1024_kl_l1": dict(id=2, B=1024, n=1024, k=64, nnz=5, eps=5e-3, datafit="kl", lam=1.0,
+                                  penalty="l1", alpha=1e-2, iters=2000, tol=1e-5, dtype=np.float32),
+    "batch4096_n4096_l2_l2sq": dict(id=3, B=4096, n=4096, k=128, nnz=5, eps=1e-2, datafit="l2", lam=1.0,
+                                    penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
+    "ragged10000_tv_l1": dict(id=4, count=10000, datafit="tv", lam=1.0, penalty="l1", alpha=1e-2,
+                              iters=2000, tol=1e-5, dtype=np.float32),
+    "warmstart_n2048_kl_l2sq": dict(id=5, n=2048, k=64, nnz=5, eps=5e-3, datafit="kl", lam=1.0,
+                                    penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
+}

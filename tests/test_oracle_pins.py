@@ -1,0 +1,296 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix (CPU only).
+
+Each test checks one oracle function against something other than itself: a closed form, a
+textbook algorithm written out here, a 1-D numerical minimisation, a brute-force convex solve, or
+an invariant.  Chosen so that a dropped term, a wrong sign, a swapped index or a transposed
+operand in the oracle fails at least one of them (see also test_oracle_mutations.py).
+"""
+import numpy as np
+import pytest
+from scipy.optimize import minimize, minimize_scalar
+
+import oracle
+import spectra
+
+EPS = 2e-2
+
+
+def _tiny(n=5, k=2, seed=0, symmetric=False):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.05, 1.0, size=(n, k))
+    X /= X.sum(axis=0, keepdims=True)
+    y = rng.uniform(0.1, 0.6, size=n)
+    if symmetric:
+        x = np.linspace(0, 1, n)
+        C = (x[:, None] - x[None, :]) ** 2
+    else:
+        C = rng.uniform(0.0, 0.08, size=(n, n))
+        np.fill_diagonal(C, 0.0)
+    return X, y, C
+
+
+# --- Lambert W / Wright omega (library primitives; pinned by their defining identities) -------
+
+def test_lambert_w0_defining_identity():
+    z = np.concatenate([-np.exp(-1) + np.logspace(-12, -1, 12), np.linspace(-0.3, 0.0, 7),
+                        np.logspace(-12, 250, 60)])
+    W = oracle.lambert_w0(z)
+    assert np.all(W >= -1.0)
+    small = z < 10
+    np.testing.assert_allclose(W[small] * np.exp(W[small]), z[small], rtol=2e-14, atol=1e-300)
+    # for large z, exp(W) amplifies W's rounding by W: compare in the log form W + log W = log z
+    np.testing.assert_allclose(W[~small] + np.log(W[~small]), np.log(z[~small]), rtol=1e-15)
+
+
+def test_wright_omega_identity_and_relation_to_w0():
+    z = np.linspace(-700, 700, 1401)
+    om = oracle.wright_omega(z)
+    np.testing.assert_allclose(om + np.log(om), z, rtol=1e-14, atol=1e-12)
+    zs = np.linspace(-20, 20, 41)
+    np.testing.assert_allclose(oracle.wright_omega(zs), oracle.lambert_w0(np.exp(zs)), rtol=1e-14)
+
+
+# --- Generalised KL, Eq. (generalized_kl) ------------------------------------------------------
+
+def test_generalized_kl_closed_forms():
+    assert oracle.generalized_kl([2.0], [1.0]) == pytest.approx(2 * np.log(2) - 2 + 1, rel=1e-15)
+    assert oracle.generalized_kl([0.0], [3.0]) == pytest.approx(3.0, rel=1e-15)  # 0 log 0 = 0
+    p = np.array([0.3, 1.7, 0.0, 2.2])
+    assert oracle.generalized_kl(p, p) == pytest.approx(0.0, abs=1e-15)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        a, b = rng.uniform(0.01, 3, 6), rng.uniform(0.01, 3, 6)
+        assert oracle.generalized_kl(a, b) > 0
+
+
+# --- Table 1: datafit proximal operators -------------------------------------------------------
+
+def _prox_by_minimisation(datafit, b, y, eps, lam):
+    """argmin_v lam L(v | y) + eps KL(v || b) over v > 0, solved numerically in log v."""
+    def obj(lv):
+        v = np.exp(lv)
+        if datafit == "kl":
+            L = v * np.log(v / y) - v + y
+        elif datafit == "tv":
+            L = abs(v - y)
+        else:
+            L = 0.5 * (v - y) ** 2
+        return lam * L + eps * (v * np.log(v / b) - v + b)
+    lo, hi = np.log(min(b, y)) - 30 * eps / lam - 5, np.log(max(b, y)) + 5
+    res = minimize_scalar(obj, bounds=(lo, hi), method="bounded", options=dict(xatol=1e-13, maxiter=2000))
+    return np.exp(res.x)
+
+
+@pytest.mark.parametrize("datafit", ["kl", "tv", "l2"])
+@pytest.mark.parametrize("eps,lam", [(0.05, 1.0), (0.5, 0.3), (1.0, 2.0)])
+def test_prox_matches_1d_minimisation(datafit, eps, lam):
+    rng = np.random.default_rng(7)
+    for _ in range(12):
+        b, y = rng.uniform(0.05, 2.0), rng.uniform(0.05, 2.0)
+        got = float(oracle.prox_datafit(datafit, np.array([b]), np.array([y]), eps, lam)[0])
+        ref = _prox_by_minimisation(datafit, b, y, eps, lam)
+        assert got == pytest.approx(ref, rel=2e-6), (datafit, b, y)
+
+
+def test_prox_balanced_is_target():
+    y = np.array([0.2, 0.0, 1.5])
+    np.testing.assert_array_equal(oracle.prox_datafit("balanced", np.array([3.0, 1.0, 2.0]), y, 0.1, 1.0), y)
+
+
+@pytest.mark.parametrize("datafit", ["balanced", "kl", "tv", "l2"])
+def test_log_potential_equals_linear_prox(datafit):
+    """The log-domain potential update equals eps log(prox(b)/b); the second setting makes
+    the TV clamp bind (|eps log(y/b)| > lam for part of the bins)."""
+    from oracle.otlm import _log_datafit_potential
+    rng = np.random.default_rng(3)
+    b, y = rng.uniform(0.01, 2.0, 50), rng.uniform(0.01, 2.0, 50)
+    for eps, lam in ((0.05, 1.0), (0.8, 0.5)):
+        g = _log_datafit_potential(datafit, np.log(b), y, eps, lam)
+        ref = eps * np.log(oracle.prox_datafit(datafit, b, y, eps, lam) / b)
+        np.testing.assert_allclose(g, ref, rtol=1e-11, atol=1e-13)
+
+
+# --- Table 2 / App. A: the MM step --------------------------------------------------------------
+
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+def test_mm_step_minimises_majorizer(penalty):
+    """G(w, w') is separable in w_j: coordinate-wise 1-D minimisation must give the MM step."""
+    X, _, _ = _tiny(n=6, k=3, seed=2)
+    X[0, 1] = 0.0  # an exact zero in the dictionary (0 log 0 = 0)
+    rng = np.random.default_rng(5)
+    a = rng.uniform(0.1, 1.0, 6)
+    w_prev = rng.uniform(0.2, 2.0, 3)
+    alpha = 0.05
+    w = oracle.mm_step(penalty, a, w_prev, X, EPS, alpha)
+    for j in range(3):
+        def obj(lv, j=j):
+            ww = w.copy()
+            ww[j] = np.exp(lv)
+            return oracle.majorizer_G(ww, w_prev, a, X, EPS, alpha, penalty)
+        res = minimize_scalar(obj, bounds=(np.log(w[j]) - 3, np.log(w[j]) + 3), method="bounded",
+                              options=dict(xatol=1e-12))
+        assert np.exp(res.x) == pytest.approx(w[j], rel=1e-6)
+
+
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+def test_majorizer_majorises_and_touches(penalty):
+    X, _, _ = _tiny(n=6, k=3, seed=4)
+    rng = np.random.default_rng(6)
+    a = rng.uniform(0.1, 1.0, 6)
+    w_prev = rng.uniform(0.2, 2.0, 3)
+    V = lambda w: oracle.prox_objective_V(w, a, X, EPS, 0.05, penalty)  # noqa: E731
+    G = lambda w: oracle.majorizer_G(w, w_prev, a, X, EPS, 0.05, penalty)  # noqa: E731
+    assert G(w_prev) == pytest.approx(V(w_prev), rel=1e-13)
+    for _ in range(30):
+        w = rng.uniform(0.0, 3.0, 3)
+        assert G(w) >= V(w) - 1e-13
+
+
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+def test_repeated_mm_steps_decrease_V_to_the_proxP_minimum(penalty):
+    """MM on Eq. (ProxP) with a fixed: V non-increasing, and the limit minimises V over w >= 0."""
+    X, _, _ = _tiny(n=7, k=3, seed=8)
+    rng = np.random.default_rng(9)
+    a = rng.uniform(0.2, 1.0, 7)
+    alpha = 0.01
+    w = np.ones(3)
+    vals = [oracle.prox_objective_V(w, a, X, EPS, alpha, penalty)]
+    for _ in range(4000):
+        w = oracle.mm_step(penalty, a, w, X, EPS, alpha)
+        vals.append(oracle.prox_objective_V(w, a, X, EPS, alpha, penalty))
+    assert np.all(np.diff(vals) <= 1e-13 * np.abs(vals[:-1]) + 1e-16)
+    res = minimize(lambda lw: oracle.prox_objective_V(np.exp(lw), a, X, EPS, alpha, penalty),
+                   np.log(w) + 0.3, method="Nelder-Mead", options=dict(xatol=1e-12, fatol=1e-15, maxiter=20000))
+    assert vals[-1] <= res.fun + 1e-12
+    np.testing.assert_allclose(w, np.exp(res.x), rtol=1e-4)
+
+
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+def test_mm_step_log_equals_linear(penalty):
+    X, _, _ = _tiny(n=8, k=4, seed=10)
+    X[2, :2] = 0.0
+    rng = np.random.default_rng(11)
+    a = rng.uniform(0.1, 1.0, 8)
+    w_prev = rng.uniform(0.2, 2.0, 4)
+    np.testing.assert_allclose(oracle.mm_step_log(penalty, np.log(a), w_prev, X, EPS, 0.03),
+                               oracle.mm_step(penalty, a, w_prev, X, EPS, 0.03), rtol=1e-13)
+
+
+# --- Algorithm 1 --------------------------------------------------------------------------------
+
+def test_balanced_single_column_reduces_to_sinkhorn():
+    """Balanced datafit, one dictionary column, no penalty: classic Sinkhorn between
+    w*a and y; at the fixed point w = sum(y)/sum(a) and both marginals are met."""
+    n = 12
+    x = np.linspace(0, 1, n)
+    rng = np.random.default_rng(12)
+    col = rng.uniform(0.2, 1.0, n)
+    col /= col.sum() * 0.8  # column mass 1.25
+    y = rng.uniform(0.1, 1.0, n)
+    C = np.abs(x[:, None] - x[None, :]) * 0.7 + rng.uniform(0, 0.05, (n, n))  # not symmetric
+    eps = 0.1
+    r = oracle.solve(C, col[:, None], y, eps, 1.0, 0.0, "balanced", "none", np.array([1.0]), 3000)
+    w_expected = y.sum() / col.sum()
+    assert r["w"][0] == pytest.approx(w_expected, rel=1e-12)
+    # textbook Sinkhorn, written out independently: Q = diag(p) K diag(q)
+    K = np.exp(-C / eps)
+    mu, nu = col * w_expected, y
+    q = np.ones(n)
+    for _ in range(5000):
+        p = mu / (K @ q)
+        q = nu / (K.T @ p)
+    Q_ref = p[:, None] * K * q[None, :]
+    np.testing.assert_allclose(r["Q"], Q_ref, rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(r["t"], y, rtol=1e-12)
+    np.testing.assert_allclose(r["s"], mu, rtol=1e-9)
+
+
+def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty):
+    """Minimise eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w) s.t. Q 1 = X w, Q >= 0, w >= 0,
+    with Q_ij = (X w)_i softmax_j(theta_i), w = exp(eta); gradients by torch autograd (FP64)."""
+    import torch
+    n, k = X.shape
+    Xt, yt, Kt = (torch.tensor(v, dtype=torch.float64) for v in (X, y, np.exp(-C / eps)))
+
+    def obj(z):
+        th = z[: n * n].reshape(n, n)
+        w = torch.exp(z[n * n:])
+        Q = (Xt @ w)[:, None] * torch.softmax(th, dim=1)
+        kl = torch.sum(Q * torch.log(Q / Kt) - Q + Kt)
+        t = Q.sum(0)
+        if datafit == "kl":
+            L = torch.sum(t * torch.log(t / yt) - t + yt)
+        else:
+            L = 0.5 * torch.sum((t - yt) ** 2)
+        R = torch.sum(w) if penalty == "l1" else 0.5 * torch.sum(w * w)
+        return eps * kl + lam * L + alpha * R
+
+    def fg(zn):
+        z = torch.tensor(zn, dtype=torch.float64, requires_grad=True)
+        v = obj(z)
+        v.backward()
+        return v.item(), z.grad.numpy().copy()
+
+    z0 = np.concatenate([-C.ravel() / eps, np.zeros(k)])
+    res = minimize(fg, z0, jac=True, method="L-BFGS-B", options=dict(maxiter=50000, ftol=1e-16, gtol=1e-13))
+    return np.exp(res.x[n * n:]), res.fun
+
+
+@pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("l2", "l1"), ("kl", "l1"), ("l2", "l2sq")])
+def test_brute_force_tiny_instance(datafit, penalty):
+    """Same convex problem solved by a generic optimiser; C is not symmetric, so a transposed
+    K or a swapped marginal in Algorithm 1 lands on a different w."""
+    X, y, C = _tiny(n=5, k=2, seed=13)
+    eps, lam, alpha = 0.05, 1.0, 0.02
+    r = oracle.solve(C, X, y, eps, lam, alpha, datafit, penalty, np.ones(2), 20000, tol=1e-15)
+    w_bf, P_bf = _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty)
+    P = oracle.primal_objective(r["Q"], r["w"], C, y, eps, lam, alpha, datafit, penalty)
+    assert P == pytest.approx(P_bf, rel=1e-9, abs=1e-12)
+    np.testing.assert_allclose(r["w"], w_bf, rtol=2e-5)
+
+
+@pytest.mark.parametrize("datafit", oracle.DATAFITS)
+@pytest.mark.parametrize("penalty", oracle.PENALTIES)
+def test_linear_and_log_domain_agree(datafit, penalty):
+    d = spectra.batch(99, 1, 48, 5, 3, dtype=np.float64)
+    C = spectra.squared_cost(d["x"])
+    y = d["y"][0]
+    w0 = spectra.initial_weights(y, d["D"])
+    a = oracle.solve(C, d["D"], y, 0.03, 1.0, 0.01, datafit, penalty, w0, 60)
+    b = oracle.solve_log(C, d["D"], y, 0.03, 1.0, 0.01, datafit, penalty, w0, 60)
+    np.testing.assert_allclose(b["w"], a["w"], rtol=1e-11, atol=1e-300)
+    np.testing.assert_allclose(b["t"], a["t"], rtol=1e-10, atol=1e-300)
+    assert b["iters"] == a["iters"] == 60
+
+
+@pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("kl", "l1"), ("tv", "l1"), ("l2", "l2sq"), ("l2", "none")])
+def test_invariants_along_the_trajectory(datafit, penalty):
+    """w >= 0, Q >= 0, Q 1 = X w after the source step; primal objective non-increasing (observed,
+    not proved in the paper: slack 1e-12 relative); weak duality P >= D at every iterate;
+    gap -> 0 at convergence."""
+    d = spectra.batch(98, 1, 40, 5, 3, dtype=np.float64)
+    C = spectra.squared_cost(d["x"])
+    y, X = d["y"][0], d["D"]
+    eps, lam, alpha = 0.03, 1.0, 0.01
+    w, g = spectra.initial_weights(y, X), np.zeros(40)
+    prev = np.inf
+    for _ in range(150):
+        r = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 1, g0=g)
+        w, g = r["w"], r["g"]
+        assert np.all(w >= 0) and np.all(r["Q"] >= 0)
+        P, Dv, Q = oracle.objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty)
+        np.testing.assert_allclose(Q.sum(axis=1), X @ w, rtol=1e-12)
+        assert P <= prev + 1e-12 * abs(prev) if np.isfinite(prev) else True
+        assert P - Dv >= -1e-12 * abs(P)
+        prev = P
+    r = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 20000, tol=1e-15, g0=g)
+    P, Dv, _ = oracle.objective_and_dual(r["w"], r["g"], C, X, y, eps, lam, alpha, datafit, penalty)
+    assert P - Dv <= 1e-9 * abs(P)
+
+
+def test_balanced_target_marginal_met():
+    d = spectra.batch(97, 1, 30, 4, 2, dtype=np.float64)
+    C = spectra.squared_cost(d["x"])
+    y = d["y"][0]
+    r = oracle.solve(C, d["D"], y, 0.05, 1.0, 0.0, "balanced", "none", spectra.initial_weights(y, d["D"]), 10)
+    np.testing.assert_allclose(r["t"], y, rtol=1e-12)
