@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: OTLM problems solved per second to a 1e-5 marginal tolerance at n = 4096 on GB300.
+
+One step = one solve of a whole batch (every problem run from the cold start until its
+source-marginal violation e <= tol, Algorithm 1 with one MM step per iteration) through the C ABI.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line (rank 0).  `value` = problems solved per second over all ranks (replicas:
+every rank solves its own batch, no collective on the data path).  `e2e` = the same metric through
+otlm_solve_host with pinned host buffers (host<->device copies inside the timed region).
+`roofline` = the dominant kernel (the kernel apply) against the exponent-unit peak; its launch
+durations are measured live with CUDA events on the solver's stream.  `cpu_baseline` = the FP64
+oracle (numpy, one thread) on a bounded sample of the same workload.
+`--impl reference` times that oracle alone (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import spectra  # noqa: E402
+
+METRIC = "OTLM problems solved/s to 1e-5 marginal tol (n=4096) vs plain FP32 on 1 GB300; % roofline"
+SMS = 152
+MAX_SM_MHZ = 2070.0
+# exponent-unit results per SM per clock (MUFU.EX2); see DESIGN.md "Rooflines"
+EX2_PER_SM_CLK = 32
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle sample (also the reference arm); runs in a child process pinned to one thread
+# ------------------------------------------------------------------------------------------------
+
+_ORACLE_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle, spectra
+c = spectra.WORKLOADS[{wl!r}]
+d = spectra.batch(c["id"], {count}, c["n"], c["k"], c["nnz"], first={first})
+C = spectra.squared_cost(d["x"].astype(np.float64))
+D = d["D"].astype(np.float64)
+out = []
+for p in range({count}):
+    y = d["y"][p].astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.solve_log(C, D, y, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"],
+                         spectra.initial_weights(y, D), c["iters"], tol=c["tol"])
+    out.append((time.perf_counter() - t0, int(r["iters"])))
+print(json.dumps(out))
+"""
+
+
+def oracle_sample(workload: str, count: int, first: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    src = _ORACLE_CHILD.format(root=ROOT, wl=workload, count=count, first=first)
+    r = subprocess.run([sys.executable, "-c", src], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2504_04609_gb300 import otlm as api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = spectra.WORKLOADS[args.workload]
+    B, n, k = c["B"], c["n"], c["k"]
+    d = spectra.batch(c["id"], B, n, k, c["nnz"], first=rank * B)
+    x = torch.tensor(d["x"], device=dev)
+    D = torch.tensor(d["D"], device=dev)
+    y = torch.tensor(d["y"], device=dev)
+    w0_np = spectra.initial_weights(d["y"], d["D"]).astype(np.float32)
+    w0 = torch.tensor(w0_np, device=dev)
+    w = torch.empty_like(w0)
+    t = torch.empty_like(y)
+    iters = torch.empty(B, dtype=torch.int32, device=dev)
+    err = torch.empty(B, dtype=torch.float32, device=dev)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = api.Handle(n, k, B, "fp32", c["datafit"], c["penalty"], c["iters"], c["tol"], poll_every=4,
+                   stream=stream.cuda_stream)
+
+    def step():
+        w.copy_(w0)
+        h.solve(x, D, y, c["eps"], c["lam"], c["alpha"], w, None, t, iters, err, status)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs
+    h.set_timing(True)
+    h.get_timing()
+    l0 = h.launches
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = h.launches - l0
+    timing = h.get_timing()
+    h.set_timing(False)
+    it_np = iters.cpu().numpy()
+    st_np = status.cpu().numpy()
+    clocks = clk.summary()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    hx, hD, hy, hw0 = pin(d["x"]), pin(d["D"]), pin(d["y"]), pin(w0_np)
+    hw = torch.empty_like(hw0).pin_memory()
+    ht = torch.empty_like(hy).pin_memory()
+    hit = torch.empty(B, dtype=torch.int32).pin_memory()
+    herr = torch.empty(B, dtype=torch.float32).pin_memory()
+    hst = torch.empty(B, dtype=torch.int32).pin_memory()
+
+    def step_host():
+        hw.copy_(hw0)
+        h.solve_host(hx, hD, hy, c["eps"], c["lam"], c["alpha"], hw, None, ht, hit, herr, hst)
+
+    step_host()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    h2d = hx.numel() * 4 + hD.numel() * 4 + hy.numel() * 4 + hw.numel() * 4
+    d2h = hw.numel() * 4 + ht.numel() * 4 + B * 4 * 3
+
+    # max over ranks
+    vals = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms, e2e_s = float(vals[0]), float(vals[1])
+    h.close()
+    if rank != 0:
+        return None
+
+    value = B * world * args.steps / (ms / 1e3)
+    mean_iters = float(it_np.mean())
+    # algorithmic work of the kernel apply: n^2 exponentials per problem per launch; a problem that
+    # stops after T iterations sees T + 1 source applies (the last one measures e) and T target applies
+    exps_per_step = float(n) * n * float(np.sum(2 * it_np.astype(np.float64) + 1))
+    apply_ms, apply_launches = timing["apply"]
+    apply_ms_step = apply_ms / args.steps
+    achieved = exps_per_step / (apply_ms_step / 1e3) / 1e9  # Gexp2/s
+    peak = SMS * EX2_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "apply_kernel_traffic.json")))
+        if prof.get("workload") == args.workload and prof.get("kernel_rev") == KERNEL_REV:
+            traffic = prof["bytes_per_launch"]
+    except Exception:
+        pass
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "problems/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
+        "config": {"workload": args.workload, "B_per_gpu": B, "n": n, "k": k, "eps": c["eps"],
+                   "datafit": c["datafit"], "lam": c["lam"], "penalty": c["penalty"], "alpha": c["alpha"],
+                   "tol": c["tol"], "path": "fp32 log-domain (plain FP32)", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (potentials 5 x 64 MiB per step)",
+                   "mean_iters": mean_iters, "max_iters": int(it_np.max()),
+                   "converged": int(np.sum(st_np == 0))},
+        "iters_per_s": float(it_np.sum()) * world * args.steps / (ms / 1e3),
+        "roofline": {"bound": "alu", "kernel": "apply_kernel (log-sum-exp kernel apply)", "achieved": achieved,
+                     "peak": peak, "unit": "Gexp2/s", "frac": achieved / peak, "traffic": traffic,
+                     "launch_ms_avg": apply_ms / max(apply_launches, 1),
+                     "peak_basis": f"{SMS} SMs x {EX2_PER_SM_CLK} ex2/clk x {MAX_SM_MHZ:.0f} MHz (derived)",
+                     "frac_at_sampled_clock": (achieved / (SMS * EX2_PER_SM_CLK * clocks["sm_mhz"] * 1e-3))
+                     if clocks.get("sm_mhz") else None},
+        "kernel_ms_per_step": {kind: v[0] / args.steps for kind, v in timing.items()},
+        "e2e": {"value": B * world * e2e_steps / e2e_s, "unit": "problems/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        samp = oracle_sample(args.workload, 1, 0)
+        secs = sum(s for s, _ in samp)
+        out["cpu_baseline"] = {"value": len(samp) / secs, "unit": "problems/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{len(samp)} problem(s) of {args.workload} (n={n}) solved to tol by the "
+                                         f"FP64 numpy oracle, {samp[0][1]} iterations, {secs:.1f} s"}
+    return out
+
+
+KERNEL_REV = "apply-v1"
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    c = spectra.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are skipped to bound the run time
+    samp = []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        samp += oracle_sample(args.workload, 1, s)
+    secs = time.perf_counter() - t0
+    v = len(samp) / secs
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "problems/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
+            "config": {"workload": args.workload, "n": c["n"], "k": c["k"], "eps": c["eps"], "tol": c["tol"],
+                       "sample_per_step": "1 problem", "iters": [i for _, i in samp]},
+            "cpu_baseline": {"value": v, "unit": "problems/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(samp)} problems of {args.workload}, one per step, FP64 numpy oracle"},
+            "e2e": {"value": v, "unit": "problems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch4096_n4096_l2_l2sq")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

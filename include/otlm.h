@@ -1,0 +1,169 @@
+/*
+ * otlm.h -- C ABI of the GB300 solver for Optimal Transport Linear Models (OTLM).
+ *
+ * The solver runs the Scaling Algorithm for OTLM (Algorithm 1 of Kacprzak et al.,
+ * "Scalable Approximate Algorithms for Optimal Transport Linear Models", arXiv 2504.04609):
+ * per iteration a Gibbs-kernel apply a = K u1, one majorisation-minimisation (MM) step on the
+ * dictionary weights w (Table 2), the source scaling u2 = X w / a, a second apply b = K^T u2,
+ * and the datafit proximal step u1 = prox_L(b | y) / b (Table 1).  K = exp(-C/eps) with the
+ * squared-distance cost C_ij = (x_i - x_j)^2 on a 1-D grid x (Sec. 2.2, Gibbs kernel).
+ *
+ * Conventions shared by every entry point
+ *  - Every array argument is a DEVICE pointer owned by the caller, except where a function
+ *    says "host".  The library never frees caller memory.  A handle owns only its workspace.
+ *  - Element type: `double` when the handle was created with OTLM_PREC_FP64, otherwise `float`.
+ *    Integer outputs are int32.
+ *  - Layouts are row-major and dense: x [n]; D [n][k] (the paper's X, one column per atom,
+ *    shared by every problem of the batch); y, g, t [batch][n]; w [batch][k].
+ *  - Calls are asynchronous on the stream given at create time (NULL = the legacy default
+ *    stream); results are valid once that stream has been synchronised.  The host blocks only
+ *    for the short convergence polls that `otlm_solve` makes every few iterations.
+ *  - Return value: OTLM_OK (0) or a negative OTLM_E* code; otlm_strerror() names it.  No C++
+ *    exception crosses the ABI.  Arguments are validated before any work is queued.
+ *  - Potentials: g = eps log u1 (target side), f = eps log u2 (source side).
+ *  - Readings of passages the paper leaves open (used throughout):
+ *      Q_ij = u2_i K_ij u1_j; the objective is eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w)
+ *      (Eq. OTLM without the duplicated <C,Q> term); Table 2's l1 shift is alpha/(eps x_j) and
+ *      its squared-l2 update is w_j = W0(c_j e^{nu_j})/c_j, c_j = alpha/(eps x_j) (App. A);
+ *      "not converged" (Algorithm 1) means e = ||u2*(K u1) - X w||_1 / ||X w||_1 > tol,
+ *      measured with the u1 of the following iteration.
+ */
+#ifndef OTLM_H
+#define OTLM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define OTLM_OK            0
+#define OTLM_EINVAL       -1  /* an argument is out of range or inconsistent with the handle */
+#define OTLM_ECUDA        -2  /* a CUDA runtime call failed (the CUDA error is not cleared)  */
+#define OTLM_ENOMEM       -3  /* workspace allocation failed                                  */
+#define OTLM_EUNSUPPORTED -4  /* valid request this build does not implement                  */
+
+/* per-problem status written to status_out[] */
+#define OTLM_CONVERGED     0  /* e <= tol                                                     */
+#define OTLM_MAX_ITER      1  /* stopped at max_iter                                          */
+#define OTLM_NONFINITE     2  /* a NaN/Inf appeared in the violation e; state left as is      */
+
+/* ---- problem options ----------------------------------------------------------------------- */
+typedef enum {            /* marginal datafit L(. | y), Table 1 */
+  OTLM_DATAFIT_BALANCED = 0,  /* indicator {Q^T 1 = y}: prox = y                               */
+  OTLM_DATAFIT_KL       = 1,  /* lam KL(s|y): prox = s^{eps/(eps+lam)} y^{lam/(eps+lam)}        */
+  OTLM_DATAFIT_TV       = 2,  /* lam ||s-y||_1: prox = min(s e^{lam/eps}, max(s e^{-lam/eps},y)) */
+  OTLM_DATAFIT_L2       = 3   /* (lam/2)||s-y||^2: prox = (eps/lam) W0((lam/eps) s e^{lam y/eps}) */
+} otlm_datafit;
+
+typedef enum {            /* weight penalty R(w), Table 2 */
+  OTLM_PENALTY_NONE = 0,
+  OTLM_PENALTY_L1   = 1,      /* alpha sum w                                                 */
+  OTLM_PENALTY_L2SQ = 2       /* (alpha/2) ||w||^2                                           */
+} otlm_penalty;
+
+typedef enum {
+  OTLM_PREC_FP32_LOG = 0,     /* FP32, scalings carried as log2 potentials (stable at small eps) */
+  OTLM_PREC_FP64     = 1      /* FP64 throughout, same log-domain arithmetic                   */
+} otlm_precision;
+
+typedef struct otlm_config {
+  int    n_max;        /* largest grid size a solve on this handle may use (>= 2)             */
+  int    k_max;        /* largest dictionary size (1..256)                                    */
+  int    batch_max;    /* largest number of problems per solve (>= 1)                         */
+  int    precision;    /* otlm_precision                                                      */
+  int    datafit;      /* otlm_datafit                                                        */
+  int    penalty;      /* otlm_penalty                                                        */
+  int    max_iter;     /* iteration cap (>= 1)                                                */
+  double tol;          /* stop a problem once e <= tol; tol <= 0 runs exactly max_iter        */
+  int    poll_every;   /* host polls the number of unfinished problems every this many
+                          iterations (>= 1); larger = fewer host syncs, more idle launches   */
+} otlm_config;
+
+typedef struct otlm_ctx* otlm_handle;
+
+/* Create a handle and its device workspace (about (8 n_max + 2 k_max + 16) * batch_max
+ * elements).  `cuda_stream` is a cudaStream_t (NULL = default stream).  The workspace is
+ * owned by the handle and released by otlm_destroy.
+ * Errors: OTLM_EINVAL (null pointers, sizes out of range, unknown enum), OTLM_ENOMEM,
+ * OTLM_ECUDA.  On error *h is set to NULL. */
+int otlm_create(otlm_handle* h, const otlm_config* cfg, void* cuda_stream);
+
+/* Release the workspace.  Waits for the handle's stream.  NULL is ignored. */
+void otlm_destroy(otlm_handle h);
+
+/* Solve `batch` independent OTLM problems sharing one grid and one dictionary
+ * (Algorithm 1, one MM step per iteration as in Sec. 4.2).
+ *   x      [n]          grid; cost C_ij = (x_i - x_j)^2
+ *   D      [n][k]       dictionary X of the paper; entries >= 0, every column sum > 0
+ *   y      [batch][n]   targets, >= 0
+ *   eps, lam, alpha     entropic weight (> 0), datafit weight (> 0; ignored for BALANCED),
+ *                       penalty weight (>= 0; > 0 for L2SQ)
+ *   w      [batch][k]   in: initial weights (every entry > 0: zero weights stay zero);
+ *                       out: weights after the last completed iteration
+ *   g      [batch][n]   in: initial target potential g = eps log u1 (warm start), or NULL for
+ *                       u1 = 1; out (when not NULL): final g
+ *   t_out  [batch][n]   transported target marginal Q^T 1 of the returned state, or NULL
+ *   iters_out  [batch]  completed iterations (device int32, may be NULL)
+ *   err_out    [batch]  last measured violation e (device; float for an FP32 handle, double
+ *                       for FP64; may be NULL)
+ *   status_out [batch]  OTLM_CONVERGED / OTLM_MAX_ITER / OTLM_NONFINITE (device int32, may be NULL)
+ * Problems stop independently; finished problems drop out of the remaining launches.
+ * Errors: OTLM_EINVAL (batch/n/k beyond the handle, n < 2, k < 1, eps <= 0, lam <= 0 for a
+ * soft datafit, alpha < 0, alpha == 0 with L2SQ, a NULL required pointer), OTLM_ECUDA. */
+int otlm_solve(otlm_handle h, int batch, int n, int k,
+               const void* x, const void* D, const void* y,
+               double eps, double lam, double alpha,
+               void* w, void* g, void* t_out,
+               int* iters_out, void* err_out, int* status_out);
+
+/* Same as otlm_solve, with x, D, y, w (in/out), g (in/out, may be NULL) and t_out (may be
+ * NULL) in HOST memory (pageable or pinned), and iters_out / status_out / err_out as host
+ * arrays (may be NULL).  The host<->device copies run on the handle's stream through the
+ * handle's workspace; the call returns after the results are in host memory. */
+int otlm_solve_host(otlm_handle h, int batch, int n, int k,
+                    const void* x, const void* D, const void* y,
+                    double eps, double lam, double alpha,
+                    void* w, void* g, void* t_out,
+                    int* iters_out, void* err_out, int* status_out);
+
+/* Objective of a solver state (w, g), in FP64 (Eq. OTLM with the reading above).
+ * From (w, g): a = K u1, s = D w, f = eps log(s/a); the plan Q = diag(e^{f/eps}) K diag(e^{g/eps})
+ * satisfies Q 1 = D w, so primal_out = eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w) is the value
+ * of a feasible point.  dual_out is the Fenchel dual
+ *   -F1*(-f') - F2*(-g') - eps sum_ij K_ij (e^{(f'_i+g'_j)/eps} - 1)
+ * at g' = the datafit step from K^T e^{f/eps} and f' = f shifted by the smallest constant that
+ * makes it dual-feasible (l1 / no penalty), so dual_out <= optimum <= primal_out and
+ * primal_out - dual_out is a duality gap.  BALANCED datafit: primal_out is +inf unless Q^T 1 = y.
+ * The two kernel applies run in the handle's arithmetic; all sums are FP64.
+ *   w [batch][k], g [batch][n] as returned by otlm_solve; primal_out, dual_out [batch] device
+ *   doubles.  Errors as otlm_solve. */
+int otlm_objective(otlm_handle h, int batch, int n, int k,
+                   const void* x, const void* D, const void* y,
+                   double eps, double lam, double alpha,
+                   const void* w, const void* g,
+                   double* primal_out, double* dual_out);
+
+/* Number of kernel launches the handle has queued since creation (instrumentation; the paper
+ * has no counterpart).  NULL handle: -1. */
+long long otlm_launch_count(otlm_handle h);
+
+/* Device-time instrumentation (the paper has no counterpart).  When enabled, every launch a
+ * solve or objective call queues is bracketed by two CUDA events on the handle's stream, and
+ * the elapsed device time is accumulated per kernel kind: [0] kernel apply (a = K u1 and
+ * b = K^T u2), [1] MM weight update + source step, [2] batch compaction, [3] set-up / finalize
+ * / objective reductions.  otlm_get_timing writes the sums (milliseconds) and launch counts
+ * into ms[4] and launches[4] (host arrays) and resets them; it waits for pending events.
+ * Errors: OTLM_EINVAL (NULL arguments), OTLM_ECUDA (event creation or query failed). */
+int otlm_set_timing(otlm_handle h, int enable);
+int otlm_get_timing(otlm_handle h, double* ms, long long* launches);
+
+/* Static description of a status code; never NULL. */
+const char* otlm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTLM_H */

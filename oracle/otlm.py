@@ -327,7 +327,9 @@ def _F2_conj_neg(datafit, g, y, lam):
     """F2*(-g) for F2 = lam L(. | y) on t >= 0 (convex conjugate, per datafit)."""
     y = np.asarray(y, dtype=np.float64)
     if datafit == "balanced":
-        return -float(np.dot(g, y))
+        # <-g, y> over the bins with y > 0; a bin with y = 0 contributes 0 whatever g is
+        with np.errstate(invalid="ignore"):
+            return -float(np.sum(np.where(y > 0, g * y, 0.0)))
     if datafit == "kl":
         # lam sum y (e^{-g/lam} - 1); a bin with y = 0 contributes 0 whatever g is
         with np.errstate(over="ignore", invalid="ignore"):

@@ -1,0 +1,480 @@
+// Kernels of the batched OTLM scaling iteration (Algorithm 1) on a shared 1-D grid and a shared
+// dictionary, carried in the log domain:
+//   G2 = g / (eps ln2)   target potential,  F2 = f / (eps ln2)   source potential,
+//   LA2 = log2 (K u1),  LB2 = log2 (K^T u2),  S = X w  (the paper's X is the dictionary D).
+// With the scaled grid xt = x / sqrt(eps ln2), C_ij / (eps ln2) = (xt_i - xt_j)^2, so
+//   LA2_i = log2 sum_j 2^(G2_j - (xt_i - xt_j)^2),   LB2_j = log2 sum_i 2^(F2_i - (xt_i - xt_j)^2).
+#pragma once
+
+#include "common.cuh"
+
+namespace otlm {
+
+enum { EPI_SOURCE = 0, EPI_TARGET = 1 };
+enum { DF_BALANCED = 0, DF_KL = 1, DF_TV = 2, DF_L2 = 3 };
+enum { PEN_NONE = 0, PEN_L1 = 1, PEN_L2SQ = 2 };
+enum { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_NONFINITE = 2 };
+
+template <typename T>
+struct ApplyArgs {
+  const T* in;          // [P][n] potentials in log2 units (G2 for the source apply, F2 for the target apply)
+  T* out;               // [P][n] log2 sums; on entry the previous sums (the fast path's shift)
+  const T* xt;          // [n] scaled grid
+  const int* active;    // active problem ids, compacted
+  const int* n_active;  // number of active problems
+  int n;
+  // source-apply epilogue: violation e = sum_i S_i |2^(LA2new_i - LA2old_i) - 1| (numerator)
+  const T* S;           // [P][n] X w of the previous source step
+  T* err_acc;           // [P] numerators, accumulated atomically
+  int check;
+  // target-apply epilogue: datafit prox (Table 1) in log2 units
+  const T* y;           // [P][n]
+  T* G2;                // [P][n]
+  int datafit;
+  T kl_coef;            // lam / (eps + lam)
+  T tv_bound;           // lam / (eps ln2)
+  T lam_over_eps;       // lam / eps
+  T log_lam_over_eps;   // ln(lam / eps)
+};
+
+// Tile of the kernel apply: TB = RB*WB problems x TI = 32*RI*WI rows; warp (wb, wi) owns RB
+// problems and 32*RI rows, lane l the rows wi*32*RI + r*32 + l.  The input potentials of the
+// CTA's problems are staged through shared memory in chunks of TJ columns, stored [j][b] so that
+// every lane reads its RB problems of one column as one broadcast vector load.
+template <typename T, int RB_, int RI_, int WB_, int WI_, int TJ_>
+struct ApplyTile {
+  static constexpr int RB = RB_, RI = RI_, WB = WB_, WI = WI_, TJ = TJ_;
+  static constexpr int TB = RB * WB, TI = 32 * RI * WI, NT = 32 * WB * WI;
+};
+
+template <typename T, int N> struct VecLoad;  // N consecutive T from shared memory
+template <> struct VecLoad<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float* v) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+};
+template <> struct VecLoad<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double* v) {
+    double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+};
+
+// One sweep over all columns j. PASS 0: m = max_j(in_bj - c_ij); PASS 1: acc = sum_j 2^(in_bj - c_ij - m).
+template <typename T, class Cfg, int PASS>
+__device__ __forceinline__ void apply_sweep(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
+                                            const T (&xi)[Cfg::RI], int wb, T (&m)[Cfg::RB][Cfg::RI],
+                                            T (&acc)[Cfg::RB][Cfg::RI]) {
+  using P = Prec<T>;
+  constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ, NT = Cfg::NT;
+  const int n = A.n;
+  for (int j0 = 0; j0 < n; j0 += TJ) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < TB * TJ; e += NT) {
+      const int bb = e / TJ, jj = e - bb * TJ, j = j0 + jj, p = prob_s[bb];
+      in_s[jj * TB + bb] = (p >= 0 && j < n) ? A.in[(size_t)p * n + j] : P::ninf();
+    }
+    for (int jj = threadIdx.x; jj < TJ; jj += NT) xj_s[jj] = (j0 + jj < n) ? A.xt[j0 + jj] : T(0);
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < TJ; ++jj) {
+      const T xj = xj_s[jj];
+      T v[RB];
+      VecLoad<T, RB>::ld(in_s + jj * TB + wb * RB, v);
+      T c[RI];
+#pragma unroll
+      for (int r = 0; r < RI; ++r) {
+        const T d = xi[r] - xj;
+        c[r] = d * d;
+      }
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+          if (PASS == 0) m[q][r] = fmax(m[q][r], v[q] - c[r]);
+          else acc[q][r] += P::exp2((v[q] - m[q][r]) - c[r]);
+        }
+    }
+  }
+}
+
+// Kernel apply with fused epilogue.  SAFE: exact max pass then sum pass.  Fast path (SAFE =
+// false): the previous sums in `out` serve as the shift; if any sum of the tile leaves
+// [2^-60, 2^60] or a shift is not finite, the CTA redoes the tile on the safe path.
+template <typename T, class Cfg, int EPI, bool SAFE>
+__global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
+  using P = Prec<T>;
+  constexpr int RB = Cfg::RB, RI = Cfg::RI, WB = Cfg::WB, TB = Cfg::TB, TI = Cfg::TI, TJ = Cfg::TJ;
+  __shared__ __align__(16) T in_s[TJ * TB];
+  __shared__ T xj_s[TJ];
+  __shared__ int prob_s[TB];
+  const int na = *A.n_active;
+  const int b0 = blockIdx.y * TB;
+  if (b0 >= na) return;
+  const int n = A.n;
+  const int i0 = blockIdx.x * TI;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wb = warp % WB, wi = warp / WB;
+  if (threadIdx.x < TB) prob_s[threadIdx.x] = (b0 + threadIdx.x < na) ? A.active[b0 + threadIdx.x] : -1;
+  __syncthreads();
+  int pr[RB];
+#pragma unroll
+  for (int q = 0; q < RB; ++q) pr[q] = prob_s[wb * RB + q];
+  int row[RI];
+  T xi[RI];
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    row[r] = i0 + wi * 32 * RI + r * 32 + lane;
+    xi[r] = row[r] < n ? A.xt[row[r]] : T(0);
+  }
+  T m[RB][RI], acc[RB][RI];
+  bool safe = SAFE;
+  if (!SAFE) {
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+#pragma unroll
+      for (int r = 0; r < RI; ++r) {
+        const bool ok = pr[q] >= 0 && row[r] < n;
+        m[q][r] = ok ? A.out[(size_t)pr[q] * n + row[r]] : T(0);
+        acc[q][r] = T(0);
+        bad |= ok && !isfinite(m[q][r]);
+      }
+    safe = __syncthreads_or(bad);
+    if (!safe) {
+      apply_sweep<T, Cfg, 1>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+      bad = false;
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+          const bool ok = pr[q] >= 0 && row[r] < n;
+          bad |= ok && !(acc[q][r] >= T(8.673617379884035e-19) && acc[q][r] <= T(1.152921504606847e18));
+        }
+      safe = __syncthreads_or(bad);
+    }
+  }
+  if (safe) {
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+#pragma unroll
+      for (int r = 0; r < RI; ++r) { m[q][r] = P::ninf(); acc[q][r] = T(0); }
+    apply_sweep<T, Cfg, 0>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+        if (!(m[q][r] > P::ninf())) m[q][r] = T(0);  // every term vanishes: the sum stays 0
+    apply_sweep<T, Cfg, 1>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+  }
+
+  // ---- epilogue -----------------------------------------------------------------------------
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    const int p = pr[q];
+    T part = T(0);
+    if (p >= 0) {
+#pragma unroll
+      for (int r = 0; r < RI; ++r) {
+        if (row[r] >= n) continue;
+        const size_t idx = (size_t)p * n + row[r];
+        const T v = acc[q][r] > T(0) ? m[q][r] + P::log2(acc[q][r]) : P::ninf();
+        if (EPI == EPI_SOURCE) {
+          if (A.check) {
+            // s |a_new / a_old - 1| = s |2^dl - 1|: expm1 keeps the small ratios (the ones that
+            // decide convergence) accurate; a jump beyond 2^64 is taken in log form, capped at
+            // 2^120, so that an early, far-off row cannot overflow to inf.
+            // On the fast path the shift m is the previous LA2 itself, so the ratio a_new/a_old is
+            // the tile sum acc, known to FP32 relative precision; subtracting two logs of size
+            // |LA2| would quantise it to |LA2| ulp.
+            const T s = A.S[idx];
+            if (s > T(0)) {
+              if (!safe) {
+                part += s * fabs(acc[q][r] - T(1));
+              } else {
+                const T dl = v - A.out[idx];
+                part += dl > T(64) ? P::exp2(fmin(P::log2(s) + dl, T(120))) : s * fabs(P::expm1(dl * T(kLn2)));
+              }
+            }
+          }
+          A.out[idx] = v;
+        } else {
+          A.out[idx] = v;
+          const T yv = A.y[idx];
+          T gn;
+          switch (A.datafit) {
+            case DF_BALANCED: gn = P::log2(yv) - v; break;
+            case DF_KL: gn = A.kl_coef * (P::log2(yv) - v); break;
+            case DF_TV: gn = fmin(fmax(P::log2(yv) - v, -A.tv_bound), A.tv_bound); break;
+            default: {  // L2: g = lam y - eps omega(ln(lam/eps) + ln b + (lam/eps) y)
+              const T z = A.log_lam_over_eps + v * T(kLn2) + A.lam_over_eps * yv;
+              gn = (A.lam_over_eps * yv - wright_omega<T>(z)) * T(kLog2e);
+            }
+          }
+          A.G2[idx] = gn;
+        }
+      }
+    }
+    if (EPI == EPI_SOURCE) {
+      // every lane of the warp holds the same problem p (or -1)
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (A.check && p >= 0 && lane == 0) atomicAdd(A.err_acc + p, part);
+    }
+  }
+}
+
+template <typename T>
+struct MMArgs {
+  const int* active;
+  const int* n_active;
+  int n, k;
+  const T* D;       // [n][k]
+  const T* Dt;      // [k][n]
+  const T* xcol;    // [k] column sums of D
+  const T* LA2;     // [P][n]
+  T* S;             // [P][n] in: X w_prev, out: X w
+  T* F2;            // [P][n] out: log2 S - LA2
+  T* W;             // [P][k]
+  T* mass;          // [P] sum_i S_i
+  T* err_acc;       // [P] violation numerators (reset here)
+  T* err;           // [P]
+  int* done;
+  int* iters;
+  int* status;
+  int it, max_iter;
+  T tol;
+  int penalty;
+  T eps, alpha;
+};
+
+// S = D w for problem p (rows strided over the block), F2 = log2 S - LA2 when LA2 != nullptr,
+// and the mass sum_i S_i.
+template <typename T>
+__device__ __forceinline__ T source_marginal(const T* __restrict__ Dt, const T* w_s, int n, int k,
+                                             T* __restrict__ S, T* __restrict__ F2, const T* __restrict__ LA2,
+                                             T* red) {
+  using P = Prec<T>;
+  T mass = T(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T s = T(0);
+    for (int j = 0; j < k; ++j) s = fma(Dt[(size_t)j * n + i], w_s[j], s);
+    // a subnormal FP32 mass is taken as 0 (the log2 instruction flushes it to -inf); such a row
+    // carries no source mass and drops out of the MM sum, as rows with s_i = 0 do
+    if (s < P::tiny()) s = T(0);
+    S[i] = s;
+    if (F2) F2[i] = s > T(0) ? P::log2(s) - LA2[i] : P::ninf();
+    mass += s;
+  }
+  return block_sum(mass, red);
+}
+
+// Per active problem (one CTA of 256 threads): convergence decision for the previous iteration,
+// then Table 2's MM step  nu_j = log w_j + (ln2 / x_j) sum_i D_ij (LA2_i - log2 S_i)  (rows with
+// S_i = 0 dropped), the penalty update, and the source step S = D w, F2 = log2 S - LA2.
+template <typename T, int KQ>
+__global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
+  using P = Prec<T>;
+  constexpr int KP = KQ * 32;
+  __shared__ T red_s[8][KP];
+  __shared__ T w_s[KP];
+  __shared__ T red[32];
+  __shared__ int stop;
+  const int slot = blockIdx.x;
+  if (slot >= *A.n_active) return;
+  const int p = A.active[slot];
+  const int n = A.n, k = A.k;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* LA2 = A.LA2 + (size_t)p * n;
+  T* S = A.S + (size_t)p * n;
+
+  if (A.it > 0) {
+    if (threadIdx.x == 0) {
+      const T e = A.err_acc[p] / A.mass[p];
+      A.err[p] = e;
+      int st = -1;
+      if (e != e) st = ST_NONFINITE;
+      else if (A.tol > T(0) && e <= A.tol) st = ST_CONVERGED;
+      else if (A.it >= A.max_iter) st = ST_MAX_ITER;
+      if (st >= 0) {
+        A.status[p] = st;
+        A.iters[p] = A.it;
+        A.done[p] = 1;
+      }
+      A.err_acc[p] = T(0);
+      stop = st >= 0;
+    }
+    __syncthreads();
+    if (stop) return;
+  }
+
+  // phase A: Dt r, r_i = LA2_i - log2 S_i (log2 units), 32 rows per warp step
+  T acc[KQ];
+#pragma unroll
+  for (int q = 0; q < KQ; ++q) acc[q] = T(0);
+  for (int base = warp * 32; base < n; base += 8 * 32) {
+    const int i = base + lane;
+    T r = T(0);
+    if (i < n) {
+      const T s = S[i];
+      r = s > T(0) ? LA2[i] - P::log2(s) : T(0);
+    }
+    const int cnt = min(32, n - base);
+    for (int t = 0; t < cnt; ++t) {
+      const T rt = __shfl_sync(0xffffffffu, r, t);
+      const T* Drow = A.D + (size_t)(base + t) * k;
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const int j = lane + 32 * q;
+        if (j < k) acc[q] = fma(Drow[j], rt, acc[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KQ; ++q) red_s[warp][lane + 32 * q] = acc[q];
+  __syncthreads();
+
+  // phase B: penalty update (Table 2)
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    T sum = T(0);
+#pragma unroll
+    for (int w8 = 0; w8 < 8; ++w8) sum += red_s[w8][j];
+    const T xj = A.xcol[j];
+    const T wold = A.W[(size_t)p * k + j];
+    const T nu = P::log(wold) + sum * T(kLn2) / xj;
+    T wn;
+    if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
+    else if (A.penalty == PEN_L2SQ) {
+      const T c = A.alpha / (A.eps * xj);
+      wn = wright_omega<T>(P::log(c) + nu) / c;
+    } else wn = P::exp(nu);
+    A.W[(size_t)p * k + j] = wn;
+    w_s[j] = wn;
+  }
+  __syncthreads();
+
+  // phase C: source step
+  const T mass = source_marginal<T>(A.Dt, w_s, n, k, S, A.F2 + (size_t)p * n, LA2, red);
+  if (threadIdx.x == 0) A.mass[p] = mass;
+}
+
+// S = D w0 and its mass for every problem of the batch (one CTA per problem).
+template <typename T>
+__global__ void __launch_bounds__(256) source_init_kernel(const T* Dt, const T* W, T* S, T* mass, int n, int k) {
+  __shared__ T w_s[256];
+  __shared__ T red[32];
+  const int p = blockIdx.x;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) w_s[j] = W[(size_t)p * k + j];
+  __syncthreads();
+  const T m = source_marginal<T>(Dt, w_s, n, k, S + (size_t)p * n, nullptr, nullptr, red);
+  if (threadIdx.x == 0) mass[p] = m;
+}
+
+// Order-preserving removal of finished problems from the active list (one CTA, in place).
+__global__ void __launch_bounds__(1024) compact_kernel(int* active, int* n_active, const int* done) {
+  __shared__ int warp_tot[32];
+  __shared__ int total_s;
+  const int na = *n_active;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int out = 0;
+  for (int base = 0; base < na; base += 1024) {
+    const int idx = base + threadIdx.x;
+    const int p = idx < na ? active[idx] : -1;
+    const int keep = (p >= 0 && !done[p]) ? 1 : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int before = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+      const int v = warp_tot[lane];
+      int incl = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      warp_tot[lane] = incl - v;
+      if (lane == 31) total_s = incl;
+    }
+    __syncthreads();
+    if (keep) active[out + warp_tot[warp] + before] = p;
+    out += total_s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_active = out;
+}
+
+template <typename T>
+struct PrepArgs {
+  const T* x; const T* D; const T* w_in; const T* g_in; const T* y;
+  T* xt; T* Dt; T* xcol; T* W; T* G2;
+  int* active; int* done; int* n_active; T* err_acc; int* iters; int* status; T* err;
+  int batch, n, k;
+  T xscale;    // 1 / sqrt(eps ln2)
+  T gscale;    // 1 / (eps ln2)
+};
+
+// Per-solve preparation: scaled grid, transposed dictionary and its column sums, weights and
+// potentials copied in, active list reset.  Grid-stride over the largest of the index spaces.
+template <typename T>
+__global__ void prep_kernel(PrepArgs<T> A) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nk = (size_t)A.n * A.k, bn = (size_t)A.batch * A.n, bk = (size_t)A.batch * A.k;
+  for (size_t e = tid; e < (size_t)A.n; e += stride) A.xt[e] = A.x[e] * A.xscale;
+  for (size_t e = tid; e < nk; e += stride) {
+    const size_t i = e / A.k, j = e - i * A.k;
+    A.Dt[j * A.n + i] = A.D[e];
+  }
+  for (size_t e = tid; e < bk; e += stride) A.W[e] = A.w_in[e];
+  for (size_t e = tid; e < bn; e += stride) A.G2[e] = A.g_in ? A.g_in[e] * A.gscale : T(0);
+  for (size_t e = tid; e < (size_t)A.batch; e += stride) {
+    A.active[e] = (int)e;
+    A.done[e] = 0;
+    A.err_acc[e] = T(0);
+    A.iters[e] = 0;
+    A.status[e] = ST_MAX_ITER;
+    A.err[e] = T(0);
+  }
+  if (tid == 0) *A.n_active = A.batch;
+}
+
+// Column sums x_j of the dictionary (one warp per column).
+template <typename T>
+__global__ void colsum_kernel(const T* Dt, T* xcol, int n, int k) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= k) return;
+  T s = T(0);
+  for (int i = lane; i < n; i += 32) s += Dt[(size_t)j * n + i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) xcol[j] = s;
+}
+
+template <typename T>
+struct FinArgs {
+  const T* W; const T* G2; const T* LB2; const int* iters; const int* status; const T* err;
+  T* w_out; T* g_out; T* t_out; int* iters_out; int* status_out; T* err_out;
+  int batch, n, k;
+  T gscale_inv;  // eps ln2
+};
+
+// Copy the solver state out: w, g = eps ln2 G2, t = Q^T 1 = 2^(G2 + LB2), per-problem stats.
+template <typename T>
+__global__ void finalize_kernel(FinArgs<T> A) {
+  using P = Prec<T>;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t bn = (size_t)A.batch * A.n, bk = (size_t)A.batch * A.k;
+  for (size_t e = tid; e < bk; e += stride) A.w_out[e] = A.W[e];
+  for (size_t e = tid; e < bn; e += stride) {
+    if (A.g_out) A.g_out[e] = A.G2[e] * A.gscale_inv;
+    if (A.t_out) A.t_out[e] = P::exp2(A.G2[e] + A.LB2[e]);
+  }
+  for (size_t e = tid; e < (size_t)A.batch; e += stride) {
+    if (A.iters_out) A.iters_out[e] = A.iters[e];
+    if (A.status_out) A.status_out[e] = A.status[e];
+    if (A.err_out) A.err_out[e] = A.err[e];
+  }
+}
+
+}  // namespace otlm

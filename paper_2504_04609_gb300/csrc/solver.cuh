@@ -1,0 +1,222 @@
+// Host driver of the batched scaling iteration: workspace layout and the per-iteration launch
+// sequence (source apply -> MM/source step -> compaction -> target apply/prox), for one precision.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace otlm {
+
+// Optional device timing of launches by kind: each launch is bracketed by two events on the
+// launching stream; pairs are harvested at the host's convergence polls and at the end of a solve.
+enum { KIND_APPLY = 0, KIND_MM = 1, KIND_COMPACT = 2, KIND_OTHER = 3, KIND_COUNT = 4 };
+
+struct Timer {
+  static constexpr int kPairs = 96;
+  bool on = false;
+  cudaEvent_t ev[2 * kPairs];
+  int kind[kPairs];
+  int used = 0;
+  double ms[KIND_COUNT] = {0, 0, 0, 0};
+  long long count[KIND_COUNT] = {0, 0, 0, 0};
+
+  cudaError_t create() {
+    for (int i = 0; i < 2 * kPairs; ++i) {
+      cudaError_t e = cudaEventCreate(&ev[i]);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  void destroy() {
+    for (int i = 0; i < 2 * kPairs; ++i) cudaEventDestroy(ev[i]);
+  }
+  // Sum the recorded pairs; the caller has synchronised the stream (or we wait here).
+  cudaError_t harvest() {
+    for (int i = 0; i < used; ++i) {
+      float t = 0.f;
+      cudaError_t e = cudaEventSynchronize(ev[2 * i + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      if (e != cudaSuccess) return e;
+      ms[kind[i]] += t;
+      count[kind[i]] += 1;
+    }
+    used = 0;
+    return cudaSuccess;
+  }
+};
+
+struct Launch {
+  cudaStream_t stream;
+  long long* counter;
+  int* host_flag;  // pinned int used for the convergence polls
+  Timer* timer;    // may be null
+
+  // Bracket one launch: call begin(kind) before and end() after it.
+  void begin(int k) const {
+    if (timer && timer->on) {
+      if (timer->used == Timer::kPairs) timer->harvest();
+      timer->kind[timer->used] = k;
+      cudaEventRecord(timer->ev[2 * timer->used], stream);
+    }
+  }
+  void end() const {
+    ++*counter;
+    if (timer && timer->on) {
+      cudaEventRecord(timer->ev[2 * timer->used + 1], stream);
+      ++timer->used;
+    }
+  }
+};
+
+template <typename T>
+struct Workspace {
+  T *xt, *Dt, *xcol, *G2, *LA2, *LB2, *F2, *S, *W, *mass, *err_acc, *err;
+  int *active, *n_active, *done, *iters, *status;
+  double* kmass;
+};
+
+inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Bytes of one workspace for the given maxima, and the carving of a base pointer into it.
+template <typename T>
+size_t carve_workspace(void* base, int n_max, int k_max, int batch_max, Workspace<T>* ws) {
+  const size_t bn = (size_t)batch_max * n_max, bk = (size_t)batch_max * k_max;
+  size_t off = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? b + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  Workspace<T> w;
+  w.xt = (T*)take(sizeof(T) * n_max);
+  w.Dt = (T*)take(sizeof(T) * (size_t)n_max * k_max);
+  w.xcol = (T*)take(sizeof(T) * k_max);
+  w.G2 = (T*)take(sizeof(T) * bn);
+  w.LA2 = (T*)take(sizeof(T) * bn);
+  w.LB2 = (T*)take(sizeof(T) * bn);
+  w.F2 = (T*)take(sizeof(T) * bn);
+  w.S = (T*)take(sizeof(T) * bn);
+  w.W = (T*)take(sizeof(T) * bk);
+  w.mass = (T*)take(sizeof(T) * batch_max);
+  w.err_acc = (T*)take(sizeof(T) * batch_max);
+  w.err = (T*)take(sizeof(T) * batch_max);
+  w.active = (int*)take(sizeof(int) * batch_max);
+  w.n_active = (int*)take(sizeof(int) * 32);
+  w.done = (int*)take(sizeof(int) * batch_max);
+  w.iters = (int*)take(sizeof(int) * batch_max);
+  w.status = (int*)take(sizeof(int) * batch_max);
+  w.kmass = (double*)take(sizeof(double) * 4);
+  if (ws) *ws = w;
+  return off;
+}
+
+struct SolveParams {
+  int batch, n, k;
+  double eps, lam, alpha;
+  int datafit, penalty, max_iter, poll_every;
+  double tol;
+};
+
+template <typename T> struct TileFor;
+template <> struct TileFor<float> { using type = ApplyTile<float, 4, 4, 2, 2, 64>; };
+template <> struct TileFor<double> { using type = ApplyTile<double, 2, 2, 2, 2, 32>; };
+
+template <typename T, int EPI>
+void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool safe, int batch, int n) {
+  using Cfg = typename TileFor<T>::type;
+  const dim3 grid((n + Cfg::TI - 1) / Cfg::TI, (batch + Cfg::TB - 1) / Cfg::TB);
+  L.begin(KIND_APPLY);
+  if (safe) apply_kernel<T, Cfg, EPI, true><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  else apply_kernel<T, Cfg, EPI, false><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  L.end();
+}
+
+template <typename T>
+void launch_mm(const Launch& L, const MMArgs<T>& a, int batch) {
+  L.begin(KIND_MM);
+  if (a.k <= 32) mm_kernel<T, 1><<<batch, 256, 0, L.stream>>>(a);
+  else if (a.k <= 64) mm_kernel<T, 2><<<batch, 256, 0, L.stream>>>(a);
+  else if (a.k <= 128) mm_kernel<T, 4><<<batch, 256, 0, L.stream>>>(a);
+  else mm_kernel<T, 8><<<batch, 256, 0, L.stream>>>(a);
+  L.end();
+}
+
+// Run Algorithm 1 on device buffers.  Returns cudaSuccess or the first launch/copy error.
+template <typename T>
+cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const SolveParams& sp, const T* x, const T* D,
+                         const T* y, T* w, T* g, T* t_out, int* iters_out, T* err_out, int* status_out) {
+  const int batch = sp.batch, n = sp.n, k = sp.k;
+  const double eps_ln2 = sp.eps * kLn2;
+
+  PrepArgs<T> pa;
+  pa.x = x; pa.D = D; pa.w_in = w; pa.g_in = g; pa.y = y;
+  pa.xt = ws.xt; pa.Dt = ws.Dt; pa.xcol = ws.xcol; pa.W = ws.W; pa.G2 = ws.G2;
+  pa.active = ws.active; pa.done = ws.done; pa.n_active = ws.n_active; pa.err_acc = ws.err_acc;
+  pa.iters = ws.iters; pa.status = ws.status; pa.err = ws.err;
+  pa.batch = batch; pa.n = n; pa.k = k;
+  pa.xscale = T(1.0 / sqrt(eps_ln2));
+  pa.gscale = T(1.0 / eps_ln2);
+  L.begin(KIND_OTHER);
+  prep_kernel<T><<<1184, 256, 0, L.stream>>>(pa);
+  L.end();
+  L.begin(KIND_OTHER);
+  colsum_kernel<T><<<(k + 7) / 8, 256, 0, L.stream>>>(ws.Dt, ws.xcol, n, k);
+  L.end();
+  L.begin(KIND_OTHER);
+  source_init_kernel<T><<<batch, 256, 0, L.stream>>>(ws.Dt, ws.W, ws.S, ws.mass, n, k);
+  L.end();
+
+  ApplyArgs<T> src{};
+  src.in = ws.G2; src.out = ws.LA2; src.xt = ws.xt; src.active = ws.active; src.n_active = ws.n_active;
+  src.n = n; src.S = ws.S; src.err_acc = ws.err_acc;
+  ApplyArgs<T> tgt = src;
+  tgt.in = ws.F2; tgt.out = ws.LB2; tgt.check = 0; tgt.y = y; tgt.G2 = ws.G2; tgt.datafit = sp.datafit;
+  tgt.kl_coef = T(sp.lam / (sp.eps + sp.lam));
+  tgt.tv_bound = T(sp.lam / eps_ln2);
+  tgt.lam_over_eps = T(sp.lam / sp.eps);
+  tgt.log_lam_over_eps = T(log(sp.lam / sp.eps));
+
+  MMArgs<T> mm{};
+  mm.active = ws.active; mm.n_active = ws.n_active; mm.n = n; mm.k = k; mm.D = D; mm.Dt = ws.Dt;
+  mm.xcol = ws.xcol; mm.LA2 = ws.LA2; mm.S = ws.S; mm.F2 = ws.F2; mm.W = ws.W; mm.mass = ws.mass;
+  mm.err_acc = ws.err_acc; mm.err = ws.err; mm.done = ws.done; mm.iters = ws.iters; mm.status = ws.status;
+  mm.max_iter = sp.max_iter; mm.tol = T(sp.tol); mm.penalty = sp.penalty; mm.eps = T(sp.eps);
+  mm.alpha = T(sp.alpha);
+
+  for (int it = 0;; ++it) {
+    src.check = it > 0;
+    launch_apply<T, EPI_SOURCE>(L, src, it == 0, batch, n);
+    mm.it = it;
+    launch_mm<T>(L, mm, batch);
+    L.begin(KIND_COMPACT);
+    compact_kernel<<<1, 1024, 0, L.stream>>>(ws.active, ws.n_active, ws.done);
+    L.end();
+    if (it >= sp.max_iter) break;
+    launch_apply<T, EPI_TARGET>(L, tgt, it == 0, batch, n);
+    if ((it + 1) % sp.poll_every == 0) {
+      cudaError_t e = cudaMemcpyAsync(L.host_flag, ws.n_active, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+      if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();
+      if (e != cudaSuccess) return e;
+      if (*L.host_flag == 0) break;
+    }
+  }
+
+  FinArgs<T> fa;
+  fa.W = ws.W; fa.G2 = ws.G2; fa.LB2 = ws.LB2; fa.iters = ws.iters; fa.status = ws.status; fa.err = ws.err;
+  fa.w_out = w; fa.g_out = g; fa.t_out = t_out; fa.iters_out = iters_out; fa.status_out = status_out;
+  fa.err_out = err_out; fa.batch = batch; fa.n = n; fa.k = k; fa.gscale_inv = T(eps_ln2);
+  L.begin(KIND_OTHER);
+  finalize_kernel<T><<<1184, 256, 0, L.stream>>>(fa);
+  L.end();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();
+  return e;
+}
+
+}  // namespace otlm

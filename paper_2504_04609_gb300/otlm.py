@@ -1,0 +1,182 @@
+"""ctypes binding of the C ABI in include/otlm.h (argument marshalling only).
+
+Every step of the solver runs in libotlm.so; this module only converts torch tensors / numpy
+arrays to pointers.  There is no CPU fallback: if the library is missing or cannot be loaded,
+`lib()` raises.  Device buffers are torch CUDA tensors (torch provides memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libotlm.so")
+
+OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED = 0, -1, -2, -3, -4
+CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
+DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3}
+PENALTY = {"none": 0, "l1": 1, "l2sq": 2}
+PRECISION = {"fp32": 0, "fp64": 1}
+
+EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_host", "otlm_objective",
+           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_strerror")
+TIMING_KINDS = ("apply", "mm_source", "compact", "other")
+
+
+class otlm_config(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int), ("k_max", ctypes.c_int), ("batch_max", ctypes.c_int),
+                ("precision", ctypes.c_int), ("datafit", ctypes.c_int), ("penalty", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("poll_every", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libotlm.so (built by paper_2504_04609_gb300.build); raises if it is not there."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2504_04609_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.otlm_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(otlm_config), vp]
+        L.otlm_create.restype = i
+        L.otlm_destroy.argtypes = [vp]
+        L.otlm_destroy.restype = None
+        solve_args = [vp, i, i, i, vp, vp, vp, d, d, d, vp, vp, vp, vp, vp, vp]
+        L.otlm_solve.argtypes = solve_args
+        L.otlm_solve.restype = i
+        L.otlm_solve_host.argtypes = solve_args
+        L.otlm_solve_host.restype = i
+        L.otlm_objective.argtypes = [vp, i, i, i, vp, vp, vp, d, d, d, vp, vp, vp, vp]
+        L.otlm_objective.restype = i
+        L.otlm_launch_count.argtypes = [vp]
+        L.otlm_launch_count.restype = ctypes.c_longlong
+        L.otlm_set_timing.argtypes = [vp, i]
+        L.otlm_set_timing.restype = i
+        L.otlm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+        L.otlm_get_timing.restype = i
+        L.otlm_strerror.argtypes = [i]
+        L.otlm_strerror.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+class OTLMError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != OTLM_OK:
+        raise OTLMError(f"{what}: {lib().otlm_strerror(rc).decode()} ({rc})")
+
+
+def _ptr(t):
+    """Device/host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+@dataclass
+class SolveResult:
+    w: object
+    g: object
+    t: object
+    iters: object
+    err: object
+    status: object
+
+
+class Handle:
+    """Owns one otlm handle (workspace sized for n_max x k_max x batch_max)."""
+
+    def __init__(self, n_max, k_max, batch_max, precision="fp32", datafit="kl", penalty="l2sq",
+                 max_iter=1000, tol=0.0, poll_every=8, stream=None):
+        self.cfg = otlm_config(n_max, k_max, batch_max, PRECISION[precision], DATAFIT[datafit], PENALTY[penalty],
+                               max_iter, float(tol), poll_every)
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        _check(lib().otlm_create(ctypes.byref(self._h), ctypes.byref(self.cfg), stream), "otlm_create")
+
+    def close(self):
+        if self._h:
+            lib().otlm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return lib().otlm_launch_count(self._h)
+
+    def set_timing(self, enable: bool):
+        _check(lib().otlm_set_timing(self._h, int(bool(enable))), "otlm_set_timing")
+
+    def get_timing(self):
+        """{kind: (device ms, launches)} accumulated since the last call (resets the sums)."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_longlong * 4)()
+        _check(lib().otlm_get_timing(self._h, ms, cnt), "otlm_get_timing")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(TIMING_KINDS)}
+
+    def solve(self, x, D, y, eps, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):
+        """otlm_solve on torch CUDA tensors; w (and g) are updated in place."""
+        B, n = y.shape
+        k = D.shape[1]
+        rc = lib().otlm_solve(self._h, B, n, k, _ptr(x), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),
+                              _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
+        _check(rc, "otlm_solve")
+        return SolveResult(w, g, t_out, iters, err, status)
+
+    def solve_host(self, x, D, y, eps, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):
+        """otlm_solve_host on host (numpy or pinned torch CPU) buffers."""
+        B, n = y.shape
+        k = D.shape[1]
+        rc = lib().otlm_solve_host(self._h, B, n, k, _ptr(x), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),
+                                   _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
+        _check(rc, "otlm_solve_host")
+        return SolveResult(w, g, t_out, iters, err, status)
+
+    def objective(self, x, D, y, eps, lam, alpha, w, g, primal, dual):
+        B, n = y.shape
+        k = D.shape[1]
+        rc = lib().otlm_objective(self._h, B, n, k, _ptr(x), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),
+                                  _ptr(primal), _ptr(dual))
+        _check(rc, "otlm_objective")
+
+
+def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000, tol=0.0,
+          precision="fp32", poll_every=8):
+    """One-shot convenience: allocate a handle sized for this problem and solve on the GPU.
+
+    Inputs are torch CUDA tensors of the handle's dtype.  Returns SolveResult of CUDA tensors.
+    """
+    import torch
+    B, n = y.shape
+    k = D.shape[1]
+    h = Handle(n, k, B, precision, datafit, penalty, max_iter, tol, poll_every,
+               stream=torch.cuda.current_stream().cuda_stream)
+    dt = y.dtype
+    w = w0.clone()
+    g = torch.zeros_like(y) if g0 is None else g0.clone()
+    t = torch.empty_like(y)
+    iters = torch.empty(B, dtype=torch.int32, device=y.device)
+    err = torch.empty(B, dtype=dt, device=y.device)
+    status = torch.empty(B, dtype=torch.int32, device=y.device)
+    h.solve(x, D, y, eps, lam, alpha, w, g, t, iters, err, status)
+    torch.cuda.current_stream().synchronize()
+    h.close()
+    return SolveResult(w, g, t, iters, err, status)

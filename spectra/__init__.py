@@ -20,7 +20,7 @@ shared dictionary and one per target, so that a sub-batch of a workload reproduc
 same problems as the full batch.
 
 Every array is produced in float64 and then rounded to the precision the solver is given
-(`dtype`), so both sides see bit-identical input values.
+(`dtype`; float32 subnormals flushed to zero), so both sides see bit-identical input values.
 """
 from __future__ import annotations
 
@@ -76,6 +76,15 @@ def target(x: np.ndarray, mu: np.ndarray, sigma: np.ndarray, nnz: int, rng: np.r
     return y, w_true
 
 
+def to_dtype(a: np.ndarray, dtype) -> np.ndarray:
+    """Round to `dtype`; in float32, values below the smallest normal number become 0, matching
+    the flush-to-zero arithmetic of the FP32 kernels so both sides see the same input."""
+    out = np.asarray(a).astype(dtype)
+    if np.dtype(dtype) == np.float32:
+        out[np.abs(out) < np.finfo(np.float32).tiny] = 0.0
+    return out
+
+
 def batch(workload: int, B: int, n: int, k: int, nnz: int, dtype=np.float32, first: int = 0):
     """A batch of B targets sharing one grid and one dictionary.
 
@@ -89,7 +98,7 @@ def batch(workload: int, B: int, n: int, k: int, nnz: int, dtype=np.float32, fir
     W = np.empty((B, k))
     for p in range(B):
         Y[p], W[p] = target(x, mu, sigma, nnz, _rng(workload, 1, first + p))
-    return dict(x=x.astype(dtype), D=D.astype(dtype), y=Y.astype(dtype), w_true=W)
+    return dict(x=to_dtype(x, dtype), D=to_dtype(D, dtype), y=to_dtype(Y, dtype), w_true=W)
 
 
 def ragged(workload: int, count: int, n_range=(256, 4096), k_range=(8, 128), eps_range=(2e-3, 5e-2),
@@ -108,7 +117,7 @@ def ragged(workload: int, count: int, n_range=(256, 4096), k_range=(8, 128), eps
         x = grid(n)
         D, mu, sigma = dictionary(x, k, rng)
         y, _ = target(x, mu, sigma, nnz, rng)
-        out.append(dict(x=x.astype(dtype), D=D.astype(dtype), y=y.astype(dtype), eps=eps, n=n, k=k))
+        out.append(dict(x=to_dtype(x, dtype), D=to_dtype(D, dtype), y=to_dtype(y, dtype), eps=eps, n=n, k=k))
     return out
 
 

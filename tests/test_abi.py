@@ -1,0 +1,61 @@
+"""CPU checks of the C ABI: the library loads, exports every function include/otlm.h declares,
+and rejects invalid arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2504_04609_gb300 import otlm as api
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _ensure_built():
+    if not os.path.exists(api.LIB_PATH):
+        from paper_2504_04609_gb300 import build
+        build.build()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "otlm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(otlm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared_functions() == sorted(api.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    _ensure_built()
+    L = ctypes.CDLL(api.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_strerror_names_every_code():
+    _ensure_built()
+    for code in (api.OTLM_OK, api.OTLM_EINVAL, api.OTLM_ECUDA, api.OTLM_ENOMEM, api.OTLM_EUNSUPPORTED):
+        assert api.lib().otlm_strerror(code).decode() not in ("", "unknown otlm status")
+    assert api.lib().otlm_strerror(12345).decode() == "unknown otlm status"
+
+
+@pytest.mark.parametrize("field,value", [("n_max", 1), ("k_max", 0), ("k_max", 257), ("batch_max", 0),
+                                         ("max_iter", 0), ("poll_every", 0), ("precision", 7),
+                                         ("datafit", 9), ("penalty", -1)])
+def test_create_rejects_bad_config_without_gpu(field, value):
+    _ensure_built()
+    cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p(123)
+    rc = api.lib().otlm_create(ctypes.byref(h), ctypes.byref(cfg), None)
+    assert rc == api.OTLM_EINVAL
+    assert h.value is None
+
+
+def test_null_handle_is_rejected():
+    _ensure_built()
+    rc = api.lib().otlm_solve(None, 1, 8, 2, 1, 1, 1, 0.1, 1.0, 0.1, 1, None, None, None, None, None)
+    assert rc == api.OTLM_EINVAL
+    assert api.lib().otlm_launch_count(None) == -1

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Parity is trajectory parity: same inputs, same initial state, same number of iterations; the
+oracle runs in FP64 on the FP32-rounded inputs the GPU gets.  Bar (FP32 path): relative L1 error
+<= 1e-5 in w and in the transported marginal t = Q^T 1.  FP64 path: 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import spectra
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2504_04609_gb300 import otlm as api  # noqa: E402
+
+TOL32 = 1e-5
+TOL64 = 1e-9
+
+
+def rel_l1(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
+
+
+def _gpu_solve(d, eps, lam, alpha, datafit, penalty, iters, tol=0.0, precision="fp32", g0=None, w0=None,
+               poll_every=4):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    dev = "cuda"
+    x = torch.tensor(d["x"], dtype=dt, device=dev)
+    D = torch.tensor(d["D"], dtype=dt, device=dev)
+    y = torch.tensor(d["y"], dtype=dt, device=dev)
+    if w0 is None:
+        w0 = spectra.initial_weights(d["y"], d["D"])
+    w = torch.tensor(w0, dtype=dt, device=dev)
+    g = None if g0 is None else torch.tensor(g0, dtype=dt, device=dev)
+    r = api.solve(x, D, y, eps, lam, alpha, datafit, penalty, w, g, max_iter=iters, tol=tol,
+                  precision=precision, poll_every=poll_every)
+    return {k: getattr(r, k).cpu().numpy() for k in ("w", "g", "t", "iters", "err", "status")}
+
+
+def _oracle(d, p, eps, lam, alpha, datafit, penalty, iters, tol=0.0, g0=None, w0=None):
+    x = np.asarray(d["x"], dtype=np.float64)
+    D = np.asarray(d["D"], dtype=np.float64)
+    y = np.asarray(d["y"][p], dtype=np.float64)
+    if w0 is None:
+        w0 = spectra.initial_weights(y, D)
+    return oracle.solve_log(spectra.squared_cost(x), D, y, eps, lam, alpha, datafit, penalty, w0, iters, tol=tol, g0=g0)
+
+
+CASES = [  # (datafit, penalty, eps, lam, alpha)
+    ("kl", "l1", 5e-3, 1.0, 1e-2),
+    ("kl", "l2sq", 1e-2, 1.0, 1e-3),
+    ("l2", "l2sq", 1e-2, 1.0, 1e-3),
+    ("tv", "l1", 2e-2, 1.0, 1e-2),
+    ("balanced", "none", 2e-2, 1.0, 0.0),
+    ("l2", "none", 3e-2, 1.0, 0.0),
+    ("kl", "none", 2e-2, 0.5, 0.0),
+]
+
+
+@pytest.mark.parametrize("datafit,penalty,eps,lam,alpha", CASES)
+def test_fp32_trajectory_parity_small(datafit, penalty, eps, lam, alpha):
+    """B = 9 problems (two problem tiles, ragged), n = 300 (two row tiles, ragged), k = 12."""
+    d = spectra.batch(11, 9, 300, 12, 3)
+    T = 40
+    r = _gpu_solve(d, eps, lam, alpha, datafit, penalty, T)
+    assert np.all(r["iters"] == T) and np.all(r["status"] == api.MAX_ITER)
+    for p in range(9):
+        o = _oracle(d, p, eps, lam, alpha, datafit, penalty, T)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL32, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL32, (p, rel_l1(r["t"][p], o["t"]))
+        assert abs(float(r["err"][p]) - o["err"]) <= 1e-3 * o["err"] + 1e-6
+
+
+def test_fp64_single_target_n200():
+    """Single target, FP64, n = m = 200, k = 10, KL datafit, squared-l2 penalty, 500 iterations."""
+    c = spectra.WORKLOADS["single_fp64_n200"]
+    d = spectra.batch(c["id"], 1, c["n"], c["k"], c["nnz"], dtype=np.float64)
+    r = _gpu_solve(d, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"], precision="fp64")
+    o = _oracle(d, 0, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"])
+    assert int(r["iters"][0]) == c["iters"]
+    assert rel_l1(r["w"][0], o["w"]) <= TOL64
+    assert rel_l1(r["t"][0], o["t"]) <= TOL64
+    np.testing.assert_allclose(r["g"][0], o["g"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("datafit,penalty,eps,lam,alpha", [CASES[0], CASES[2], CASES[3]])
+def test_fp64_parity_matches_oracle_tightly(datafit, penalty, eps, lam, alpha):
+    d = spectra.batch(12, 3, 257, 33, 4, dtype=np.float64)
+    r = _gpu_solve(d, eps, lam, alpha, datafit, penalty, 60, precision="fp64")
+    for p in range(3):
+        o = _oracle(d, p, eps, lam, alpha, datafit, penalty, 60)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL64
+        assert rel_l1(r["t"][p], o["t"]) <= TOL64
+
+
+def test_stopping_rule_matches_oracle():
+    """tol = 1e-5: every problem stops at the oracle's iteration (a problem whose violation sits
+    within 0.2 % of tol at the deciding check may differ by one), and its state matches the oracle
+    run for the GPU's own iteration count."""
+    d = spectra.batch(13, 6, 256, 16, 3)
+    eps, lam, alpha = 5e-3, 1.0, 1e-2
+    r = _gpu_solve(d, eps, lam, alpha, "kl", "l1", 2000, tol=1e-5)
+    for p in range(6):
+        o = _oracle(d, p, eps, lam, alpha, "kl", "l1", 2000, tol=1e-5)
+        gi = int(r["iters"][p])
+        assert r["status"][p] == api.CONVERGED
+        if gi != o["iters"]:
+            near = np.abs(o["err_hist"] / 1e-5 - 1) < 2e-3
+            assert abs(gi - o["iters"]) == 1 and near.any(), (p, gi, o["iters"])
+        o2 = _oracle(d, p, eps, lam, alpha, "kl", "l1", gi)
+        assert rel_l1(r["w"][p], o2["w"]) <= TOL32
+        assert rel_l1(r["t"][p], o2["t"]) <= TOL32
+        assert float(r["err"][p]) <= 1e-5
+
+
+def test_warm_start_continues_the_trajectory():
+    """Solving T1 iterations and restarting from (w, g) for T2 more equals T1 + T2 iterations."""
+    d = spectra.batch(14, 4, 200, 10, 3)
+    args = (1e-2, 1.0, 1e-3, "kl", "l2sq")
+    a = _gpu_solve(d, *args, 30)
+    b = _gpu_solve(d, *args, 20, g0=a["g"], w0=a["w"])
+    c = _gpu_solve(d, *args, 50)
+    for p in range(4):
+        assert rel_l1(b["w"][p], c["w"][p]) <= 2e-6
+        assert rel_l1(b["t"][p], c["t"][p]) <= 2e-6
+
+
+def test_zero_bins_in_target_and_minimum_sizes():
+    """y with exact zeros (KL: g = -inf there), n = 2, k = 1, batch = 1."""
+    d = spectra.batch(15, 3, 64, 5, 2)
+    d["y"][:, :20] = 0.0
+    r = _gpu_solve(d, 2e-2, 1.0, 1e-2, "kl", "l1", 25)
+    for p in range(3):
+        o = _oracle(d, p, 2e-2, 1.0, 1e-2, "kl", "l1", 25)
+        assert np.all(r["t"][p][:20] == 0) and np.all(np.isneginf(r["g"][p][:20]))
+        assert rel_l1(r["w"][p], o["w"]) <= TOL32 and rel_l1(r["t"][p], o["t"]) <= TOL32
+    tiny = dict(x=np.array([0.0, 1.0], np.float32), D=np.array([[0.6], [0.4]], np.float32),
+                y=np.array([[0.3, 0.5]], np.float32))
+    r = _gpu_solve(tiny, 0.5, 1.0, 0.1, "kl", "l2sq", 15)
+    o = _oracle(tiny, 0, 0.5, 1.0, 0.1, "kl", "l2sq", 15)
+    assert rel_l1(r["w"][0], o["w"]) <= TOL32 and rel_l1(r["t"][0], o["t"]) <= TOL32
+
+
+def test_host_buffer_entry_point_matches_device_entry_point():
+    d = spectra.batch(16, 5, 130, 7, 3)
+    eps, lam, alpha = 1e-2, 1.0, 1e-3
+    dev = _gpu_solve(d, eps, lam, alpha, "l2", "l2sq", 20)
+    h = api.Handle(130, 7, 5, "fp32", "l2", "l2sq", 20, 0.0, 4)
+    w = spectra.initial_weights(d["y"], d["D"]).astype(np.float32)
+    g = np.zeros_like(d["y"])
+    t = np.empty_like(d["y"])
+    iters = np.empty(5, np.int32)
+    err = np.empty(5, np.float32)
+    status = np.empty(5, np.int32)
+    h.solve_host(d["x"], d["D"], d["y"], eps, lam, alpha, w, g, t, iters, err, status)
+    h.close()
+    np.testing.assert_array_equal(w, dev["w"])
+    np.testing.assert_array_equal(t, dev["t"])
+    np.testing.assert_array_equal(iters, dev["iters"])
+
+
+def test_invalid_problem_arguments_are_rejected():
+    d = spectra.batch(17, 2, 32, 4, 2)
+    h = api.Handle(32, 4, 2, "fp32", "kl", "l1", 5, 0.0, 4)
+    x, D, y = (torch.tensor(d[k], device="cuda") for k in ("x", "D", "y"))
+    w = torch.ones(2, 4, device="cuda")
+    for bad in (dict(eps=0.0), dict(eps=-1.0), dict(lam=0.0), dict(alpha=-1.0)):
+        kw = dict(eps=0.1, lam=1.0, alpha=0.1)
+        kw.update(bad)
+        with pytest.raises(api.OTLMError):
+            h.solve(x, D, y, kw["eps"], kw["lam"], kw["alpha"], w)
+    with pytest.raises(api.OTLMError):  # batch beyond the handle
+        h.solve(x, D, torch.zeros(3, 32, device="cuda"), 0.1, 1.0, 0.1, torch.ones(3, 4, device="cuda"))
+    h.close()
+
+
+@pytest.mark.parametrize("datafit,penalty,eps,lam,alpha", [CASES[0], CASES[2], CASES[3], CASES[4]])
+def test_objective_and_gap_match_oracle(datafit, penalty, eps, lam, alpha):
+    d = spectra.batch(18, 3, 200, 10, 3)
+    r = _gpu_solve(d, eps, lam, alpha, datafit, penalty, 30)
+    dt = torch.float32
+    h = api.Handle(200, 10, 3, "fp32", datafit, penalty, 30, 0.0, 4)
+    P = torch.empty(3, dtype=torch.float64, device="cuda")
+    Dv = torch.empty(3, dtype=torch.float64, device="cuda")
+    h.objective(torch.tensor(d["x"], device="cuda"), torch.tensor(d["D"], device="cuda"),
+                torch.tensor(d["y"], device="cuda"), eps, lam, alpha, torch.tensor(r["w"], dtype=dt, device="cuda"),
+                torch.tensor(r["g"], dtype=dt, device="cuda"), P, Dv)
+    torch.cuda.synchronize()
+    h.close()
+    C = spectra.squared_cost(d["x"].astype(np.float64))
+    for p in range(3):
+        Po, Do, _ = oracle.objective_and_dual(r["w"][p].astype(np.float64), r["g"][p].astype(np.float64), C,
+                                              d["D"].astype(np.float64), d["y"][p].astype(np.float64), eps, lam,
+                                              alpha, datafit, penalty)
+        if datafit == "balanced":
+            assert np.isfinite(P[p].item())
+        else:
+            assert P[p].item() == pytest.approx(Po, rel=2e-6)
+        assert Dv[p].item() == pytest.approx(Do, rel=2e-6)
+        assert P[p].item() - Dv[p].item() >= -1e-6 * abs(Po)
