@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) source_init_kernel(const T* Dt, const T* 
 }
 
 // Order-preserving removal of finished problems from the active list (one CTA, in place).
-__global__ void __launch_bounds__(1024) compact_kernel(int* active, int* n_active, const int* done) {
+static __global__ void __launch_bounds__(1024) compact_kernel(int* active, int* n_active, const int* done) {
   __shared__ int warp_tot[32];
   __shared__ int total_s;
   const int na = *n_active;
