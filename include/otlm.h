@@ -43,6 +43,7 @@ extern "C" {
 #define OTLM_ECUDA        -2  /* a CUDA runtime call failed (the CUDA error is not cleared)  */
 #define OTLM_ENOMEM       -3  /* workspace allocation failed                                  */
 #define OTLM_EUNSUPPORTED -4  /* valid request this build does not implement                  */
+#define OTLM_ESCRATCH     -5  /* problem too large for otlm_solve_noalloc's static scratch    */
 
 /* per-problem status written to status_out[] */
 #define OTLM_CONVERGED     0  /* e <= tol                                                     */
@@ -158,6 +159,30 @@ long long otlm_launch_count(otlm_handle h);
  * Errors: OTLM_EINVAL (NULL arguments), OTLM_ECUDA (event creation or query failed). */
 int otlm_set_timing(otlm_handle h, int enable);
 int otlm_get_timing(otlm_handle h, double* ms, long long* launches);
+
+/* FP32 solve that allocates nothing.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory themselves -- code living inside a host framework
+ * whose allocator owns the GPU's memory budget (an extra cudaMalloc could fail against the
+ * framework's quota or fragment its pool), or latency-critical loops in which cudaMalloc/cudaFree
+ * would synchronise the device.  It needs no handle: the caller passes inputs and outputs
+ * (device pointers, same meaning and layout as otlm_solve, float only) plus the options a handle
+ * would hold (datafit, penalty, max_iter, tol) and a cudaStream_t (NULL = default stream).
+ * All workspace comes from one statically allocated 16 MiB __device__ array that every GPU
+ * loading the library reserves until process exit; no cudaMalloc, cudaFree or allocating
+ * library routine is called.  The problem fits when its workspace (about 4 * (5 batch*n + n*k
+ * + batch*k + 8 batch) bytes) is at most 16 MiB, e.g. batch 64 at n = 4096 and k = 128;
+ * larger problems return OTLM_ESCRATCH before any work is queued.
+ * The first call on a device looks up the array's device address (with that device current)
+ * and caches it; make that first call before any stream capture.  Every call on a device
+ * shares the one array and it keeps the previous call's contents (each solve re-initialises
+ * what it reads), so calls whose GPU work overlaps -- two streams, two host threads -- race.
+ * The host waits at the convergence polls (every 8 iterations) like otlm_solve.
+ * Errors: OTLM_EINVAL (as otlm_solve, plus unknown datafit/penalty, max_iter < 1),
+ * OTLM_ESCRATCH, OTLM_ECUDA. */
+int otlm_solve_noalloc(int batch, int n, int k, const float* x, const float* D, const float* y,
+                       double eps, double lam, double alpha, int datafit, int penalty, int max_iter,
+                       double tol, float* w, float* g, float* t_out, int* iters_out, float* err_out,
+                       int* status_out, void* cuda_stream);
 
 /* Static description of a status code; never NULL. */
 const char* otlm_strerror(int code);

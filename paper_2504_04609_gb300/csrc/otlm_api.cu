@@ -228,6 +228,7 @@ const char* otlm_strerror(int code) {
     case OTLM_ECUDA: return "CUDA runtime error";
     case OTLM_ENOMEM: return "device allocation failed";
     case OTLM_EUNSUPPORTED: return "not supported by this build";
+    case OTLM_ESCRATCH: return "problem exceeds the 16 MiB static scratch of otlm_solve_noalloc";
     default: return "unknown otlm status";
   }
 }

@@ -15,14 +15,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libotlm.so")
 
-OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED = 0, -1, -2, -3, -4
+OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED, OTLM_ESCRATCH = 0, -1, -2, -3, -4, -5
 CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3}
 PENALTY = {"none": 0, "l1": 1, "l2sq": 2}
 PRECISION = {"fp32": 0, "fp64": 1}
 
 EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_host", "otlm_objective",
-           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_strerror")
+           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 
 
@@ -60,6 +60,8 @@ def lib() -> ctypes.CDLL:
         L.otlm_set_timing.restype = i
         L.otlm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.otlm_get_timing.restype = i
+        L.otlm_solve_noalloc.argtypes = [i, i, i, vp, vp, vp, d, d, d, i, i, i, d, vp, vp, vp, vp, vp, vp, vp]
+        L.otlm_solve_noalloc.restype = i
         L.otlm_strerror.argtypes = [i]
         L.otlm_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -156,6 +158,17 @@ class Handle:
         rc = lib().otlm_objective(self._h, B, n, k, _ptr(x), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),
                                   _ptr(primal), _ptr(dual))
         _check(rc, "otlm_objective")
+
+
+def solve_noalloc(x, D, y, eps, lam, alpha, datafit, penalty, max_iter, tol, w, g=None, t_out=None, iters=None,
+                  err=None, status=None, stream=None):
+    """otlm_solve_noalloc on float32 torch CUDA tensors: the solve with no device allocation by the
+    library (workspace in its static 16 MiB device array).  Returns the C status code."""
+    B, n = y.shape
+    k = D.shape[1]
+    return lib().otlm_solve_noalloc(B, n, k, _ptr(x), _ptr(D), _ptr(y), eps, lam, alpha, DATAFIT[datafit],
+                                    PENALTY[penalty], max_iter, tol, _ptr(w), _ptr(g), _ptr(t_out), _ptr(iters),
+                                    _ptr(err), _ptr(status), stream)
 
 
 def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000, tol=0.0,

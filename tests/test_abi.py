@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_names_every_code():
     _ensure_built()
-    for code in (api.OTLM_OK, api.OTLM_EINVAL, api.OTLM_ECUDA, api.OTLM_ENOMEM, api.OTLM_EUNSUPPORTED):
+    for code in (api.OTLM_OK, api.OTLM_EINVAL, api.OTLM_ECUDA, api.OTLM_ENOMEM, api.OTLM_EUNSUPPORTED, api.OTLM_ESCRATCH):
         assert api.lib().otlm_strerror(code).decode() not in ("", "unknown otlm status")
     assert api.lib().otlm_strerror(12345).decode() == "unknown otlm status"
 
