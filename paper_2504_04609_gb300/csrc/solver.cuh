@@ -123,16 +123,33 @@ struct SolveParams {
 };
 
 template <typename T> struct TileFor;
-template <> struct TileFor<float> { using type = ApplyTile<float, 4, 4, 2, 2, 64>; };
+// FP32 apply tile (problems per thread, rows per thread, warps along problems, warps along rows,
+// columns per staged chunk); chosen by the tile sweep recorded in profiles/.
+#ifndef OTLM_F32_RB
+#define OTLM_F32_RB 4
+#endif
+#ifndef OTLM_F32_RI
+#define OTLM_F32_RI 4
+#endif
+#ifndef OTLM_F32_WB
+#define OTLM_F32_WB 4
+#endif
+#ifndef OTLM_F32_TJ
+#define OTLM_F32_TJ 64
+#endif
+template <> struct TileFor<float> {
+  using type = ApplyTile<float, OTLM_F32_RB, OTLM_F32_RI, OTLM_F32_WB, 1, OTLM_F32_TJ>;
+};
 template <> struct TileFor<double> { using type = ApplyTile<double, 2, 2, 2, 2, 32>; };
 
+// first = true: no previous sums exist yet, shift by the diagonal term.
 template <typename T, int EPI>
-void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool safe, int batch, int n) {
+void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n) {
   using Cfg = typename TileFor<T>::type;
   const dim3 grid((n + Cfg::TI - 1) / Cfg::TI, (batch + Cfg::TB - 1) / Cfg::TB);
   L.begin(KIND_APPLY);
-  if (safe) apply_kernel<T, Cfg, EPI, true><<<grid, Cfg::NT, 0, L.stream>>>(a);
-  else apply_kernel<T, Cfg, EPI, false><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  else apply_kernel<T, Cfg, EPI, SHIFT_PREV><<<grid, Cfg::NT, 0, L.stream>>>(a);
   L.end();
 }
 
