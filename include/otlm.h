@@ -44,6 +44,7 @@ extern "C" {
 #define OTLM_ENOMEM       -3  /* workspace allocation failed                                  */
 #define OTLM_EUNSUPPORTED -4  /* valid request this build does not implement                  */
 #define OTLM_ESCRATCH     -5  /* problem too large for otlm_solve_noalloc's static scratch    */
+#define OTLM_ETIMEOUT     -6  /* a bounded device-side wait expired (tensor-core path)        */
 
 /* per-problem status written to status_out[] */
 #define OTLM_CONVERGED     0  /* e <= tol                                                     */
@@ -66,7 +67,13 @@ typedef enum {            /* weight penalty R(w), Table 2 */
 
 typedef enum {
   OTLM_PREC_FP32_LOG = 0,     /* FP32, scalings carried as log2 potentials (stable at small eps) */
-  OTLM_PREC_FP64     = 1      /* FP64 throughout, same log-domain arithmetic                   */
+  OTLM_PREC_FP64     = 1,     /* FP64 throughout, same log-domain arithmetic                   */
+  OTLM_PREC_BF16_TC  = 2      /* kernel applies as tensor-core GEMMs K V^T: BF16 hi/lo operands
+                                 (three products, ~16 mantissa bits), FP32 accumulation, a
+                                 per-problem max shift; potentials and updates in FP32.  Element
+                                 type float.  A problem whose apply underflows (a row with all
+                                 significant terms below 2^-126 of the problem's largest) reports
+                                 OTLM_NONFINITE.  otlm_objective on such a handle runs FP32 applies. */
 } otlm_precision;
 
 typedef struct otlm_config {

@@ -47,6 +47,8 @@ struct ApplyTile {
   static constexpr int TB = RB * WB, TI = 32 * RI * WI, NT = 32 * WB * WI;
 };
 
+enum { SHIFT_PREV = 0, SHIFT_DIAG = 1, SHIFT_EXACT = 2 };
+
 template <typename T, int N> struct VecLoad;  // N consecutive T from shared memory
 template <> struct VecLoad<float, 4> {
   static __device__ __forceinline__ void ld(const float* p, float* v) {
@@ -61,53 +63,197 @@ template <> struct VecLoad<double, 2> {
   }
 };
 
-// One sweep over all columns j. PASS 0: m = max_j(in_bj - c_ij); PASS 1: acc = sum_j 2^(in_bj - c_ij - m).
-template <typename T, class Cfg, int PASS>
-__device__ __forceinline__ void apply_sweep(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
-                                            const T (&xi)[Cfg::RI], int wb, T (&m)[Cfg::RB][Cfg::RI],
-                                            T (&acc)[Cfg::RB][Cfg::RI]) {
+// Packed FP32x2 arithmetic (two lanes of a 64-bit register per instruction).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Stage one chunk of TJ columns: the CTA's TB input rows into in_s[j][b] and the grid values.
+template <typename T, class Cfg>
+__device__ __forceinline__ void stage_chunk(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s, int j0) {
   using P = Prec<T>;
-  constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ, NT = Cfg::NT;
+  constexpr int TB = Cfg::TB, TJ = Cfg::TJ, NT = Cfg::NT;
   const int n = A.n;
-  for (int j0 = 0; j0 < n; j0 += TJ) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * TJ; e += NT) {
-      const int bb = e / TJ, jj = e - bb * TJ, j = j0 + jj, p = prob_s[bb];
-      in_s[jj * TB + bb] = (p >= 0 && j < n) ? A.in[(size_t)p * n + j] : P::ninf();
-    }
-    for (int jj = threadIdx.x; jj < TJ; jj += NT) xj_s[jj] = (j0 + jj < n) ? A.xt[j0 + jj] : T(0);
-    __syncthreads();
+  __syncthreads();
+  for (int e = threadIdx.x; e < TB * TJ; e += NT) {
+    const int bb = e / TJ, jj = e - bb * TJ, j = j0 + jj, p = prob_s[bb];
+    in_s[jj * TB + bb] = (p >= 0 && j < n) ? A.in[(size_t)p * n + j] : P::ninf();
+  }
+  for (int jj = threadIdx.x; jj < TJ; jj += NT) xj_s[jj] = (j0 + jj < n) ? A.xt[j0 + jj] : T(0);
+  __syncthreads();
+}
+
+// Exact shift: m = max_j (in_bj - c_ij), c_ij = (xt_i - xt_j)^2 (scalar; the rare path).
+template <typename T, class Cfg>
+__device__ __forceinline__ void sweep_max(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
+                                          const T (&xi)[Cfg::RI], int wb, T (&m)[Cfg::RB][Cfg::RI]) {
+  constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
+  for (int j0 = 0; j0 < A.n; j0 += TJ) {
+    stage_chunk<T, Cfg>(A, prob_s, in_s, xj_s, j0);
 #pragma unroll 4
     for (int jj = 0; jj < TJ; ++jj) {
       const T xj = xj_s[jj];
       T v[RB];
       VecLoad<T, RB>::ld(in_s + jj * TB + wb * RB, v);
-      T c[RI];
 #pragma unroll
       for (int r = 0; r < RI; ++r) {
         const T d = xi[r] - xj;
-        c[r] = d * d;
+#pragma unroll
+        for (int q = 0; q < RB; ++q) m[q][r] = fmax(m[q][r], v[q] - d * d);
       }
-#pragma unroll
-      for (int q = 0; q < RB; ++q)
-#pragma unroll
-        for (int r = 0; r < RI; ++r) {
-          if (PASS == 0) m[q][r] = fmax(m[q][r], v[q] - c[r]);
-          else acc[q][r] += P::exp2((v[q] - m[q][r]) - c[r]);
-        }
     }
   }
 }
 
-// Kernel apply with fused epilogue.  SAFE: exact max pass then sum pass.  Fast path (SAFE =
-// false): the previous sums in `out` serve as the shift; if any sum of the tile leaves
-// [2^-60, 2^60] or a shift is not finite, the CTA redoes the tile on the safe path.
-template <typename T, class Cfg, int EPI, bool SAFE>
+// Sum with a known shift: acc = sum_j 2^(in_bj - m_bi - c_ij).  Generic (double) version.
+template <typename T, class Cfg>
+__device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
+                                          const T (&xi)[Cfg::RI], int wb, const T (&m)[Cfg::RB][Cfg::RI],
+                                          T (&acc)[Cfg::RB][Cfg::RI]) {
+  using P = Prec<T>;
+  constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
+  for (int j0 = 0; j0 < A.n; j0 += TJ) {
+    stage_chunk<T, Cfg>(A, prob_s, in_s, xj_s, j0);
+#pragma unroll 4
+    for (int jj = 0; jj < TJ; ++jj) {
+      const T xj = xj_s[jj];
+      T v[RB];
+      VecLoad<T, RB>::ld(in_s + jj * TB + wb * RB, v);
+#pragma unroll
+      for (int r = 0; r < RI; ++r) {
+        const T d = xi[r] - xj;
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q][r] += P::exp2(fma(-d, d, v[q] - m[q][r]));
+      }
+    }
+  }
+}
+
+// FP32 path: centred expansion.  With a tile centre xc, di = xt_i - xc and dj = xt_j - xc,
+//   in_bj - m_bi - (xt_i - xt_j)^2 = h_bj + 2 di dj - q_bi,   h_bj = in_bj - dj^2,  q_bi = m_bi + di^2.
+// h is formed once per staged element, q once per row, so an element costs one FFMA and one FADD
+// plus the accumulate: on packed pairs of problems (fma/add.f32x2) that is three FP32 lane-ops per
+// element against one exponent-unit op, and the exponent unit (32 results / SM / clock) is the
+// bound.  The centre keeps di small (a tile spans TI rows) and dj is small for every column that
+// matters, so no large squares are added and cancelled.
+template <class Cfg>
+__device__ __forceinline__ void stage_chunk_f32(const ApplyArgs<float>& A, const int* prob_s, float* h_s, float* dj_s,
+                                                float xc, int j0) {
+  using P = Prec<float>;
+  constexpr int TB = Cfg::TB, TJ = Cfg::TJ, NT = Cfg::NT;
+  const int n = A.n;
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < TJ; jj += NT) {
+    const float d = (j0 + jj < n) ? A.xt[j0 + jj] - xc : 0.f;
+    dj_s[2 * jj] = d;
+    dj_s[2 * jj + 1] = d;
+  }
+  for (int e = threadIdx.x; e < TB * TJ; e += NT) {
+    const int bb = e / TJ, jj = e - bb * TJ, j = j0 + jj, p = prob_s[bb];
+    float h = P::ninf();
+    if (p >= 0 && j < n) {
+      const float d = A.xt[j] - xc;
+      h = fmaf(-d, d, A.in[(size_t)p * n + j]);
+    }
+    h_s[jj * TB + bb] = h;
+  }
+  __syncthreads();
+}
+
+template <class Cfg>
+__device__ __forceinline__ void sweep_max_f32(const ApplyArgs<float>& A, const int* prob_s, float* h_s, float* dj_s,
+                                              float xc, const float (&di)[Cfg::RI], int wb,
+                                              float (&m)[Cfg::RB][Cfg::RI]) {
+  constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
+  for (int j0 = 0; j0 < A.n; j0 += TJ) {
+    stage_chunk_f32<Cfg>(A, prob_s, h_s, dj_s, xc, j0);
+#pragma unroll 4
+    for (int jj = 0; jj < TJ; ++jj) {
+      const float dj = dj_s[2 * jj];
+      float h[RB];
+      VecLoad<float, RB>::ld(h_s + jj * TB + wb * RB, h);
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int q = 0; q < RB; ++q) m[q][r] = fmaxf(m[q][r], fmaf(2.f * di[r], dj, h[q]));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RI; ++r)
+#pragma unroll
+    for (int q = 0; q < RB; ++q) m[q][r] -= di[r] * di[r];
+}
+
+template <class Cfg>
+__device__ __forceinline__ void sweep_sum_f32(const ApplyArgs<float>& A, const int* prob_s, float* h_s, float* dj_s,
+                                              float xc, const float (&di)[Cfg::RI], int wb,
+                                              const float (&m)[Cfg::RB][Cfg::RI], float (&acc)[Cfg::RB][Cfg::RI]) {
+  using P = Prec<float>;
+  constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ, QP = RB / 2;
+  static_assert(RB == 4, "packed sweep expects 4 problems per thread");
+  uint64_t nq[QP][RI], acc2[QP][RI], tdi[RI];
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    tdi[r] = f2_pack(2.f * di[r], 2.f * di[r]);
+    const float d2 = di[r] * di[r];
+#pragma unroll
+    for (int p = 0; p < QP; ++p) {
+      nq[p][r] = f2_pack(-(m[2 * p][r] + d2), -(m[2 * p + 1][r] + d2));
+      acc2[p][r] = f2_pack(0.f, 0.f);
+    }
+  }
+  for (int j0 = 0; j0 < A.n; j0 += TJ) {
+    stage_chunk_f32<Cfg>(A, prob_s, h_s, dj_s, xc, j0);
+#pragma unroll 4
+    for (int jj = 0; jj < TJ; ++jj) {
+      const float2 dq = *reinterpret_cast<const float2*>(dj_s + 2 * jj);
+      const float4 hq = *reinterpret_cast<const float4*>(h_s + jj * TB + wb * RB);
+      const uint64_t dj2 = f2_pack(dq.x, dq.y);
+      const uint64_t h2[QP] = {f2_pack(hq.x, hq.y), f2_pack(hq.z, hq.w)};
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int p = 0; p < QP; ++p) {
+          const uint64_t u2 = f2_add(f2_fma(tdi[r], dj2, h2[p]), nq[p][r]);
+          float u0, u1;
+          f2_unpack(u2, u0, u1);
+          acc2[p][r] = f2_add(acc2[p][r], f2_pack(P::exp2(u0), P::exp2(u1)));
+        }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RI; ++r)
+#pragma unroll
+    for (int p = 0; p < QP; ++p) f2_unpack(acc2[p][r], acc[2 * p][r], acc[2 * p + 1][r]);
+}
+
+// Kernel apply with fused epilogue.  The sum needs a shift m_bi close to the result:
+//   SHIFT_PREV : the previous sums held in `out` (the iteration after the first),
+//   SHIFT_DIAG : the diagonal term in_bi (c_ii = 0, so every sum is >= 1; the first iteration),
+//   SHIFT_EXACT: an exact max pass first.
+// A fast shift is checked afterwards: if any sum of the tile leaves [2^-60, 2^60] (or a shift is
+// not finite) the CTA redoes its tile with the exact shift.
+template <typename T, class Cfg, int EPI, int SHIFT>
 __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
   using P = Prec<T>;
   constexpr int RB = Cfg::RB, RI = Cfg::RI, WB = Cfg::WB, TB = Cfg::TB, TI = Cfg::TI, TJ = Cfg::TJ;
   __shared__ __align__(16) T in_s[TJ * TB];
-  __shared__ T xj_s[TJ];
+  __shared__ __align__(16) T xj_s[2 * TJ];
   __shared__ int prob_s[TB];
   const int na = *A.n_active;
   const int b0 = blockIdx.y * TB;
@@ -122,28 +268,34 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
 #pragma unroll
   for (int q = 0; q < RB; ++q) pr[q] = prob_s[wb * RB + q];
   int row[RI];
-  T xi[RI];
+  T xi[RI], di[RI];
+  // tile centre for the FP32 expansion (any value is exact in real arithmetic; the middle of the
+  // tile keeps the squares small)
+  const T xc = T(0.5) * (A.xt[min(i0, n - 1)] + A.xt[min(i0 + TI - 1, n - 1)]);
 #pragma unroll
   for (int r = 0; r < RI; ++r) {
     row[r] = i0 + wi * 32 * RI + r * 32 + lane;
-    xi[r] = row[r] < n ? A.xt[row[r]] : T(0);
+    xi[r] = row[r] < n ? A.xt[row[r]] : xc;
+    di[r] = xi[r] - xc;
   }
   T m[RB][RI], acc[RB][RI];
-  bool safe = SAFE;
-  if (!SAFE) {
+  bool safe = SHIFT == SHIFT_EXACT;
+  if (!safe) {
+    const T* src = SHIFT == SHIFT_PREV ? A.out : A.in;
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r) {
         const bool ok = pr[q] >= 0 && row[r] < n;
-        m[q][r] = ok ? A.out[(size_t)pr[q] * n + row[r]] : T(0);
+        m[q][r] = ok ? src[(size_t)pr[q] * n + row[r]] : T(0);
         acc[q][r] = T(0);
         bad |= ok && !isfinite(m[q][r]);
       }
     safe = __syncthreads_or(bad);
     if (!safe) {
-      apply_sweep<T, Cfg, 1>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+      if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg>(A, prob_s, in_s, xj_s, xc, di, wb, m, acc);
+      else sweep_sum<T, Cfg>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
       bad = false;
 #pragma unroll
       for (int q = 0; q < RB; ++q)
@@ -160,14 +312,17 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r) { m[q][r] = P::ninf(); acc[q][r] = T(0); }
-    apply_sweep<T, Cfg, 0>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+    if constexpr (sizeof(T) == 4) sweep_max_f32<Cfg>(A, prob_s, in_s, xj_s, xc, di, wb, m);
+    else sweep_max<T, Cfg>(A, prob_s, in_s, xj_s, xi, wb, m);
 #pragma unroll
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r)
         if (!(m[q][r] > P::ninf())) m[q][r] = T(0);  // every term vanishes: the sum stays 0
-    apply_sweep<T, Cfg, 1>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+    if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg>(A, prob_s, in_s, xj_s, xc, di, wb, m, acc);
+      else sweep_sum<T, Cfg>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
   }
+  const bool prev_shift = SHIFT == SHIFT_PREV && !safe;  // then acc = a_new / a_old exactly
 
   // ---- epilogue -----------------------------------------------------------------------------
 #pragma unroll
@@ -190,7 +345,7 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
             // |LA2| would quantise it to |LA2| ulp.
             const T s = A.S[idx];
             if (s > T(0)) {
-              if (!safe) {
+              if (prev_shift) {
                 part += s * fabs(acc[q][r] - T(1));
               } else {
                 const T dl = v - A.out[idx];

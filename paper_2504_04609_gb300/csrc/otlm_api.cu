@@ -11,6 +11,7 @@
 #include "../../include/otlm.h"
 #include "objective.cuh"
 #include "solver.cuh"
+#include "tc_solver.cuh"
 
 using otlm::Launch;
 using otlm::SolveParams;
@@ -32,7 +33,7 @@ struct otlm_ctx {
 namespace {
 
 bool valid_enum(const otlm_config& c) {
-  return (c.precision == OTLM_PREC_FP32_LOG || c.precision == OTLM_PREC_FP64) &&
+  return (c.precision == OTLM_PREC_FP32_LOG || c.precision == OTLM_PREC_FP64 || c.precision == OTLM_PREC_BF16_TC) &&
          (c.datafit >= OTLM_DATAFIT_BALANCED && c.datafit <= OTLM_DATAFIT_L2) &&
          (c.penalty >= OTLM_PENALTY_NONE && c.penalty <= OTLM_PENALTY_L2SQ);
 }
@@ -40,7 +41,9 @@ bool valid_enum(const otlm_config& c) {
 size_t workspace_bytes(const otlm_config& c) {
   if (c.precision == OTLM_PREC_FP64)
     return otlm::carve_workspace<double>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
-  return otlm::carve_workspace<float>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
+  size_t bytes = otlm::carve_workspace<float>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
+  if (c.precision == OTLM_PREC_BF16_TC) bytes += otlm::carve_tc_workspace(nullptr, c.n_max, c.batch_max, nullptr);
+  return bytes;
 }
 
 int check_problem(const otlm_ctx* h, int batch, int n, int k, double eps, double lam, double alpha) {
@@ -67,8 +70,19 @@ int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* D, 
   Workspace<T> ws;
   otlm::carve_workspace<T>(h->ws, h->cfg.n_max, h->cfg.k_max, h->cfg.batch_max, &ws);
   Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
-  cudaError_t e = otlm::solve_device<T>(L, ws, sp, (const T*)x, (const T*)D, (const T*)y, (T*)w, (T*)g, (T*)t_out,
-                                        iters_out, (T*)err_out, status_out);
+  cudaError_t e;
+  if (h->cfg.precision == OTLM_PREC_BF16_TC) {
+    otlm::TcWorkspace tw;
+    const size_t base = otlm::carve_workspace<float>(nullptr, h->cfg.n_max, h->cfg.k_max, h->cfg.batch_max, nullptr);
+    otlm::carve_tc_workspace(static_cast<char*>(h->ws) + base, h->cfg.n_max, h->cfg.batch_max, &tw);
+    e = otlm::solve_device_tc(L, reinterpret_cast<const Workspace<float>&>(ws), tw, sp, (const float*)x,
+                              (const float*)D, (const float*)y, (float*)w, (float*)g, (float*)t_out, iters_out,
+                              (float*)err_out, status_out);
+  } else {
+    e = otlm::solve_device<T>(L, ws, sp, (const T*)x, (const T*)D, (const T*)y, (T*)w, (T*)g, (T*)t_out, iters_out,
+                              (T*)err_out, status_out);
+  }
+  if (e == cudaErrorLaunchTimeout) return OTLM_ETIMEOUT;
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
@@ -229,6 +243,7 @@ const char* otlm_strerror(int code) {
     case OTLM_ENOMEM: return "device allocation failed";
     case OTLM_EUNSUPPORTED: return "not supported by this build";
     case OTLM_ESCRATCH: return "problem exceeds the 16 MiB static scratch of otlm_solve_noalloc";
+    case OTLM_ETIMEOUT: return "a bounded device-side wait expired";
     default: return "unknown otlm status";
   }
 }

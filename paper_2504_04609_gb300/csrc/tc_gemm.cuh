@@ -1,0 +1,294 @@
+// tcgen05 (5th-generation tensor core) GEMM for the batched kernel apply, sm_100a/sm_103a.
+//
+//   out[map(c)][r] = sum_j ( Ahi[r][j] Bhi[c][j] + Ahi[r][j] Blo[c][j] + Alo[r][j] Bhi[c][j] )
+//
+// A = the Gibbs kernel K (rows r = grid bins), B = the scaled scalings V of the batch (rows
+// c = active problems), both BF16 and K-major (contiguous along j).  Each operand is carried as a
+// hi/lo pair of BF16 values (x = hi + lo); the three products recover ~16 mantissa bits per
+// element, enough for 1e-5 relative parity of the whole solve.  Accumulation is FP32 in tensor
+// memory (TMEM); the epilogue stores the raw FP32 sums problem-major.
+//
+// One CTA computes a 128 x 256 output tile over the whole reduction:
+//   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, 2-stage ring)
+//   warp 1 lane 0: MMA issuer  (tcgen05.mma kind::f16, 3 x 4 instructions per 64-wide k block)
+//   warps 4..7   : epilogue    (tcgen05.ld 32x32b, one TMEM lane quarter per warp)
+// Every wait on an mbarrier is bounded (about 2 s of %globaltimer); on expiry the CTA records an
+// error in *err, stops issuing work, waits boundedly for its committed MMAs and frees its TMEM.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace otlm {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
+constexpr int A_TILE = BM * BK * 2;                       // 16 KiB
+constexpr int B_TILE = BN * BK * 2;                       // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;      // 96 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int THREADS = 256;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;    // bounded waits: 2 s
+
+enum { ERR_NONE = 0, ERR_WAIT_TMA = 1, ERR_WAIT_MMA = 2, ERR_WAIT_ACC = 3 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier; false after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > WAIT_NS) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
+  d |= static_cast<uint64_t>(1) << 16;                  // leading-dimension offset (unused with this swizzle)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride between 8-row atoms
+  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version (fixed 0b001)
+  d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct GemmArgs {
+  float* out;          // out[map(c) * ld_out + r]
+  const int* col_map;  // column (slot) -> output row; nullptr: identity
+  const int* n_cols;   // number of valid columns on the device; nullptr: N
+  int M, N, Kd, ld_out;
+  int* err;            // first error code of any CTA (0: none)
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm3_bf16_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                      const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                      GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int ncols = g.n_cols ? *g.n_cols : g.N;
+  if (n0 >= ncols) return;  // the whole CTA leaves before any barrier or TMEM use
+
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);  // full[2], empty[2], acc
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+  int* fail = reinterpret_cast<int*>(bars + 9);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), acc_bar = smem_u32(bars + 2 * STAGES);
+  const uint32_t tiles = smem_u32(base);
+  auto a_hi = [&](int s) { return tiles + s * STAGE_BYTES; };
+  auto a_lo = [&](int s) { return tiles + s * STAGE_BYTES + A_TILE; };
+  auto b_hi = [&](int s) { return tiles + s * STAGE_BYTES + 2 * A_TILE; };
+  auto b_lo = [&](int s) { return tiles + s * STAGE_BYTES + 2 * A_TILE + B_TILE; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(acc_bar, 1);
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int nkb = (g.Kd + BK - 1) / BK;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int last_round[STAGES];
+    for (int s = 0; s < STAGES; ++s) last_round[s] = -1;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, r = kb / STAGES;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (r - 1) & 1)) {
+        atomicCAS(g.err, 0, ERR_WAIT_MMA);
+        atomicExch(fail, 1);
+        break;
+      }
+      if (*(volatile int*)fail) break;
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kb * BK, m0);
+      tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kb * BK, m0);
+      tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kb * BK, n0);
+      tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kb * BK, n0);
+      last_round[s] = r;
+    }
+    // on an error path, let the copies already issued land before the CTA releases its memory
+    if (*(volatile int*)fail)
+      for (int s = 0; s < STAGES; ++s)
+        if (last_round[s] >= 0) (void)mbar_wait(full0 + 8 * s, last_round[s] & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, r = kb / STAGES;
+      if (!mbar_wait(full0 + 8 * s, r & 1)) {
+        atomicCAS(g.err, 0, ERR_WAIT_TMA);
+        atomicExch(fail, 1);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
+        const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
+        umma_bf16(tmem, ah, bh, idesc, issued);
+        umma_bf16(tmem, ah, bl, idesc, 1);
+        umma_bf16(tmem, al, bh, idesc, 1);
+        issued = 1;
+      }
+      umma_commit(empty0 + 8 * s);
+    }
+    umma_commit(acc_bar);  // fires once every MMA issued above has completed
+  } else if (warp >= 4) {
+    // ---- epilogue: TMEM -> registers -> problem-major FP32 rows ----
+    const bool ok = mbar_wait(acc_bar, 0);
+    if (!ok) atomicCAS(g.err, 0, ERR_WAIT_ACC);
+    tc_fence_after();
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    if (ok && !*(volatile int*)fail) {
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        if (n0 + c0 >= ncols) break;  // warp-uniform
+        uint32_t v[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int col = n0 + c0 + c;
+          if (col < ncols && row < g.M) {
+            const int o = g.col_map ? g.col_map[col] : col;
+            g.out[static_cast<size_t>(o) * g.ld_out + row] = __uint_as_float(v[c]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    // on an error path make sure no committed MMA is still writing the accumulator
+    if (*(volatile int*)fail) (void)mbar_wait(acc_bar, 0);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---- host side: tensor maps through the driver entry point (no -lcuda link needed) ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map over rows x cols (row pitch `ld` elements), box = box_rows x 64 columns.
+inline bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launch the three-term GEMM: A* [M][ld] (M x Kd used), B* [N][ld] (N x Kd used).
+inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, const void* B_hi, const void* B_lo, int M, int N,
+                                int Kd, int ld, const GemmArgs& args, cudaStream_t stream) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm3_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  if (!make_map(&ta_hi, A_hi, M, Kd, ld, BM) || !make_map(&ta_lo, A_lo, M, Kd, ld, BM) ||
+      !make_map(&tb_hi, B_hi, N, Kd, ld, BN) || !make_map(&tb_lo, B_lo, N, Kd, ld, BN))
+    return cudaErrorInvalidValue;
+  const dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  gemm3_bf16_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace otlm

@@ -15,11 +15,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libotlm.so")
 
-OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED, OTLM_ESCRATCH = 0, -1, -2, -3, -4, -5
+OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED, OTLM_ESCRATCH, OTLM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3}
 PENALTY = {"none": 0, "l1": 1, "l2sq": 2}
-PRECISION = {"fp32": 0, "fp64": 1}
+PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 
 EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_host", "otlm_objective",
            "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_strerror")
@@ -182,7 +182,7 @@ def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000
     k = D.shape[1]
     h = Handle(n, k, B, precision, datafit, penalty, max_iter, tol, poll_every,
                stream=torch.cuda.current_stream().cuda_stream)
-    dt = y.dtype
+    dt = torch.float64 if precision == "fp64" else torch.float32
     w = w0.clone()
     g = torch.zeros_like(y) if g0 is None else g0.clone()
     t = torch.empty_like(y)

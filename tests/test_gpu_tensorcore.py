@@ -1,0 +1,87 @@
+"""GPU parity of the tensor-core mode (kernel applies as BF16 hi/lo tcgen05 GEMMs, FP32 accumulation)
+against the FP64 oracle, at the same 1e-5 relative bar as the FP32 path."""
+import numpy as np
+import pytest
+
+import oracle
+import spectra
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2504_04609_gb300 import otlm as api  # noqa: E402
+
+TOL = 1e-5
+
+
+def rel_l1(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
+
+
+def _solve(d, eps, lam, alpha, datafit, penalty, iters, tol=0.0, precision="bf16tc"):
+    dev = "cuda"
+    x, D, y = (torch.tensor(d[k], device=dev) for k in ("x", "D", "y"))
+    w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=torch.float32, device=dev)
+    r = api.solve(x, D, y, eps, lam, alpha, datafit, penalty, w, max_iter=iters, tol=tol, precision=precision,
+                  poll_every=4)
+    return {k: getattr(r, k).cpu().numpy() for k in ("w", "g", "t", "iters", "err", "status")}
+
+
+def _oracle(d, p, eps, lam, alpha, datafit, penalty, iters, tol=0.0):
+    D = d["D"].astype(np.float64)
+    y = d["y"][p].astype(np.float64)
+    return oracle.solve_log(spectra.squared_cost(d["x"].astype(np.float64)), D, y, eps, lam, alpha, datafit,
+                            penalty, spectra.initial_weights(y, D), iters, tol=tol)
+
+
+@pytest.mark.parametrize("datafit,penalty,eps,lam,alpha", [
+    ("l2", "l2sq", 1e-2, 1.0, 1e-3),
+    ("l2", "l1", 2e-2, 1.0, 1e-2),
+    ("kl", "l2sq", 5e-2, 1.0, 1e-3),
+    ("tv", "l1", 5e-2, 1.0, 1e-2),
+])
+def test_tensorcore_trajectory_parity_small(datafit, penalty, eps, lam, alpha):
+    """9 problems (one partial 256-column tile), n = 300 (three 128-row tiles, ragged; reduction
+    over five 64-wide blocks with a zero-filled tail), k = 12, 30 iterations."""
+    d = spectra.batch(31, 9, 300, 12, 3)
+    r = _solve(d, eps, lam, alpha, datafit, penalty, 30)
+    assert np.all(r["status"] == api.MAX_ITER) and np.all(r["iters"] == 30)
+    for p in range(9):
+        o = _oracle(d, p, eps, lam, alpha, datafit, penalty, 30)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
+
+
+def test_tensorcore_matches_fp32_path_with_tolerance_stop():
+    d = spectra.batch(32, 40, 512, 32, 4)
+    args = (1e-2, 1.0, 1e-3, "l2", "l2sq", 500, 1e-5)
+    a = _solve(d, *args, precision="bf16tc")
+    b = _solve(d, *args, precision="fp32")
+    assert np.all(a["status"] == api.CONVERGED) and np.all(b["status"] == api.CONVERGED)
+    assert np.max(np.abs(a["iters"] - b["iters"])) <= 1
+    same = a["iters"] == b["iters"]
+    for p in np.nonzero(same)[0]:
+        assert rel_l1(a["w"][p], b["w"][p]) <= 2 * TOL
+        assert rel_l1(a["t"][p], b["t"][p]) <= 2 * TOL
+
+
+def test_tensorcore_full_workload_sampled_against_oracle():
+    """4096 problems at n = 4096, k = 128 (the measured workload) solved to tol in one call."""
+    c = spectra.WORKLOADS["batch4096_n4096_l2_l2sq"]
+    B, n, k = c["B"], c["n"], c["k"]
+    d = spectra.batch(c["id"], B, n, k, c["nnz"])
+    r = _solve(d, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"], tol=c["tol"])
+    assert np.all(r["status"] == api.CONVERGED)
+    assert np.all(r["err"] <= c["tol"])
+    assert np.all(r["w"] >= 0) and np.all(r["t"] >= 0)
+    for p in (0, 1777, 4095):
+        o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"], tol=c["tol"])
+        gi = int(r["iters"][p])
+        if gi != o["iters"]:
+            e = o["err_hist"]
+            assert abs(gi - o["iters"]) == 1 and abs(e[min(gi, o["iters"]) - 1] / c["tol"] - 1) < 1e-2
+            o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], gi)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
