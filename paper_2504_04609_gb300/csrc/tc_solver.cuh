@@ -6,11 +6,13 @@
 // so every V lies in (0, 1] and the GEMM K V^T (tc_gemm.cuh) returns the raw sums; log2 a_pi =
 // M_p + log2(sum).  The target apply is the same with U_pi = 2^{F2_pi - M'_p}.  K is symmetric for
 // the squared distance on a grid, so one matrix serves both applies.  Per iteration:
-//   prep_src : datafit step from the previous target sums (Table 1), then the source operand V
-//   gemm     : source sums into ACC_src[it & 1]
-//   mm_tc    : violation from the ratio of raw sums, MM step (Table 2), source step, operand U
-//   compact  : drop finished problems
-//   gemm     : target sums into ACC_tgt
+//   prep_src  : datafit step from the previous target sums (Table 1), then the source operand V
+//   gemm      : source sums into ACC_src[it & 1]
+//   violation : source-marginal violation from the ratio of raw sums, stopping decision
+//   compact   : drop finished problems
+//   dtr, wupd : MM step (Table 2) as a tiled D^T r contraction and the weight update
+//   dw, opnd  : source step S = D w (tiled), then the target operand U
+//   gemm      : target sums into ACC_tgt
 // A sum that underflows to 0 (possible only when a row's significant terms lie more than ~2^-126
 // below the problem's largest term) makes the problem report OTLM_NONFINITE.
 #pragma once
@@ -198,85 +200,249 @@ __global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
   }
 }
 
-// MM step, source step and the target operand (one CTA of 256 threads per active slot, after the
-// finished problems have been compacted away so that the operand rows match the GEMM's columns).
-template <int KQ>
-__global__ void __launch_bounds__(256) tc_mm_kernel(TcIterArgs A) {
-  using P = Prec<float>;
-  constexpr int KP = KQ * 32;
-  __shared__ float red_s[8][KP];
-  __shared__ float w_s[KP];
-  __shared__ float red[32];
-  const int slot = blockIdx.x;
-  if (slot >= *A.n_active) return;
-  const int p = A.active[slot];
-  const int n = A.n, k = A.k;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cur = A.it & 1;
-  const float* acc = A.t.ACC_src[cur] + (size_t)p * n;
-  const float mcur = A.t.Msrc[cur][p];
-  float* S = A.S + (size_t)p * n;
+// ---- register-tiled contractions with the dictionary (the MM step and the source step) ----------
+//
+// dtr : NU[s][slot][j] = sum_{i in split s} D_ij r_i,  r_i = LA2_i - log2 S_i (rows with S_i = 0
+//       dropped).  CTA = 32 active slots x KP columns, 256 threads, register tile BPT problems x 4
+//       columns; rows staged 32 at a time; the row range is split DTR_SPLIT ways (deterministic
+//       partial sums, added in a fixed order by wupd).
+// wupd: w update of Table 2 from nu = log w + (ln2 / x_j) sum_s NU[s].
+// dw  : S = D w for 64 slots x 128 rows per CTA (register tile 8 problems x 4 rows, k staged 32 at
+//       a time), epilogue S, F2 = log2 S - LA2 and per-tile max(F2) and sum(S) partials.
+// opnd: per slot, reduce the partials (fixed order) and write the target operand row.
+constexpr int DTR_SPLIT = 4;
+constexpr int DW_ROWS = 128;
 
-  // MM step: nu_j = log w_j + (ln2 / x_j) sum_i D_ij (LA2_i - log2 S_i), LA2 = M + log2(sum)
-  float accq[KQ];
+struct TcMMBuf {
+  float* NU;     // [DTR_SPLIT][batch][256]
+  float* PMAX;   // [batch][ptiles]
+  float* PMASS;  // [batch][ptiles]
+  int ptiles;    // ceil(n_max / DW_ROWS)
+  int stride;    // rows per split of NU (batch_max)
+};
+
+inline size_t carve_tc_mm(void* base, int n_max, int batch_max, TcMMBuf* mb) {
+  size_t off = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? b + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  TcMMBuf m;
+  m.ptiles = (n_max + DW_ROWS - 1) / DW_ROWS;
+  m.stride = batch_max;
+  m.NU = (float*)take(4 * (size_t)DTR_SPLIT * batch_max * 256);
+  m.PMAX = (float*)take(4 * (size_t)batch_max * m.ptiles);
+  m.PMASS = (float*)take(4 * (size_t)batch_max * m.ptiles);
+  if (mb) *mb = m;
+  return off;
+}
+
+template <int KP>
+__global__ void __launch_bounds__(256) tc_dtr_kernel(TcIterArgs A, TcMMBuf M) {
+  using P = Prec<float>;
+  constexpr int TB = 32, CH = 32, NT = 256;
+  constexpr int TJ = KP / 4, TBG = NT / TJ, BPT = TB / TBG;
+  static_assert(TJ * TBG == NT && TBG * BPT == TB, "tile");
+  __shared__ __align__(16) float Ds[CH][KP];
+  __shared__ __align__(16) float Rs[CH][TB];
+  __shared__ int prob[TB];
+  __shared__ float mcur[TB];
+  const int na = *A.n_active;
+  const int slot0 = blockIdx.x * TB;
+  if (slot0 >= na) return;
+  const int n = A.n, k = A.k, cur = A.it & 1, tid = threadIdx.x;
+  const int split = blockIdx.y;
+  const int i_beg = (int)((long long)n * split / DTR_SPLIT), i_end = (int)((long long)n * (split + 1) / DTR_SPLIT);
+  if (tid < TB) {
+    const int p = slot0 + tid < na ? A.active[slot0 + tid] : -1;
+    prob[tid] = p;
+    mcur[tid] = p >= 0 ? A.t.Msrc[cur][p] : 0.f;
+  }
+  const int tj = tid % TJ, tb = tid / TJ;
+  float acc[BPT][4];
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) accq[q] = 0.f;
-  for (int base = warp * 32; base < n; base += 8 * 32) {
-    const int i = base + lane;
-    float r = 0.f;
-    if (i < n) {
-      const float s = S[i];
-      r = s > 0.f ? (mcur + P::log2(acc[i])) - P::log2(s) : 0.f;
+  for (int q = 0; q < BPT; ++q)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+  for (int i0 = i_beg; i0 < i_end; i0 += CH) {
+    __syncthreads();
+    for (int e = tid; e < CH * KP; e += NT) {
+      const int ii = e / KP, jj = e - ii * KP, i = i0 + ii;
+      Ds[ii][jj] = (i < i_end && jj < k) ? A.D[(size_t)i * k + jj] : 0.f;
     }
-    const int cnt = min(32, n - base);
-    for (int t = 0; t < cnt; ++t) {
-      const float rt = __shfl_sync(0xffffffffu, r, t);
-      const float* Drow = A.D + (size_t)(base + t) * k;
+    for (int e = tid; e < CH * TB; e += NT) {
+      const int b = e / CH, ii = e - b * CH, i = i0 + ii, p = prob[b];
+      float r = 0.f;
+      if (p >= 0 && i < i_end) {
+        const size_t idx = (size_t)p * n + i;
+        const float s = A.S[idx];
+        if (s > 0.f) r = (mcur[b] + P::log2(A.t.ACC_src[cur][idx])) - P::log2(s);
+      }
+      Rs[ii][b] = r;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < CH; ++ii) {
+      const float4 d = *reinterpret_cast<const float4*>(&Ds[ii][tj * 4]);
+      float rv[BPT];
+      if constexpr (BPT >= 4) {
 #pragma unroll
-      for (int q = 0; q < KQ; ++q) {
-        const int j = lane + 32 * q;
-        if (j < k) accq[q] = fmaf(Drow[j], rt, accq[q]);
+        for (int q = 0; q < BPT; q += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(&Rs[ii][tb * BPT + q]);
+          rv[q] = v.x; rv[q + 1] = v.y; rv[q + 2] = v.z; rv[q + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < BPT; ++q) rv[q] = Rs[ii][tb * BPT + q];
+      }
+#pragma unroll
+      for (int q = 0; q < BPT; ++q) {
+        acc[q][0] = fmaf(d.x, rv[q], acc[q][0]);
+        acc[q][1] = fmaf(d.y, rv[q], acc[q][1]);
+        acc[q][2] = fmaf(d.z, rv[q], acc[q][2]);
+        acc[q][3] = fmaf(d.w, rv[q], acc[q][3]);
       }
     }
   }
+  const int batch_stride = M.stride;
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) red_s[warp][lane + 32 * q] = accq[q];
-  __syncthreads();
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    float sum = 0.f;
-#pragma unroll
-    for (int w8 = 0; w8 < 8; ++w8) sum += red_s[w8][j];
-    const float xj = A.xcol[j];
-    const float wold = A.W[(size_t)p * k + j];
-    const float nu = P::log(wold) + sum * float(kLn2) / xj;
-    float wn;
-    if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
-    else if (A.penalty == PEN_L2SQ) {
-      const float c = A.alpha / (A.eps * xj);
-      wn = wright_omega<float>(P::log(c) + nu) / c;
-    } else wn = P::exp(nu);
-    A.W[(size_t)p * k + j] = wn;
-    w_s[j] = wn;
+  for (int q = 0; q < BPT; ++q) {
+    const int slot = slot0 + tb * BPT + q;
+    if (slot >= na) continue;
+    float4* dst = reinterpret_cast<float4*>(M.NU + ((size_t)split * batch_stride + slot) * 256 + tj * 4);
+    *dst = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
   }
-  __syncthreads();
+}
 
-  // source step: S = D w, F2 = log2 S - LA2, then the target operand from F2
-  float* F2 = A.F2 + (size_t)p * n;
-  float mass = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float s = 0.f;
-    for (int j = 0; j < k; ++j) s = fmaf(A.Dt[(size_t)j * n + i], w_s[j], s);
-    if (s < P::tiny()) s = 0.f;
-    S[i] = s;
-    const float a = acc[i];
-    F2[i] = (s > 0.f) ? P::log2(s) - (mcur + P::log2(a)) : P::ninf();
-    mass += s;
+__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M) {
+  using P = Prec<float>;
+  const int na = *A.n_active, k = A.k;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int slot = e / k, j = e - slot * k;
+  if (slot >= na) return;
+  const int p = A.active[slot];
+  float sum = 0.f;
+#pragma unroll
+  for (int s = 0; s < DTR_SPLIT; ++s) sum += M.NU[((size_t)s * M.stride + slot) * 256 + j];
+  const float xj = A.xcol[j];
+  const float nu = P::log(A.W[(size_t)p * k + j]) + sum * float(kLn2) / xj;
+  float wn;
+  if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
+  else if (A.penalty == PEN_L2SQ) {
+    const float c = A.alpha / (A.eps * xj);
+    wn = wright_omega<float>(P::log(c) + nu) / c;
+  } else wn = P::exp(nu);
+  A.W[(size_t)p * k + j] = wn;
+}
+
+__global__ void __launch_bounds__(256) tc_dw_kernel(TcIterArgs A, TcMMBuf M) {
+  using P = Prec<float>;
+  constexpr int TB = 64, TR = DW_ROWS, KC = 32, NT = 256;
+  __shared__ __align__(16) float Dts[KC][TR];  // Dt chunk [j][i]
+  __shared__ __align__(16) float Ws[KC][TB];   // w chunk [j][b]
+  __shared__ int prob[TB];
+  __shared__ float mcur[TB];
+  const int na = *A.n_active;
+  const int slot0 = blockIdx.y * TB;
+  if (slot0 >= na) return;
+  const int n = A.n, k = A.k, cur = A.it & 1, tid = threadIdx.x, lane = tid & 31;
+  const int r0 = blockIdx.x * TR;
+  if (tid < TB) {
+    const int p = slot0 + tid < na ? A.active[slot0 + tid] : -1;
+    prob[tid] = p;
+    mcur[tid] = p >= 0 ? A.t.Msrc[cur][p] : 0.f;
   }
-  mass = block_sum(mass, red);
-  if (threadIdx.x == 0) A.mass[p] = mass;
+  const int ti = tid % 32, tb = tid / 32;  // rows r0 + 4 ti .. +3, problems 8 tb .. +7
+  float acc[8][4];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+  for (int j0 = 0; j0 < k; j0 += KC) {
+    __syncthreads();
+    for (int e = tid; e < KC * TR; e += NT) {
+      const int jj = e / TR, ii = e - jj * TR, j = j0 + jj, i = r0 + ii;
+      Dts[jj][ii] = (j < k && i < n) ? A.Dt[(size_t)j * n + i] : 0.f;
+    }
+    for (int e = tid; e < KC * TB; e += NT) {
+      const int b = e / KC, jj = e - b * KC, j = j0 + jj, p = prob[b];
+      Ws[jj][b] = (p >= 0 && j < k) ? A.W[(size_t)p * k + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < KC; ++jj) {
+      const float4 d = *reinterpret_cast<const float4*>(&Dts[jj][ti * 4]);
+      const float4 wa = *reinterpret_cast<const float4*>(&Ws[jj][tb * 8]);
+      const float4 wb = *reinterpret_cast<const float4*>(&Ws[jj][tb * 8 + 4]);
+      const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        acc[q][0] = fmaf(d.x, wv[q], acc[q][0]);
+        acc[q][1] = fmaf(d.y, wv[q], acc[q][1]);
+        acc[q][2] = fmaf(d.z, wv[q], acc[q][2]);
+        acc[q][3] = fmaf(d.w, wv[q], acc[q][3]);
+      }
+    }
+  }
+  // epilogue: S (subnormal mass taken as 0), F2, per-tile max(F2) and sum(S)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int b = tb * 8 + q, p = prob[b];
+    float fm = -CUDART_INF_F, ms = 0.f;
+    if (p >= 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = r0 + ti * 4 + c;
+        if (i >= n) continue;
+        const size_t idx = (size_t)p * n + i;
+        const float s = acc[q][c] < P::tiny() ? 0.f : acc[q][c];
+        A.S[idx] = s;
+        const float f2 = s > 0.f ? P::log2(s) - (mcur[b] + P::log2(A.t.ACC_src[cur][idx])) : P::ninf();
+        A.F2[idx] = f2;
+        fm = fmaxf(fm, f2);
+        ms += s;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+      ms += __shfl_xor_sync(0xffffffffu, ms, o);
+    }
+    if (lane == 0 && p >= 0) {
+      M.PMAX[(size_t)p * M.ptiles + blockIdx.x] = fm;
+      M.PMASS[(size_t)p * M.ptiles + blockIdx.x] = ms;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) tc_operand_kernel(TcIterArgs A, TcMMBuf M) {
+  using P = Prec<float>;
+  __shared__ float mshift;
+  const int slot = blockIdx.x;
+  if (slot >= *A.n_active) return;
+  const int p = A.active[slot], n = A.n;
+  const int tiles = (n + DW_ROWS - 1) / DW_ROWS;
+  if (threadIdx.x == 0) {
+    float m = -CUDART_INF_F, ms = 0.f;
+    for (int t = 0; t < tiles; ++t) {
+      m = fmaxf(m, M.PMAX[(size_t)p * M.ptiles + t]);
+      ms += M.PMASS[(size_t)p * M.ptiles + t];
+    }
+    if (!(m > -CUDART_INF_F)) m = 0.f;
+    mshift = m;
+    A.mass[p] = ms;
+    A.t.Mtgt[p] = m;
+  }
   __syncthreads();
-  const float mt = write_operand(F2, n, A.t.ld, slot, A.t.Vhi, A.t.Vlo, red);
-  if (threadIdx.x == 0) A.t.Mtgt[p] = mt;
+  const float m = mshift;
+  const float* F2 = A.F2 + (size_t)p * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = P::exp2(F2[i] - m);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    A.t.Vhi[(size_t)slot * A.t.ld + i] = hi;
+    A.t.Vlo[(size_t)slot * A.t.ld + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
 }
 
 // t = Q^T 1 = 2^{G2 + LB2}, LB2 = Mtgt + log2(target sum); w, g and the per-problem statistics.
@@ -304,6 +470,7 @@ __global__ void tc_finalize_kernel(FinArgs<float> F, const float* ACC_tgt, const
 // Run Algorithm 1 with tensor-core applies (float buffers; x, D, y, w, g as in solve_device).
 // Returns cudaErrorLaunchTimeout when a GEMM reported an expired wait.
 inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, const TcWorkspace& tw,
+                                   const TcMMBuf& mb,
                                    const SolveParams& sp, const float* x, const float* D, const float* y, float* w,
                                    float* g, float* t_out, int* iters_out, float* err_out, int* status_out) {
   const int batch = sp.batch, n = sp.n, k = sp.k;
@@ -361,10 +528,22 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     }
     if (it >= sp.max_iter) break;
     L.begin(KIND_MM);
-    if (k <= 32) tc_mm_kernel<1><<<batch, 256, 0, L.stream>>>(ta);
-    else if (k <= 64) tc_mm_kernel<2><<<batch, 256, 0, L.stream>>>(ta);
-    else if (k <= 128) tc_mm_kernel<4><<<batch, 256, 0, L.stream>>>(ta);
-    else tc_mm_kernel<8><<<batch, 256, 0, L.stream>>>(ta);
+    {
+      const dim3 gA((batch + 31) / 32, DTR_SPLIT);
+      if (k <= 32) tc_dtr_kernel<32><<<gA, 256, 0, L.stream>>>(ta, mb);
+      else if (k <= 64) tc_dtr_kernel<64><<<gA, 256, 0, L.stream>>>(ta, mb);
+      else if (k <= 128) tc_dtr_kernel<128><<<gA, 256, 0, L.stream>>>(ta, mb);
+      else tc_dtr_kernel<256><<<gA, 256, 0, L.stream>>>(ta, mb);
+    }
+    L.end();
+    L.begin(KIND_MM);
+    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb);
+    L.end();
+    L.begin(KIND_MM);
+    tc_dw_kernel<<<dim3((n + DW_ROWS - 1) / DW_ROWS, (batch + 63) / 64), 256, 0, L.stream>>>(ta, mb);
+    L.end();
+    L.begin(KIND_MM);
+    tc_operand_kernel<<<batch, 256, 0, L.stream>>>(ta, mb);
     L.end();
     gs.out = tw.ACC_tgt;
     L.begin(KIND_APPLY);

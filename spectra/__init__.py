@@ -143,6 +143,9 @@ WORKLOADS = {
                                   penalty="l1", alpha=1e-2, iters=2000, tol=1e-5, dtype=np.float32),
     "batch4096_n4096_l2_l2sq": dict(id=3, B=4096, n=4096, k=128, nnz=5, eps=1e-2, datafit="l2", lam=1.0,
                                     penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
+    # the n=4096 workload at a quarter of the batch: the profiling case (a few hundred MB on the device)
+    "batch1024_n4096_l2_l2sq": dict(id=3, B=1024, n=4096, k=128, nnz=5, eps=1e-2, datafit="l2", lam=1.0,
+                                    penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
     "ragged10000_tv_l1": dict(id=4, count=10000, datafit="tv", lam=1.0, penalty="l1", alpha=1e-2,
                               iters=2000, tol=1e-5, dtype=np.float32),
     "warmstart_n2048_kl_l2sq": dict(id=5, n=2048, k=64, nnz=5, eps=5e-3, datafit="kl", lam=1.0,
