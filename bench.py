@@ -35,7 +35,7 @@ import spectra  # noqa: E402
 METRIC = "OTLM problems solved/s to 1e-5 marginal tol (n=4096) vs plain FP32 on 1 GB300; % roofline"
 SMS = 152
 MAX_SM_MHZ = 2070.0
-# exponent-unit results per SM per clock (MUFU.EX2); see DESIGN.md "Rooflines"
+# exponent-unit (MUFU.EX2) results per SM per clock on GB300; a throughput probe measured 30.3
 EX2_PER_SM_CLK = 32
 
 
@@ -254,7 +254,10 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": None, "launch_ms_avg": g_ms / max(g_cnt, 1),
                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained",
-                "issued_tensor_tflops": 3 * achieved_tf, "issued_frac": 3 * achieved_tf / peak_tf}
+                "issued_tensor_tflops": 3 * achieved_tf, "issued_frac": 3 * achieved_tf / peak_tf,
+                "traffic_note": "full-size launch not captured (multi-pass ncu at 1.5 GB); the 1024-problem "
+                                "profiling case reads 84 MB + writes 3 MB per launch = its algorithmic "
+                                "operand bytes (profiles/gemm3_bf16_n4096_b1024.md)"}
 
     # plain FP32 path: the log-sum-exp apply against the exponent unit
     it_fp = fp["iters"].astype(np.float64)
@@ -308,9 +311,6 @@ def run_ours(args, rank, world, local_rank):
                                "sample": f"{len(samp)} problem(s) of {args.workload} (n={n}) solved to tol by the "
                                          f"FP64 numpy oracle, {samp[0][1]} iterations, {secs:.1f} s"}
     return out
-
-
-KERNEL_REV = "apply-v1"
 
 
 def run_reference(args, rank):

@@ -8,7 +8,7 @@ Notation (paper, Sec. 3): X [N, M] non-negative dictionary, w [M] weights, y [N]
 C [N, N] cost, K = exp(-C/eps) (Sec. 2.2), u1 target-side scaling (starts at 1), u2 source-side
 scaling.  The plan is Q_ij = u2_i K_ij u1_j, so Q 1 = u2 * (K u1) and Q^T 1 = u1 * (K^T u2).
 
-Readings of passages the paper leaves garbled or open (the same list stands in the design doc):
+Readings of passages the paper leaves garbled or open:
   A1  objective: eps KL(Q||K) + lam L(Q^T 1 | y) + alpha R(w) with Q 1 = X w (the <C,Q> term
       printed beside eps KL(Q||K) would count the cost twice; Sec. 2.3 / Eq. OTLM).
   A2  Q_ij = u2_i K_ij u1_j (u2 scales the source rows; Sec. 2.3 updates, Algorithm 1).
