@@ -136,6 +136,36 @@ int otlm_solve_host(otlm_handle h, int batch, int n, int k,
                     void* w, void* g, void* t_out,
                     int* iters_out, void* err_out, int* status_out);
 
+/* Solve an UNEVEN batch in one persistent launch (Algorithm 1 per problem, FP32 log domain):
+ * problem p has its own grid size n[p] (2..n_max, n_max <= 4096), dictionary size k[p]
+ * (1..k_max), eps[p] > 0, grid, dictionary and target.  Arrays are concatenated over problems:
+ *   x, y, g, t_out  [sum n]     problem p at offset off_n[p]
+ *   D               [sum n k]   problem p at offset off_D[p], row-major [n[p]][k[p]]
+ *   w               [sum k]     problem p at offset off_k[p]; in: initial weights (> 0), out: result
+ *   n, k, eps, off_* , iters_out, err_out, status_out: [batch], device memory
+ * g: in/out potentials (NULL = cold start, no output); t_out may be NULL.  lam and alpha as in
+ * otlm_solve; datafit, penalty, max_iter and tol come from the handle, which must be
+ * OTLM_PREC_FP32_LOG.  One CTA solves one problem at a time with its state in shared memory; CTAs
+ * take problems largest-first from a device queue; the launch is captured in a CUDA graph (on an
+ * internal stream ordered after the handle's stream) and replayed while the arguments repeat.
+ * The host copies n, k, eps once to validate and order the batch (a synchronous copy).
+ * Errors: OTLM_EINVAL (sizes beyond the handle, eps <= 0, NULL pointers), OTLM_EUNSUPPORTED
+ * (handle not FP32), OTLM_ENOMEM, OTLM_ECUDA. */
+int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
+                      const long long* off_n, const long long* off_D, const long long* off_k,
+                      const float* x, const float* D, const float* y, double lam, double alpha,
+                      float* w, float* g, float* t_out, int* iters_out, float* err_out,
+                      int* status_out);
+
+/* Autotuner for otlm_solve_ragged (the paper has no counterpart): times each CTA size (128, 256,
+ * 512 threads) on every sample_every-th problem of the largest-first order for `iters`
+ * iterations, keeps the fastest on the handle and writes its thread count to *cta_threads_out.
+ * Caller buffers are not modified (w is copied).  Same argument rules as otlm_solve_ragged. */
+int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
+                     const long long* off_n, const long long* off_D, const long long* off_k,
+                     const float* x, const float* D, const float* y, double lam, double alpha,
+                     const float* w, int sample_every, int iters, int* cta_threads_out);
+
 /* Objective of a solver state (w, g), in FP64 (Eq. OTLM with the reading above).
  * From (w, g): a = K u1, s = D w, f = eps log(s/a); the plan Q = diag(e^{f/eps}) K diag(e^{g/eps})
  * satisfies Q 1 = D w, so primal_out = eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w) is the value

@@ -12,6 +12,10 @@
 #include "objective.cuh"
 #include "solver.cuh"
 #include "tc_solver.cuh"
+#include "ragged.cuh"
+
+#include <algorithm>
+#include <vector>
 
 using otlm::Launch;
 using otlm::SolveParams;
@@ -28,6 +32,13 @@ struct otlm_ctx {
   size_t elem = 4;
   otlm::Timer timer;
   bool timer_ready = false;
+  // uneven-batch path (allocated on first use)
+  int* rg_order = nullptr;         // [batch_max] queue order + 1 counter
+  cudaStream_t rg_stream = nullptr;
+  cudaEvent_t rg_ev[2] = {nullptr, nullptr};
+  cudaGraphExec_t rg_exec = nullptr;
+  unsigned char rg_key[sizeof(otlm::RaggedArgs) + 2 * sizeof(int)] = {};
+  int rg_variant = 1;              // CTA size chosen by otlm_tune_ragged (default 256 threads)
 };
 
 namespace {
@@ -101,6 +112,103 @@ int run_objective(otlm_ctx* h, const SolveParams& sp, const void* x, const void*
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
+
+// Validate an uneven batch on host copies of n, k, eps and build the largest-work-first order.
+int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps, std::vector<int>* order) {
+  const otlm_config& c = h->cfg;
+  if (c.precision != OTLM_PREC_FP32_LOG) return OTLM_EUNSUPPORTED;
+  if (batch < 1 || batch > c.batch_max || c.n_max > 4096) return OTLM_EINVAL;
+  std::vector<int> hn(batch), hk(batch);
+  std::vector<float> he(batch);
+  if (cudaMemcpy(hn.data(), n, sizeof(int) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hk.data(), k, sizeof(int) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(he.data(), eps, sizeof(float) * batch, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OTLM_ECUDA;
+  for (int p = 0; p < batch; ++p)
+    if (hn[p] < 2 || hn[p] > c.n_max || hk[p] < 1 || hk[p] > c.k_max || !(he[p] > 0.f) || !std::isfinite(he[p]))
+      return OTLM_EINVAL;
+  order->resize(batch);
+  for (int p = 0; p < batch; ++p) (*order)[p] = p;
+  std::stable_sort(order->begin(), order->end(),
+                   [&](int a, int b) { return (long long)hn[a] * hn[a] > (long long)hn[b] * hn[b]; });
+  if (!h->rg_order) {
+    if (cudaMalloc(&h->rg_order, sizeof(int) * (c.batch_max + 64)) != cudaSuccess) return OTLM_ENOMEM;
+    if (cudaStreamCreateWithFlags(&h->rg_stream, cudaStreamNonBlocking) != cudaSuccess) return OTLM_ECUDA;
+    for (cudaEvent_t& e : h->rg_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return OTLM_ECUDA;
+  }
+  return OTLM_OK;
+}
+
+// Launch the persistent kernel as a captured CUDA graph on the internal stream, ordered after
+// the handle's stream and before its later work.  The graph is re-instantiated only when the
+// arguments or the variant change.
+int ragged_run(otlm_ctx* h, const otlm::RaggedArgs& a, int variant, bool use_graph) {
+  int bps = 0;
+  size_t smem = 0;
+  if (otlm::ragged_prepare(variant, h->cfg.n_max, h->cfg.k_max, &bps, &smem) != cudaSuccess || bps < 1)
+    return OTLM_ECUDA;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const dim3 grid(std::max(1, std::min(sms * bps, a.batch)));
+  Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
+  cudaError_t e = cudaEventRecord(h->rg_ev[0], h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->rg_stream, h->rg_ev[0], 0);
+  if (e != cudaSuccess) return OTLM_ECUDA;
+  L.begin(otlm::KIND_APPLY);
+  if (use_graph) {
+    unsigned char key[sizeof(h->rg_key)];
+    std::memcpy(key, &a, sizeof(a));
+    std::memcpy(key + sizeof(a), &variant, sizeof(int));
+    const int gx = (int)grid.x;
+    std::memcpy(key + sizeof(a) + sizeof(int), &gx, sizeof(int));
+    if (!h->rg_exec || std::memcmp(key, h->rg_key, sizeof(key)) != 0) {
+      if (h->rg_exec) {
+        cudaGraphExecDestroy(h->rg_exec);
+        h->rg_exec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(h->rg_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaMemsetAsync(a.next, 0, sizeof(int), h->rg_stream);
+        otlm::ragged_launch(variant, grid, smem, h->rg_stream, a);
+        e = cudaStreamEndCapture(h->rg_stream, &graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->rg_exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return OTLM_ECUDA;
+      std::memcpy(h->rg_key, key, sizeof(key));
+    }
+    e = cudaGraphLaunch(h->rg_exec, h->rg_stream);
+  } else {
+    e = cudaMemsetAsync(a.next, 0, sizeof(int), h->rg_stream);
+    if (e == cudaSuccess) {
+      otlm::ragged_launch(variant, grid, smem, h->rg_stream, a);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->rg_ev[1], h->rg_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->rg_ev[1], 0);
+  L.end();
+  return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
+}
+
+otlm::RaggedArgs ragged_args(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps,
+                             const long long* off_n, const long long* off_D, const long long* off_k, const float* x,
+                             const float* D, const float* y, double lam, double alpha, float* w, float* g,
+                             float* t_out, int* iters_out, float* err_out, int* status_out) {
+  otlm::RaggedArgs a{};
+  a.batch = batch; a.order = h->rg_order; a.next = h->rg_order + h->cfg.batch_max;
+  a.n = n; a.k = k; a.eps = eps; a.off_n = off_n; a.off_D = off_D; a.off_k = off_k;
+  a.x = x; a.D = D; a.y = y; a.w = w; a.g_in = g; a.g_out = g; a.t_out = t_out;
+  a.iters = iters_out; a.err = err_out; a.status = status_out;
+  a.datafit = h->cfg.datafit; a.penalty = h->cfg.penalty; a.max_iter = h->cfg.max_iter;
+  a.lam = (float)lam; a.alpha = (float)alpha; a.tol = (float)h->cfg.tol;
+  a.n_max = h->cfg.n_max; a.k_max = h->cfg.k_max;
+  return a;
+}
+
 }  // namespace
 
 extern "C" {
@@ -139,6 +247,11 @@ void otlm_destroy(otlm_handle h) {
   if (h->stage) cudaFree(h->stage);
   cudaFreeHost(h->host_flag);
   if (h->timer_ready) h->timer.destroy();
+  if (h->rg_exec) cudaGraphExecDestroy(h->rg_exec);
+  if (h->rg_order) cudaFree(h->rg_order);
+  if (h->rg_stream) cudaStreamDestroy(h->rg_stream);
+  for (cudaEvent_t e : h->rg_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
@@ -213,6 +326,92 @@ int otlm_objective(otlm_handle h, int batch, int n, int k, const void* x, const 
   const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
   if (h->cfg.precision == OTLM_PREC_FP64) return run_objective<double>(h, sp, x, D, y, w, g, primal_out, dual_out);
   return run_objective<float>(h, sp, x, D, y, w, g, primal_out, dual_out);
+}
+
+int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
+                      const long long* off_n, const long long* off_D, const long long* off_k, const float* x,
+                      const float* D, const float* y, double lam, double alpha, float* w, float* g, float* t_out,
+                      int* iters_out, float* err_out, int* status_out) {
+  if (!h || !n || !k || !eps || !off_n || !off_D || !off_k || !x || !D || !y || !w || !iters_out || !err_out ||
+      !status_out)
+    return OTLM_EINVAL;
+  if ((h->cfg.datafit != OTLM_DATAFIT_BALANCED && !(lam > 0)) || !(alpha >= 0) ||
+      (h->cfg.penalty == OTLM_PENALTY_L2SQ && !(alpha > 0)))
+    return OTLM_EINVAL;
+  std::vector<int> order;
+  int rc = ragged_setup(h, batch, n, k, eps, &order);
+  if (rc != OTLM_OK) return rc;
+  if (cudaMemcpyAsync(h->rg_order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, h->stream) !=
+      cudaSuccess)
+    return OTLM_ECUDA;
+  const otlm::RaggedArgs a = ragged_args(h, batch, n, k, eps, off_n, off_D, off_k, x, D, y, lam, alpha, w, g, t_out,
+                                         iters_out, err_out, status_out);
+  rc = ragged_run(h, a, h->rg_variant, true);
+  if (rc == OTLM_OK && h->timer.on && cudaStreamSynchronize(h->stream) == cudaSuccess) h->timer.harvest();
+  return rc;
+}
+
+int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
+                     const long long* off_n, const long long* off_D, const long long* off_k, const float* x,
+                     const float* D, const float* y, double lam, double alpha, const float* w, int sample_every,
+                     int iters, int* cta_threads_out) {
+  if (!h || !n || !k || !eps || !off_n || !off_D || !off_k || !x || !D || !y || !w || sample_every < 1 || iters < 1)
+    return OTLM_EINVAL;
+  std::vector<int> order;
+  int rc = ragged_setup(h, batch, n, k, eps, &order);
+  if (rc != OTLM_OK) return rc;
+  // sample: every sample_every-th problem of the work order (so the sample spans the sizes)
+  std::vector<int> sample;
+  for (int i = 0; i < batch; i += sample_every) sample.push_back(order[i]);
+  long long last_k = 0;
+  int kk = 0;
+  if (cudaMemcpy(&last_k, off_k + (batch - 1), sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&kk, k + (batch - 1), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OTLM_ECUDA;
+  const size_t wn = (size_t)(last_k + kk);
+  float *wtmp = nullptr, *etmp = nullptr;
+  int *itmp = nullptr, *stmp = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaMalloc(&wtmp, sizeof(float) * wn) == cudaSuccess &&
+            cudaMalloc(&etmp, sizeof(float) * batch) == cudaSuccess &&
+            cudaMalloc(&itmp, sizeof(int) * batch) == cudaSuccess &&
+            cudaMalloc(&stmp, sizeof(int) * batch) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(h->rg_order, sample.data(), sizeof(int) * sample.size(), cudaMemcpyHostToDevice,
+                             h->stream) == cudaSuccess;
+  const int saved_iter = h->cfg.max_iter;
+  const double saved_tol = h->cfg.tol;
+  h->cfg.max_iter = iters;
+  h->cfg.tol = 0.0;
+  float best = 1e30f;
+  int best_v = h->rg_variant;
+  for (int v = 0; ok && v < otlm::RAGGED_VARIANTS; ++v) {
+    otlm::RaggedArgs a = ragged_args(h, (int)sample.size(), n, k, eps, off_n, off_D, off_k, x, D, y, lam, alpha,
+                                     wtmp, nullptr, nullptr, itmp, etmp, stmp);
+    for (int rep = 0; ok && rep < 2; ++rep) {  // the first run warms up
+      ok = cudaMemcpyAsync(wtmp, w, sizeof(float) * wn, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess &&
+           cudaEventRecord(e0, h->stream) == cudaSuccess && ragged_run(h, a, v, false) == OTLM_OK &&
+           cudaEventRecord(e1, h->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    }
+    float ms = 0.f;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  h->cfg.max_iter = saved_iter;
+  h->cfg.tol = saved_tol;
+  cudaFree(wtmp); cudaFree(etmp); cudaFree(itmp); cudaFree(stmp);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (!ok) return OTLM_ECUDA;
+  h->rg_variant = best_v;
+  if (h->rg_exec) {  // the cached graph was built for the previous order buffer contents / variant
+    cudaGraphExecDestroy(h->rg_exec);
+    h->rg_exec = nullptr;
+  }
+  if (cta_threads_out) *cta_threads_out = otlm::ragged_nt(best_v);
+  return OTLM_OK;
 }
 
 long long otlm_launch_count(otlm_handle h) { return h ? h->launches : -1; }

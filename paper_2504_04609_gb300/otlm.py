@@ -22,7 +22,8 @@ PENALTY = {"none": 0, "l1": 1, "l2sq": 2}
 PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 
 EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_host", "otlm_objective",
-           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_strerror")
+           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged",
+           "otlm_tune_ragged", "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 
 
@@ -62,6 +63,11 @@ def lib() -> ctypes.CDLL:
         L.otlm_get_timing.restype = i
         L.otlm_solve_noalloc.argtypes = [i, i, i, vp, vp, vp, d, d, d, i, i, i, d, vp, vp, vp, vp, vp, vp, vp]
         L.otlm_solve_noalloc.restype = i
+        L.otlm_solve_ragged.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp]
+        L.otlm_solve_ragged.restype = i
+        L.otlm_tune_ragged.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp, i, i,
+                                       ctypes.POINTER(ctypes.c_int)]
+        L.otlm_tune_ragged.restype = i
         L.otlm_strerror.argtypes = [i]
         L.otlm_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -152,6 +158,22 @@ class Handle:
         _check(rc, "otlm_solve_host")
         return SolveResult(w, g, t_out, iters, err, status)
 
+    def solve_ragged(self, rb, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):
+        """otlm_solve_ragged on a RaggedBatch of device tensors (see ragged_batch)."""
+        rc = lib().otlm_solve_ragged(self._h, rb.batch, _ptr(rb.n), _ptr(rb.k), _ptr(rb.eps), _ptr(rb.off_n),
+                                     _ptr(rb.off_D), _ptr(rb.off_k), _ptr(rb.x), _ptr(rb.D), _ptr(rb.y), lam, alpha,
+                                     _ptr(w), _ptr(g), _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
+        _check(rc, "otlm_solve_ragged")
+
+    def tune_ragged(self, rb, lam, alpha, w, sample_every=40, iters=6):
+        """otlm_tune_ragged: returns the CTA size the tuner kept on this handle."""
+        out = ctypes.c_int(0)
+        rc = lib().otlm_tune_ragged(self._h, rb.batch, _ptr(rb.n), _ptr(rb.k), _ptr(rb.eps), _ptr(rb.off_n),
+                                    _ptr(rb.off_D), _ptr(rb.off_k), _ptr(rb.x), _ptr(rb.D), _ptr(rb.y), lam, alpha,
+                                    _ptr(w), sample_every, iters, ctypes.byref(out))
+        _check(rc, "otlm_tune_ragged")
+        return out.value
+
     def objective(self, x, D, y, eps, lam, alpha, w, g, primal, dual):
         B, n = y.shape
         k = D.shape[1]
@@ -193,3 +215,31 @@ def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000
     torch.cuda.current_stream().synchronize()
     h.close()
     return SolveResult(w, g, t, iters, err, status)
+
+
+@dataclass
+class RaggedBatch:
+    batch: int
+    n: object
+    k: object
+    eps: object
+    off_n: object
+    off_D: object
+    off_k: object
+    x: object
+    D: object
+    y: object
+
+
+def ragged_batch(problems, device="cuda"):
+    """Concatenate a list of dicts(x, D, y, eps, n, k) (float32 arrays) into device tensors."""
+    import torch
+    n = np.array([p["n"] for p in problems], np.int32)
+    k = np.array([p["k"] for p in problems], np.int32)
+    off_n = np.concatenate([[0], np.cumsum(n.astype(np.int64))[:-1]]).astype(np.int64)
+    off_D = np.concatenate([[0], np.cumsum((n.astype(np.int64) * k))[:-1]]).astype(np.int64)
+    off_k = np.concatenate([[0], np.cumsum(k.astype(np.int64))[:-1]]).astype(np.int64)
+    cat = lambda key: np.concatenate([np.asarray(p[key], np.float32).ravel() for p in problems])  # noqa: E731
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+    return RaggedBatch(len(problems), t(n), t(k), t(np.array([p["eps"] for p in problems], np.float32)),
+                       t(off_n), t(off_D), t(off_k), t(cat("x")), t(cat("D")), t(cat("y")))
