@@ -50,6 +50,8 @@ extern "C" {
 #define OTLM_CONVERGED     0  /* e <= tol                                                     */
 #define OTLM_MAX_ITER      1  /* stopped at max_iter                                          */
 #define OTLM_NONFINITE     2  /* a NaN/Inf appeared in the violation e; state left as is      */
+#define OTLM_INVALID       3  /* otlm_solve_ragged: the problem's sizes or offsets fall outside
+                                 the packed arrays; the problem was not touched                */
 
 /* ---- problem options ----------------------------------------------------------------------- */
 typedef enum {            /* marginal datafit L(. | y), Table 1 */

@@ -13,7 +13,7 @@ namespace otlm {
 enum { EPI_SOURCE = 0, EPI_TARGET = 1 };
 enum { DF_BALANCED = 0, DF_KL = 1, DF_TV = 2, DF_L2 = 3 };
 enum { PEN_NONE = 0, PEN_L1 = 1, PEN_L2SQ = 2 };
-enum { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_NONFINITE = 2 };
+enum { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_NONFINITE = 2, ST_INVALID = 3 };
 
 template <typename T>
 struct ApplyArgs {

@@ -39,6 +39,7 @@ struct otlm_ctx {
   cudaGraphExec_t rg_exec = nullptr;
   unsigned char rg_key[sizeof(otlm::RaggedArgs) + 2 * sizeof(int)] = {};
   int rg_variant = 1;              // CTA size chosen by otlm_tune_ragged (default 256 threads)
+  long long rg_tot[3] = {0, 0, 0}; // packed sizes sum n, sum n k, sum k of the last batch
 };
 
 namespace {
@@ -127,6 +128,13 @@ int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float
   for (int p = 0; p < batch; ++p)
     if (hn[p] < 2 || hn[p] > c.n_max || hk[p] < 1 || hk[p] > c.k_max || !(he[p] > 0.f) || !std::isfinite(he[p]))
       return OTLM_EINVAL;
+  long long tn = 0, tD = 0, tk = 0;
+  for (int p = 0; p < batch; ++p) {
+    tn += hn[p];
+    tD += (long long)hn[p] * hk[p];
+    tk += hk[p];
+  }
+  h->rg_tot[0] = tn; h->rg_tot[1] = tD; h->rg_tot[2] = tk;
   order->resize(batch);
   for (int p = 0; p < batch; ++p) (*order)[p] = p;
   std::stable_sort(order->begin(), order->end(),
@@ -143,11 +151,13 @@ int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float
 // Launch the persistent kernel as a captured CUDA graph on the internal stream, ordered after
 // the handle's stream and before its later work.  The graph is re-instantiated only when the
 // arguments or the variant change.
-int ragged_run(otlm_ctx* h, const otlm::RaggedArgs& a, int variant, bool use_graph) {
+int ragged_run(otlm_ctx* h, const otlm::RaggedArgs& a0, int variant, bool use_graph) {
   int bps = 0;
   size_t smem = 0;
   if (otlm::ragged_prepare(variant, h->cfg.n_max, h->cfg.k_max, &bps, &smem) != cudaSuccess || bps < 1)
     return OTLM_ECUDA;
+  otlm::RaggedArgs a = a0;
+  a.smem_floats = (int)(smem / 4);
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -206,6 +216,7 @@ otlm::RaggedArgs ragged_args(otlm_ctx* h, int batch, const int* n, const int* k,
   a.datafit = h->cfg.datafit; a.penalty = h->cfg.penalty; a.max_iter = h->cfg.max_iter;
   a.lam = (float)lam; a.alpha = (float)alpha; a.tol = (float)h->cfg.tol;
   a.n_max = h->cfg.n_max; a.k_max = h->cfg.k_max;
+  a.tot_n = h->rg_tot[0]; a.tot_D = h->rg_tot[1]; a.tot_k = h->rg_tot[2];
   return a;
 }
 

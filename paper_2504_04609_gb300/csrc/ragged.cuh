@@ -41,6 +41,8 @@ struct RaggedArgs {
   int datafit, penalty, max_iter;
   float lam, alpha, tol;
   int n_max, k_max;
+  long long tot_n, tot_D, tot_k;  // packed sizes of x/y, D and w (sum n, sum n k, sum k)
+  int smem_floats;                // dynamic shared memory of the launch, in floats
 };
 
 template <int NT>
@@ -176,6 +178,20 @@ __device__ void ragged_solve_one(const RaggedArgs& A, int p, float* sm) {
   const float eps = A.eps[p];
   const float eps_ln2 = eps * float(kLn2);
   const long long on = A.off_n[p], oD = A.off_D[p], ok = A.off_k[p];
+  // a problem whose sizes or offsets fall outside the packed arrays is marked invalid and not
+  // touched; the barrier also separates the previous problem's last reads from this one's writes
+  const bool valid = n >= 2 && n <= A.n_max && k >= 1 && k <= A.k_max && (n + NT - 1) / NT <= R && on >= 0 &&
+                     on + n <= A.tot_n && oD >= 0 && oD + (long long)n * k <= A.tot_D && ok >= 0 &&
+                     ok + k <= A.tot_k &&
+                     6 * (long long)A.n_max + 2 * A.k_max + (NT / 32) * A.k_max + 64 <= A.smem_floats;
+  if (!__syncthreads_and(valid)) {
+    if (threadIdx.x == 0) {
+      A.iters[p] = 0;
+      A.err[p] = CUDART_NAN_F;
+      A.status[p] = ST_INVALID;
+    }
+    return;
+  }
   const float* D = A.D + oD;
   float* xt = sm;
   float* G2 = xt + A.n_max;
