@@ -168,6 +168,39 @@ int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const
                      const float* x, const float* D, const float* y, double lam, double alpha,
                      const float* w, int sample_every, int iters, int* cta_threads_out);
 
+/* ---- learned warm start (an extension: the paper starts every solve from u1 = 1) -------------
+ * A 4-layer MLP maps a target y [n] to an initial state for Algorithm 1: features
+ * [n y / sum(y), log sum(y)] -> 3 x (Linear + GELU, width H) -> Linear -> [g/eps (n), log w (k)],
+ * with outputs normalised per coordinate by (mean, std).  Weights: FP32 masters updated by AdamW
+ * (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay) and BF16 copies for the forward pass; all
+ * accumulation in FP32.  Parameters are one flat FP32 vector: for each layer W [out][in] then
+ * b [out].  All pointers are device pointers; calls are asynchronous on the stream given at
+ * create time.  Errors: OTLM_EINVAL, OTLM_ENOMEM, OTLM_ECUDA. */
+typedef struct otlm_ws_ctx* otlm_ws;
+
+/* Create a network for grids of n bins and k atoms, hidden width H, at most batch_max rows per
+ * call; weights uniform(+-sqrt(6/(fan_in+fan_out))) from a counter-based hash of `seed`. */
+int otlm_ws_create(otlm_ws* out, int n, int k, int width, int batch_max, unsigned long long seed,
+                   void* cuda_stream);
+void otlm_ws_destroy(otlm_ws w);
+long long otlm_ws_num_params(otlm_ws w);
+/* Output normalisation: mean, std [n + k] (device). */
+int otlm_ws_set_normalization(otlm_ws w, const float* mean, const float* std);
+int otlm_ws_get_params(otlm_ws w, float* params_out);
+int otlm_ws_set_params(otlm_ws w, const float* params);
+/* Loss and its gradient for y [batch][n] and targets [batch][n + k] (g/eps, log w of solved
+ * problems; non-finite entries are masked): loss = mean over unmasked entries of
+ * (z - (t - mean)/std)^2.  grad_out [num_params] and loss_out [1] may be NULL. */
+int otlm_ws_gradients(otlm_ws w, int batch, const float* y, const float* target, float* grad_out,
+                      float* loss_out);
+/* One AdamW step on that loss (learning rate lr, weight decay wd); loss_out may be NULL. */
+int otlm_ws_train_step(otlm_ws w, int batch, const float* y, const float* target, double lr,
+                       double weight_decay, float* loss_out);
+/* Warm start for otlm_solve: g0 [batch][n] = eps * predicted g/eps, w0 [batch][k] = exp(predicted
+ * log w); a non-finite prediction falls back to the cold start (g0 = 0, w0 = cold_w). */
+int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const float* cold_w, float* g0,
+                    float* w0);
+
 /* Objective of a solver state (w, g), in FP64 (Eq. OTLM with the reading above).
  * From (w, g): a = K u1, s = D w, f = eps log(s/a); the plan Q = diag(e^{f/eps}) K diag(e^{g/eps})
  * satisfies Q 1 = D w, so primal_out = eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w) is the value

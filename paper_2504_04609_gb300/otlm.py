@@ -23,7 +23,9 @@ PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 
 EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_host", "otlm_objective",
            "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged",
-           "otlm_tune_ragged", "otlm_strerror")
+           "otlm_tune_ragged", "otlm_ws_create", "otlm_ws_destroy", "otlm_ws_num_params", "otlm_ws_set_normalization",
+           "otlm_ws_get_params", "otlm_ws_set_params", "otlm_ws_gradients", "otlm_ws_train_step", "otlm_ws_predict",
+           "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 
 
@@ -68,6 +70,24 @@ def lib() -> ctypes.CDLL:
         L.otlm_tune_ragged.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp, i, i,
                                        ctypes.POINTER(ctypes.c_int)]
         L.otlm_tune_ragged.restype = i
+        L.otlm_ws_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, ctypes.c_ulonglong, vp]
+        L.otlm_ws_create.restype = i
+        L.otlm_ws_destroy.argtypes = [vp]
+        L.otlm_ws_destroy.restype = None
+        L.otlm_ws_num_params.argtypes = [vp]
+        L.otlm_ws_num_params.restype = ctypes.c_longlong
+        for nm in ("otlm_ws_set_normalization",):
+            getattr(L, nm).argtypes = [vp, vp, vp]
+            getattr(L, nm).restype = i
+        for nm in ("otlm_ws_get_params", "otlm_ws_set_params"):
+            getattr(L, nm).argtypes = [vp, vp]
+            getattr(L, nm).restype = i
+        L.otlm_ws_gradients.argtypes = [vp, i, vp, vp, vp, vp]
+        L.otlm_ws_gradients.restype = i
+        L.otlm_ws_train_step.argtypes = [vp, i, vp, vp, d, d, vp]
+        L.otlm_ws_train_step.restype = i
+        L.otlm_ws_predict.argtypes = [vp, i, vp, d, vp, vp, vp]
+        L.otlm_ws_predict.restype = i
         L.otlm_strerror.argtypes = [i]
         L.otlm_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -243,3 +263,48 @@ def ragged_batch(problems, device="cuda"):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
     return RaggedBatch(len(problems), t(n), t(k), t(np.array([p["eps"] for p in problems], np.float32)),
                        t(off_n), t(off_D), t(off_k), t(cat("x")), t(cat("D")), t(cat("y")))
+
+
+class WarmStart:
+    """The learned warm start network (otlm_ws_*): device tensors in, device tensors out."""
+
+    def __init__(self, n, k, width=512, batch_max=512, seed=2504_04609, stream=None):
+        self.n, self.k, self.width, self.batch_max = n, k, width, batch_max
+        self._w = ctypes.c_void_p()
+        _check(lib().otlm_ws_create(ctypes.byref(self._w), n, k, width, batch_max, seed, stream), "otlm_ws_create")
+
+    @property
+    def num_params(self) -> int:
+        return lib().otlm_ws_num_params(self._w)
+
+    def close(self):
+        if self._w:
+            lib().otlm_ws_destroy(self._w)
+            self._w = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_normalization(self, mean, std):
+        _check(lib().otlm_ws_set_normalization(self._w, _ptr(mean), _ptr(std)), "otlm_ws_set_normalization")
+
+    def get_params(self, out):
+        _check(lib().otlm_ws_get_params(self._w, _ptr(out)), "otlm_ws_get_params")
+
+    def set_params(self, params):
+        _check(lib().otlm_ws_set_params(self._w, _ptr(params)), "otlm_ws_set_params")
+
+    def gradients(self, y, target, grad_out=None, loss_out=None):
+        _check(lib().otlm_ws_gradients(self._w, y.shape[0], _ptr(y), _ptr(target), _ptr(grad_out), _ptr(loss_out)),
+               "otlm_ws_gradients")
+
+    def train_step(self, y, target, lr, weight_decay=0.0, loss_out=None):
+        _check(lib().otlm_ws_train_step(self._w, y.shape[0], _ptr(y), _ptr(target), lr, weight_decay,
+                                        _ptr(loss_out)), "otlm_ws_train_step")
+
+    def predict(self, y, eps, cold_w, g0, w0):
+        _check(lib().otlm_ws_predict(self._w, y.shape[0], _ptr(y), eps, _ptr(cold_w), _ptr(g0), _ptr(w0)),
+               "otlm_ws_predict")
