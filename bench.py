@@ -479,6 +479,72 @@ def run_single_fp64(args, rank, local_rank):
             "config": {"workload": args.workload, "n": c["n"], "k": c["k"], "eps": c["eps"], "iters": c["iters"]}}
 
 
+def run_warmstart(args, rank, local_rank):
+    """Learned warm start at n = 2048, k = 64 (KL datafit, squared-l2 penalty, eps = 5e-3): train on
+    problems labelled by the solver, then solve held-out problems cold and warm, FP32 and tensor-core
+    paths, to the same 1e-5 tolerance.  Sizes: --ws-train (default 200,000), --ws-test (20,000)."""
+    import torch
+
+    from paper_2504_04609_gb300 import otlm as api
+    from paper_2504_04609_gb300 import warmstart as ws
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = dict(spectra.WORKLOADS[args.workload])
+    n, k = c["n"], c["k"]
+    t0 = time.perf_counter()
+    dtr = spectra.batch(c["id"], args.ws_train, n, k, c["nnz"], first=0)
+    dte = spectra.batch(c["id"], args.ws_test, n, k, c["nnz"], first=10_000_000)
+    gen_s = time.perf_counter() - t0
+    x, D = torch.tensor(dtr["x"], device=dev), torch.tensor(dtr["D"], device=dev)
+    ytr, yte = torch.tensor(dtr["y"], device=dev), torch.tensor(dte["y"], device=dev)
+    del dtr, dte
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    targets = ws.make_labels(x, D, ytr, c)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    mean, std = ws.normalization(targets)
+    net = api.WarmStart(n, k, 512, 512, seed=2504_04609)
+    net.set_normalization(mean, std)
+    t0 = time.perf_counter()
+    losses = ws.train(net, ytr, targets, epochs=args.ws_epochs, batch=512, lr=1e-3, weight_decay=1e-5, log_every=100)
+    train_s = time.perf_counter() - t0
+    out = {"metric": "OTLM problems solved/s to 1e-5 marginal tol, learned warm start vs cold start (n=2048)",
+           "unit": "problems/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 solve, bf16-weight MLP", "data": "synthetic (seeded Gaussian-peak spectra)",
+           "config": {"workload": args.workload, "n": n, "k": k, "eps": c["eps"], "datafit": c["datafit"],
+                      "penalty": c["penalty"], "alpha": c["alpha"], "tol": c["tol"], "train_problems": args.ws_train,
+                      "test_problems": args.ws_test, "mlp": "4 layers, width 512, GELU, BF16 weights, FP32 accumulate",
+                      "epochs": args.ws_epochs, "batch": 512},
+           "timings_s": {"generate_host": gen_s, "label_solves": label_s, "train": train_s},
+           "train_loss_first_last": [losses[0], losses[-1]], "forms": {}}
+    for prec in ("fp32", "bf16tc"):
+        ws.evaluate(net, x, D, yte[:min(512, args.ws_test)], c, precision=prec)  # warm-up of both arms
+        r = ws.evaluate(net, x, D, yte, c, precision=prec)
+        ok_c = r["cold_status"] == 0
+        ok_w = r["warm_status"] == 0
+        out["forms"][prec] = {
+            "cold": {"problems_per_s": args.ws_test / r["cold_s"], "iters_mean": float(r["cold_iters"].mean()),
+                     "iters_p50": float(np.percentile(r["cold_iters"], 50)),
+                     "iters_p99": float(np.percentile(r["cold_iters"], 99)), "converged": int(ok_c.sum())},
+            "warm": {"problems_per_s": args.ws_test / r["warm_s"], "iters_mean": float(r["warm_iters"].mean()),
+                     "iters_p50": float(np.percentile(r["warm_iters"], 50)),
+                     "iters_p99": float(np.percentile(r["warm_iters"], 99)), "converged": int(ok_w.sum()),
+                     "predict_s": r["predict_s"]},
+            "warm_vs_cold_rel_l1": {"w_median": float(np.median(r["w_rel_diff"])),
+                                    "t_median": float(np.median(r["t_rel_diff"])),
+                                    "t_p99": float(np.percentile(r["t_rel_diff"], 99))}}
+    base = out["forms"]["fp32"]["cold"]["problems_per_s"]
+    best = max(v["warm"]["problems_per_s"] for v in out["forms"].values())
+    out["value"] = out["forms"]["bf16tc"]["warm"]["problems_per_s"]
+    out["speedup_warm_bf16_vs_plain_fp32_cold"] = out["value"] / base
+    out["best_form_problems_per_s"] = best
+    net.close()
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -510,6 +576,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch4096_n4096_l2_l2sq")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ws-train", type=int, default=200_000, help="warm start: training problems")
+    ap.add_argument("--ws-test", type=int, default=20_000, help="warm start: held-out problems")
+    ap.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -524,6 +593,8 @@ def main():
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         if args.workload.startswith("ragged"):
             out = run_ragged(args, rank, world, local_rank)
+        elif args.workload.startswith("warmstart"):
+            out = run_warmstart(args, rank, local_rank)
         elif args.workload.startswith("single"):
             out = run_single_fp64(args, rank, local_rank)
         else:
