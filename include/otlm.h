@@ -73,9 +73,9 @@ typedef enum {
   OTLM_PREC_BF16_TC  = 2      /* kernel applies as tensor-core GEMMs K V^T: BF16 hi/lo operands
                                  (three products, ~16 mantissa bits), FP32 accumulation, a
                                  per-problem max shift; potentials and updates in FP32.  Element
-                                 type float.  A problem whose apply underflows (a row with all
-                                 significant terms below 2^-126 of the problem's largest) reports
-                                 OTLM_NONFINITE.  otlm_objective on such a handle runs FP32 applies. */
+                                 type float.  Rows whose sum underflows (all significant terms
+                                 below 2^-126 of the problem's largest) are recomputed exactly in
+                                 the log domain.  otlm_objective on such a handle runs FP32 applies. */
 } otlm_precision;
 
 typedef struct otlm_config {

@@ -96,4 +96,23 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return v;
 }
 
+// Maximum over a block of `nthreads` threads; `red` holds >= 32 elements of shared scratch.
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? red[threadIdx.x] : -CUDART_INF_F;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (threadIdx.x == 0) red[0] = v;
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
 }  // namespace otlm

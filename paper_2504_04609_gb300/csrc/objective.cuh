@@ -73,8 +73,6 @@ __device__ __forceinline__ double block_min(double v, double* red) {
   return v;
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) { return -block_min(-v, red); }
-
 // One CTA (256 threads) per problem.
 template <typename T>
 __global__ void __launch_bounds__(256) objective_reduce_kernel(ObjArgs<T> A) {

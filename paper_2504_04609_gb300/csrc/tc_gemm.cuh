@@ -117,6 +117,9 @@ struct GemmArgs {
   const int* n_cols;   // number of valid columns on the device; nullptr: N
   int M, N, Kd, ld_out;
   int* err;            // first error code of any CTA (0: none)
+  int2* fix_list;                // sums below FLT_MIN as (output row, row); nullptr: not recorded
+  unsigned long long* fix_cnt;   // entries this launch appended to fix_list
+  unsigned long long fix_cap;    // capacity of fix_list (M x N covers every element)
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -220,12 +223,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (n0 + c0 >= ncols) break;  // warp-uniform
         uint32_t v[16];
         tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+        unsigned low = 0;  // columns whose sum is below FLT_MIN (including an empty sum)
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int col = n0 + c0 + c;
-          if (col < ncols && row < g.M) {
-            const int o = g.col_map ? g.col_map[col] : col;
-            g.out[static_cast<size_t>(o) * g.ld_out + row] = __uint_as_float(v[c]);
+          const bool in = col < ncols && row < g.M;
+          const int o = (col < ncols) ? (g.col_map ? g.col_map[col] : col) : 0;
+          const float val = __uint_as_float(v[c]);
+          if (in) g.out[static_cast<size_t>(o) * g.ld_out + row] = val;
+          low |= (in && !(val >= 1.17549435e-38f)) ? (1u << c) : 0u;
+        }
+        if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
+          for (; low; low &= low - 1) {
+            const int col = n0 + c0 + __ffs(low) - 1;
+            const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
+            if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
           }
         }
       }

@@ -13,8 +13,10 @@
 //   dtr, wupd : MM step (Table 2) as a tiled D^T r contraction and the weight update
 //   dw, opnd  : source step S = D w (tiled), then the target operand U
 //   gemm      : target sums into ACC_tgt
-// A sum that underflows to 0 (possible only when a row's significant terms lie more than ~2^-126
-// below the problem's largest term) makes the problem report OTLM_NONFINITE.
+// A sum that underflows (a row whose significant terms all lie more than ~2^-126 below the
+// problem's largest term, e.g. far from the support under a KL or TV datafit) is listed by the GEMM
+// epilogue and recomputed exactly (two-pass log-sum-exp for that row) by tc_fixup_kernel, which
+// runs after each GEMM and spreads the listed rows over the whole GPU.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -33,8 +35,18 @@ struct TcWorkspace {
   float* Msrc[2];            // [batch] source shifts, ping-pong
   float* Mtgt;               // [batch] target shifts
   int* err;                  // GEMM error flag
+  int2* fix_list;            // [batch x n] underflowed sums (problem, row) listed by a GEMM
+  unsigned long long* fix_cnt;  // [2] list lengths: source GEMM, target GEMM
+  unsigned long long fix_cap;
   int ld;                    // row pitch of the BF16 operands (multiple of 64)
 };
+
+// A raw GEMM sum is a sum of positive terms, so it is >= 0.  A row the fix-up recomputed exactly
+// is stored as the NEGATIVE offset log2(sum) - M (below -126, as the row underflowed), so one
+// helper recovers log2 of the sum for every consumer: raw > 0, encoded < 0, 0 = empty sum.
+__device__ __forceinline__ float tc_log2_sum(float a, float m) {
+  return a > 0.f ? m + Prec<float>::log2(a) : (a < 0.f ? m + a : -CUDART_INF_F);
+}
 
 inline int tc_ld(int n) { return (n + 63) / 64 * 64; }
 
@@ -60,6 +72,9 @@ inline size_t carve_tc_workspace(void* base, int n_max, int batch_max, TcWorkspa
   w.Msrc[1] = (float*)take(4 * (size_t)batch_max);
   w.Mtgt = (float*)take(4 * (size_t)batch_max);
   w.err = (int*)take(64);
+  w.fix_cap = (unsigned long long)batch_max * n_max;
+  w.fix_list = (int2*)take(8 * (size_t)batch_max * n_max);
+  w.fix_cnt = (unsigned long long*)take(64);
   if (ws) *ws = w;
   return off;
 }
@@ -111,6 +126,52 @@ __device__ __forceinline__ float write_operand(const float* L, int n, int ld, in
   return m;
 }
 
+// Exact fix-up of the sums a GEMM listed as underflowed, one CTA of 256 threads per listed
+// (problem p, row i) so that a row costs a few memory round trips, not n / 32:
+//   L = log2 sum_j 2^(in_pj - (xt_i - xt_j)^2)     (two passes over j: max, then sum)
+// stored as the negative offset L - M_p (decoded by tc_log2_sum); an empty sum stays 0.  in = G2
+// and M = Msrc for the source sums, in = F2 and M = Mtgt for the target sums.  The source and
+// target GEMMs count into fix_cnt[0] and fix_cnt[1]; each fix-up reads its own count and clears the
+// other, which the next GEMM appends to.  With nothing listed every CTA leaves after one load.
+constexpr int TC_FIX_GRID = 4 * 152;
+
+__global__ void __launch_bounds__(256) tc_fixup_kernel(const int2* list, const unsigned long long* cnt,
+                                                       unsigned long long* cnt_next, unsigned long long cap, int n,
+                                                       const float* xt, const float* in, float* acc,
+                                                       const float* mshift) {
+  using P = Prec<float>;
+  __shared__ float red[32];
+  const unsigned long long c = *cnt < cap ? *cnt : cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cnt_next = 0;
+  for (unsigned long long e = blockIdx.x; e < c; e += gridDim.x) {
+    const int2 pi = list[e];
+    const float* inp = in + (size_t)pi.x * n;
+    const float xi = xt[pi.y];
+    float mx = -CUDART_INF_F;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const float d = xi - xt[j];
+      mx = fmaxf(mx, inp[j] - d * d);
+    }
+    mx = block_max(mx, red);
+    float sum = 0.f;
+    if (mx > -CUDART_INF_F) {
+#pragma unroll 4
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const float d = xi - xt[j];
+        sum += P::exp2((inp[j] - mx) - d * d);
+      }
+    }
+    sum = block_sum(sum, red);
+    if (threadIdx.x == 0) {
+      const float L = sum > 0.f ? mx + P::log2(sum) : -CUDART_INF_F;
+      // a representable sum is stored raw; an underflowing one as its negative log2 offset
+      const float off = L - mshift[pi.x];
+      acc[(size_t)pi.x * n + pi.y] = !(L > -CUDART_INF_F) ? 0.f : (off >= -126.f ? P::exp2(off) : off);
+    }
+  }
+}
+
 struct TcIterArgs {
   const int* active;
   const int* n_active;
@@ -145,8 +206,7 @@ __global__ void __launch_bounds__(256) tc_prep_src_kernel(TcIterArgs A) {
     const float* y = A.y + (size_t)p * n;
     const float mt = A.t.Mtgt[p];
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const float s = acc[j];
-      const float v = s > 0.f ? mt + P::log2(s) : P::ninf();
+      const float v = tc_log2_sum(acc[j], mt);
       const float yv = y[j];
       float gn;
       switch (A.datafit) {
@@ -178,11 +238,16 @@ __global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
   const float* acc = A.t.ACC_src[cur] + (size_t)p * n;
   const float* acc_old = A.t.ACC_src[cur ^ 1] + (size_t)p * n;
   const float* S = A.S + (size_t)p * n;
-  const float f = P::exp2(A.t.Msrc[cur][p] - A.t.Msrc[cur ^ 1][p]);
+  const float mc = A.t.Msrc[cur][p], mo = A.t.Msrc[cur ^ 1][p];
+  const float f = P::exp2(mc - mo);
   float part = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float s = S[i];
-    if (s > 0.f) part += s * fabsf(acc[i] / acc_old[i] * f - 1.f);
+    if (s > 0.f) {
+      const float an = acc[i], ao = acc_old[i];
+      const float ratio = (an > 0.f && ao > 0.f) ? an / ao * f : P::exp2(tc_log2_sum(an, mc) - tc_log2_sum(ao, mo));
+      part += s * fabsf(ratio - 1.f);
+    }
   }
   part = block_sum(part, red);
   if (threadIdx.x == 0) {
@@ -278,7 +343,7 @@ __global__ void __launch_bounds__(256) tc_dtr_kernel(TcIterArgs A, TcMMBuf M) {
       if (p >= 0 && i < i_end) {
         const size_t idx = (size_t)p * n + i;
         const float s = A.S[idx];
-        if (s > 0.f) r = (mcur[b] + P::log2(A.t.ACC_src[cur][idx])) - P::log2(s);
+        if (s > 0.f) r = tc_log2_sum(A.t.ACC_src[cur][idx], mcur[b]) - P::log2(s);
       }
       Rs[ii][b] = r;
     }
@@ -399,7 +464,7 @@ __global__ void __launch_bounds__(256) tc_dw_kernel(TcIterArgs A, TcMMBuf M) {
         const size_t idx = (size_t)p * n + i;
         const float s = acc[q][c] < P::tiny() ? 0.f : acc[q][c];
         A.S[idx] = s;
-        const float f2 = s > 0.f ? P::log2(s) - (mcur[b] + P::log2(A.t.ACC_src[cur][idx])) : P::ninf();
+        const float f2 = s > 0.f ? P::log2(s) - tc_log2_sum(A.t.ACC_src[cur][idx], mcur[b]) : P::ninf();
         A.F2[idx] = f2;
         fm = fmaxf(fm, f2);
         ms += s;
@@ -456,8 +521,8 @@ __global__ void tc_finalize_kernel(FinArgs<float> F, const float* ACC_tgt, const
     const int p = (int)(e / F.n);
     if (F.g_out) F.g_out[e] = F.G2[e] * F.gscale_inv;
     if (F.t_out) {
-      const float s = ACC_tgt[e];
-      F.t_out[e] = s > 0.f ? P::exp2(F.G2[e] + Mtgt[p] + P::log2(s)) : 0.f;
+      const float lb = tc_log2_sum(ACC_tgt[e], Mtgt[p]);
+      F.t_out[e] = lb > -CUDART_INF_F ? P::exp2(F.G2[e] + lb) : 0.f;
     }
   }
   for (size_t e = tid; e < (size_t)F.batch; e += stride) {
@@ -496,6 +561,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo);
   L.end();
   cudaError_t e = cudaMemsetAsync(tw.err, 0, sizeof(int), L.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tw.fix_cnt, 0, 2 * sizeof(unsigned long long), L.stream);
   if (e != cudaSuccess) return e;
 
   TcIterArgs ta{};
@@ -507,17 +573,23 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   ta.y = y; ta.D = D; ta.Dt = ws.Dt; ta.xcol = ws.xcol; ta.G2 = ws.G2; ta.S = ws.S; ta.F2 = ws.F2; ta.W = ws.W;
   ta.mass = ws.mass; ta.err = ws.err; ta.done = ws.done; ta.iters = ws.iters; ta.status = ws.status; ta.t = tw;
 
-  tc::GemmArgs gs{nullptr, ws.active, ws.n_active, n, batch, n, n, tw.err};
+  tc::GemmArgs gs{nullptr, ws.active, ws.n_active, n, batch, n, n, tw.err, tw.fix_list, nullptr,
+                  (unsigned long long)batch * n};
   for (int it = 0;; ++it) {
     ta.it = it;
     L.begin(KIND_MM);
     tc_prep_src_kernel<<<batch, 256, 0, L.stream>>>(ta);
     L.end();
     gs.out = tw.ACC_src[it & 1];
+    gs.fix_cnt = tw.fix_cnt;
     L.begin(KIND_APPLY);
     e = tc::launch_gemm3(tw.Khi, tw.Klo, tw.Vhi, tw.Vlo, n, batch, n, tw.ld, gs, L.stream);
     L.end();
     if (e != cudaSuccess) return e;
+    L.begin(KIND_OTHER);
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, gs.fix_cap, n, ws.xt,
+                                                    ws.G2, tw.ACC_src[it & 1], tw.Msrc[it & 1]);
+    L.end();
     if (it > 0) {
       L.begin(KIND_MM);
       tc_violation_kernel<<<batch, 256, 0, L.stream>>>(ta);
@@ -546,10 +618,15 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     tc_operand_kernel<<<batch, 256, 0, L.stream>>>(ta, mb);
     L.end();
     gs.out = tw.ACC_tgt;
+    gs.fix_cnt = tw.fix_cnt + 1;
     L.begin(KIND_APPLY);
     e = tc::launch_gemm3(tw.Khi, tw.Klo, tw.Vhi, tw.Vlo, n, batch, n, tw.ld, gs, L.stream);
     L.end();
     if (e != cudaSuccess) return e;
+    L.begin(KIND_OTHER);
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 1, tw.fix_cnt, gs.fix_cap, n, ws.xt,
+                                                    ws.F2, tw.ACC_tgt, tw.Mtgt);
+    L.end();
     if ((it + 1) % sp.poll_every == 0) {
       e = cudaMemcpyAsync(L.host_flag, ws.n_active, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);

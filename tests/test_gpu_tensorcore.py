@@ -85,3 +85,19 @@ def test_tensorcore_full_workload_sampled_against_oracle():
             o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], gi)
         assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
         assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
+
+
+def test_tensorcore_underflowing_rows_are_fixed_up_exactly():
+    """KL datafit at eps = 1e-3 with bins 60..459 of each target zeroed: under the KL datafit
+    u1 = 0 there, so rows inside see only terms 2^-230 .. 2^-1100 below the problem's largest one
+    (100 to 300 rows per problem, checked with the oracle's potentials) and their tensor-core sums
+    underflow; the fix-up recomputes them in the log domain.  Every problem must stay finite and
+    match the oracle trajectory."""
+    d = spectra.batch(33, 6, 512, 16, 3)
+    d["y"][:, 60:460] = 0.0
+    r = _solve(d, 1e-3, 1.0, 1e-3, "kl", "l2sq", 20)
+    assert np.all(r["status"] == api.MAX_ITER)
+    for p in range(6):
+        o = _oracle(d, p, 1e-3, 1.0, 1e-3, "kl", "l2sq", 20)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
