@@ -249,15 +249,14 @@ def run_ours(args, rank, world, local_rank):
     g_ms_step = g_ms / args.steps
     achieved_tf = flops_step / (g_ms_step / 1e3) / 1e12
     peak_tf = float(peaks.get("bf16_tflops_sustained", 1700.0))
-    roofline = {"bound": "tensor", "kernel": "gemm3_bf16_kernel (tcgen05 K V^T, BF16 hi/lo, FP32 accumulate)",
+    roofline = {"bound": "tensor", "kernel": "gemm3_kernel<KIND_BF16> (tcgen05 K V^T, BF16 hi/lo, FP32 accumulate)",
                 "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": None, "launch_ms_avg": g_ms / max(g_cnt, 1),
+                "traffic": 404.1e6, "launch_ms_avg": g_ms / max(g_cnt, 1),
                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained",
                 "issued_tensor_tflops": 3 * achieved_tf, "issued_frac": 3 * achieved_tf / peak_tf,
-                "traffic_note": "full-size launch not captured (multi-pass ncu at 1.5 GB); the 1024-problem "
-                                "profiling case reads 84 MB + writes 3 MB per launch = its algorithmic "
-                                "operand bytes (profiles/gemm3_bf16_n4096_b1024.md)"}
+                "traffic_note": "DRAM bytes per full-size launch from a one-pass ncu capture: "
+                                "profiles/gemm3_apply_n4096_b4096.md"}
 
     # plain FP32 path: the log-sum-exp apply against the exponent unit
     it_fp = fp["iters"].astype(np.float64)

@@ -55,8 +55,8 @@ size_t workspace_bytes(const otlm_config& c) {
     return otlm::carve_workspace<double>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
   size_t bytes = otlm::carve_workspace<float>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
   if (c.precision == OTLM_PREC_BF16_TC)
-    bytes += otlm::carve_tc_workspace(nullptr, c.n_max, c.batch_max, nullptr) +
-             otlm::carve_tc_mm(nullptr, c.n_max, c.batch_max, nullptr);
+    bytes += otlm::carve_tc_workspace(nullptr, c.n_max, c.k_max, c.batch_max, nullptr) +
+             otlm::carve_tc_mm(nullptr, c.k_max, c.batch_max, nullptr);
   return bytes;
 }
 
@@ -88,9 +88,10 @@ int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* D, 
   if (h->cfg.precision == OTLM_PREC_BF16_TC) {
     otlm::TcWorkspace tw;
     const size_t base = otlm::carve_workspace<float>(nullptr, h->cfg.n_max, h->cfg.k_max, h->cfg.batch_max, nullptr);
-    const size_t tcb = otlm::carve_tc_workspace(static_cast<char*>(h->ws) + base, h->cfg.n_max, h->cfg.batch_max, &tw);
+    const size_t tcb = otlm::carve_tc_workspace(static_cast<char*>(h->ws) + base, h->cfg.n_max, h->cfg.k_max,
+                                                h->cfg.batch_max, &tw);
     otlm::TcMMBuf mb;
-    otlm::carve_tc_mm(static_cast<char*>(h->ws) + base + tcb, h->cfg.n_max, h->cfg.batch_max, &mb);
+    otlm::carve_tc_mm(static_cast<char*>(h->ws) + base + tcb, h->cfg.k_max, h->cfg.batch_max, &mb);
     e = otlm::solve_device_tc(L, reinterpret_cast<const Workspace<float>&>(ws), tw, mb, sp, (const float*)x,
                               (const float*)D, (const float*)y, (float*)w, (float*)g, (float*)t_out, iters_out,
                               (float*)err_out, status_out);

@@ -1,16 +1,20 @@
-// tcgen05 (5th-generation tensor core) GEMM for the batched kernel apply, sm_100a/sm_103a.
+// tcgen05 (5th-generation tensor core) three-term GEMM, sm_100a/sm_103a.
 //
 //   out[map(c)][r] = sum_j ( Ahi[r][j] Bhi[c][j] + Ahi[r][j] Blo[c][j] + Alo[r][j] Bhi[c][j] )
 //
-// A = the Gibbs kernel K (rows r = grid bins), B = the scaled scalings V of the batch (rows
-// c = active problems), both BF16 and K-major (contiguous along j).  Each operand is carried as a
-// hi/lo pair of BF16 values (x = hi + lo); the three products recover ~16 mantissa bits per
-// element, enough for 1e-5 relative parity of the whole solve.  Accumulation is FP32 in tensor
-// memory (TMEM); the epilogue stores the raw FP32 sums problem-major.
+// Both operands are K-major (contiguous along j) and carried as hi/lo pairs (x = hi + lo), so the
+// three products recover most of the precision the single-pass type drops:
+//   KIND_BF16 (kind::f16, BF16 operands): ~16 mantissa bits; the kernel applies K V^T, where A = the
+//             Gibbs kernel K (rows r = grid bins) and B = the scaled scalings of the batch;
+//   KIND_TF32 (kind::tf32, FP32 containers rounded to TF32): ~21 bits; the dictionary contractions
+//             D w (A = D, B = the weights) and D^T r (A = D^T, B = the log ratios).
+// Accumulation is FP32 in tensor memory (TMEM); the epilogue stores FP32 sums, optionally through a
+// column map, with an optional split of the reduction over blockIdx.z (each split stores its own
+// partial sums, added later in a fixed order).
 //
-// One CTA computes a 128 x 256 output tile over the whole reduction:
+// One CTA computes a 128 x 256 output tile over its share of the reduction:
 //   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, 2-stage ring)
-//   warp 1 lane 0: MMA issuer  (tcgen05.mma kind::f16, 3 x 4 instructions per 64-wide k block)
+//   warp 1 lane 0: MMA issuer  (3 x 4 tcgen05.mma per 128-byte k block)
 //   warps 4..7   : epilogue    (tcgen05.ld 32x32b, one TMEM lane quarter per warp)
 // Every wait on an mbarrier is bounded (about 2 s of %globaltimer); on expiry the CTA records an
 // error in *err, stops issuing work, waits boundedly for its committed MMAs and frees its TMEM.
@@ -23,9 +27,10 @@
 namespace otlm {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
-constexpr int A_TILE = BM * BK * 2;                       // 16 KiB
-constexpr int B_TILE = BN * BK * 2;                       // 32 KiB
+enum { KIND_BF16 = 0, KIND_TF32 = 1 };
+constexpr int BM = 128, BN = 256, BK_BYTES = 128, STAGES = 2;
+constexpr int A_TILE = BM * BK_BYTES;                     // 16 KiB
+constexpr int B_TILE = BN * BK_BYTES;                     // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;      // 96 KiB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 256;
@@ -82,18 +87,34 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
   return d;
 }
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+// Elements per 128-byte k block and per MMA (each MMA consumes 32 bytes of k).
+template <int KIND> struct KindTraits;
+template <> struct KindTraits<KIND_BF16> { static constexpr int BK = 64, FMT = 1; };  // BF16
+template <> struct KindTraits<KIND_TF32> { static constexpr int BK = 32, FMT = 2; };  // TF32
+
+// Instruction descriptor: FP32 accumulator, A and B of the same format (BF16 = 1 under kind::f16,
+// TF32 = 2 under kind::tf32), both K-major, M x N.
+template <int KIND>
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(KindTraits<KIND>::FMT) << 7) |
+         (static_cast<uint32_t>(KindTraits<KIND>::FMT) << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t id,
+                                     uint32_t accumulate) {
+  if constexpr (KIND == KIND_BF16)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
+        : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -112,7 +133,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 struct GemmArgs {
-  float* out;          // out[map(c) * ld_out + r]
+  float* out;          // out[z * split_stride + map(c) * ld_out + r]
   const int* col_map;  // column (slot) -> output row; nullptr: identity
   const int* n_cols;   // number of valid columns on the device; nullptr: N
   int M, N, Kd, ld_out;
@@ -120,17 +141,30 @@ struct GemmArgs {
   int2* fix_list;                // sums below FLT_MIN as (output row, row); nullptr: not recorded
   unsigned long long* fix_cnt;   // entries this launch appended to fix_list
   unsigned long long fix_cap;    // capacity of fix_list (M x N covers every element)
+  int flush_tiny;      // store sums below FLT_MIN as 0
+  int splits;          // the reduction is split into `splits` ranges of k blocks (blockIdx.z); >= 1
+  size_t split_stride; // elements between the partial-sum planes of consecutive splits
+  int bulk;            // set by launch_gemm3: every output column segment is 16-byte aligned and a
+                       // multiple of 16 bytes long, so the tile leaves through shared memory as
+                       // one bulk copy per column
 };
 
+__device__ __forceinline__ void bulk_store(float* gdst, uint32_t ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+               : "memory");
+}
+
+template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm3_bf16_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
-                      const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
-                      GemmArgs g) {
+    gemm3_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                 const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, GemmArgs g) {
+  constexpr int BK = KindTraits<KIND>::BK;
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int ncols = g.n_cols ? *g.n_cols : g.N;
   if (n0 >= ncols) return;  // the whole CTA leaves before any barrier or TMEM use
+  float* const out = g.out + blockIdx.z * g.split_stride;
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);  // full[2], empty[2], acc
@@ -162,7 +196,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int nkb = (g.Kd + BK - 1) / BK;
+  // this split's k blocks (the host keeps splits <= blocks, so every split has at least one)
+  const int nkb_all = (g.Kd + BK - 1) / BK;
+  const int kb0 = static_cast<int>(static_cast<long long>(nkb_all) * blockIdx.z / g.splits);
+  const int nkb = static_cast<int>(static_cast<long long>(nkb_all) * (blockIdx.z + 1) / g.splits) - kb0;
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
@@ -177,10 +214,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (*(volatile int*)fail) break;
       mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-      tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kb * BK, m0);
-      tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kb * BK, m0);
-      tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kb * BK, n0);
-      tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kb * BK, n0);
+      const int kc = (kb0 + kb) * BK;
+      tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kc, m0);
+      tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kc, m0);
+      tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kc, n0);
+      tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kc, n0);
       last_round[s] = r;
     }
     // on an error path, let the copies already issued land before the CTA releases its memory
@@ -189,7 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (last_round[s] >= 0) (void)mbar_wait(full0 + 8 * s, last_round[s] & 1);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    constexpr uint32_t id = idesc<KIND>(BM, BN);
     int issued = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, r = kb / STAGES;
@@ -200,12 +238,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
+      for (int kk = 0; kk < BK_BYTES / 32; ++kk) {
         const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
         const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
-        umma_bf16(tmem, ah, bh, idesc, issued);
-        umma_bf16(tmem, ah, bl, idesc, 1);
-        umma_bf16(tmem, al, bh, idesc, 1);
+        umma<KIND>(tmem, ah, bh, id, issued);
+        umma<KIND>(tmem, ah, bl, id, 1);
+        umma<KIND>(tmem, al, bh, id, 1);
         issued = 1;
       }
       umma_commit(empty0 + 8 * s);
@@ -218,9 +256,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const int q = warp & 3;
     const int row = m0 + q * 32 + lane;
+    const int ncol_tile = min(BN, ncols - n0);
+    // With `bulk`, the operand ring (idle once every MMA has completed) holds the tile column by
+    // column: stage[c][r], 128 rows = 512 bytes per column, written conflict-free by a warp.
+    float* const stage = reinterpret_cast<float*>(base);
     if (ok && !*(volatile int*)fail) {
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        if (n0 + c0 >= ncols) break;  // warp-uniform
+      for (int c0 = 0; c0 < ncol_tile; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
         unsigned low = 0;  // columns whose sum is below FLT_MIN (including an empty sum)
@@ -228,10 +269,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int c = 0; c < 16; ++c) {
           const int col = n0 + c0 + c;
           const bool in = col < ncols && row < g.M;
-          const int o = (col < ncols) ? (g.col_map ? g.col_map[col] : col) : 0;
-          const float val = __uint_as_float(v[c]);
-          if (in) g.out[static_cast<size_t>(o) * g.ld_out + row] = val;
+          float val = __uint_as_float(v[c]);
           low |= (in && !(val >= 1.17549435e-38f)) ? (1u << c) : 0u;
+          if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
+          if (g.bulk) {
+            stage[(c0 + c) * BM + q * 32 + lane] = val;
+          } else if (in) {
+            const int o = g.col_map ? g.col_map[col] : col;
+            out[static_cast<size_t>(o) * g.ld_out + row] = val;
+          }
         }
         if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
           for (; low; low &= low - 1) {
@@ -240,6 +286,22 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
           }
         }
+      }
+    }
+    if (g.bulk) {
+      // the generic-proxy writes above become visible to the bulk-copy (async) proxy, then the
+      // four epilogue warps meet; each thread sends whole columns (rows m0 .. m0 + rows - 1)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (ok && !*(volatile int*)fail) {
+        const int rows = min(BM, g.M - m0);
+        const uint32_t bytes = static_cast<uint32_t>(rows) * 4u;
+        for (int c = threadIdx.x - 128; c < ncol_tile; c += 128) {
+          const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
+          bulk_store(out + static_cast<size_t>(o) * g.ld_out + m0, tiles + static_cast<uint32_t>(c) * (BM * 4), bytes);
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory may be released
       }
     }
   }
@@ -271,35 +333,63 @@ inline EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D BF16 tensor map over rows x cols (row pitch `ld` elements), box = box_rows x 64 columns.
+// 2-D tensor map over rows x cols (row pitch `ld` elements), box = box_rows x one 128-byte k block.
+// Elements past `cols` or `rows` read as zero.
+template <int KIND>
 inline bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
+  constexpr int esize = KIND == KIND_BF16 ? 2 : 4;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esize};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(KindTraits<KIND>::BK), static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  const CUtensorMapDataType dt = KIND == KIND_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Launch the three-term GEMM: A* [M][ld] (M x Kd used), B* [N][ld] (N x Kd used).
-inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, const void* B_hi, const void* B_lo, int M, int N,
-                                int Kd, int ld, const GemmArgs& args, cudaStream_t stream) {
+// Launch the three-term GEMM: A* [M][lda] (M x Kd used), B* [N][ldb] (N x Kd used); the row
+// pitches are multiples of 16 bytes and the bases 16-byte aligned (checked by the map encoder).
+template <int KIND>
+inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, int lda, const void* B_hi, const void* B_lo,
+                                int ldb, int M, int N, int Kd, const GemmArgs& args, cudaStream_t stream) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm3_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(gemm3_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  const int nkb = (Kd + KindTraits<KIND>::BK - 1) / KindTraits<KIND>::BK;
+  if (args.splits < 1 || args.splits > nkb) return cudaErrorInvalidValue;
+  GemmArgs a = args;
+  // column segments out + o * ld_out + m0 of M - m0 (<= 128) floats: 16-byte aligned and sized
+  a.bulk = (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 && M % 4 == 0 &&
+           (a.splits == 1 || a.split_stride % 4 == 0);
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-  if (!make_map(&ta_hi, A_hi, M, Kd, ld, BM) || !make_map(&ta_lo, A_lo, M, Kd, ld, BM) ||
-      !make_map(&tb_hi, B_hi, N, Kd, ld, BN) || !make_map(&tb_lo, B_lo, N, Kd, ld, BN))
+  if (!make_map<KIND>(&ta_hi, A_hi, M, Kd, lda, BM) || !make_map<KIND>(&ta_lo, A_lo, M, Kd, lda, BM) ||
+      !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, BN) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, BN))
     return cudaErrorInvalidValue;
-  const dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  gemm3_bf16_kernel<<<grid, THREADS, SMEM_BYTES, stream>>>(ta_hi, ta_lo, tb_hi, tb_lo, args);
+  const dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, args.splits);
+  gemm3_kernel<KIND><<<grid, THREADS, SMEM_BYTES, stream>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
   return cudaGetLastError();
+}
+
+// Splits of a reduction of `nkb` k blocks over `tiles` output tiles that minimise
+// (waves of CTAs on 152 SMs) x (k blocks per split), at most 16.
+inline int choose_splits(int tiles, int nkb) {
+  int best = 1;
+  long long best_cost = -1;
+  for (int s = 1; s <= 16 && s <= nkb; ++s) {
+    const long long waves = (static_cast<long long>(tiles) * s + 151) / 152;
+    const long long cost = waves * ((nkb + s - 1) / s);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = s;
+    }
+  }
+  return best;
 }
 
 }  // namespace tc

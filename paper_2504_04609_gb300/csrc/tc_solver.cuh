@@ -1,22 +1,29 @@
-// Batched scaling iteration with the two kernel applies on the tensor cores (BF16 hi/lo operands,
-// FP32 accumulation), for a batch sharing one grid and one dictionary.
+// Batched scaling iteration with the two kernel applies and both dictionary contractions on the
+// tensor cores, for a batch sharing one grid and one dictionary.
 //
 // Linear domain with a per-problem shift: the source apply is
 //   a_pi = sum_j K_ij u1_pj = 2^{M_p} sum_j K_ij V_pj,   V_pj = 2^{G2_pj - M_p},  M_p = max_j G2_pj,
-// so every V lies in (0, 1] and the GEMM K V^T (tc_gemm.cuh) returns the raw sums; log2 a_pi =
-// M_p + log2(sum).  The target apply is the same with U_pi = 2^{F2_pi - M'_p}.  K is symmetric for
-// the squared distance on a grid, so one matrix serves both applies.  Per iteration:
+// so every V lies in (0, 1] and the GEMM K V^T (tc_gemm.cuh, BF16 hi/lo) returns the raw sums;
+// log2 a_pi = M_p + log2(sum).  The target apply is the same with U_pi = 2^{F2_pi - M'_p}.  K is
+// symmetric for the squared distance on a grid, so one matrix serves both applies.  The MM step
+// (Table 2) and the source step s = D w are GEMMs with the shared dictionary (TF32 hi/lo, ~21 bits:
+// w and s must stay well inside the 1e-5 stopping tolerance).  Per iteration:
 //   prep_src  : datafit step from the previous target sums (Table 1), then the source operand V
-//   gemm      : source sums into ACC_src[it & 1]
-//   violation : source-marginal violation from the ratio of raw sums, stopping decision
+//   gemm      : source sums into ACC_src[it & 1] (BF16)
+//   violation : source-marginal violation from the ratio of raw sums, stopping decision (it > 0),
+//               and the MM log ratios r_i = log2(a_i / s_i) as a TF32 hi/lo operand
+//   dtr gemm  : NU = D^T r per problem (TF32, reduction over bins split across CTAs)
+//   wupd      : the weight update of Table 2, skipping problems that have just stopped
+//   dw gemm   : s = D w per problem (TF32)
 //   compact   : drop finished problems
-//   dtr, wupd : MM step (Table 2) as a tiled D^T r contraction and the weight update
-//   dw, opnd  : source step S = D w (tiled), then the target operand U
-//   gemm      : target sums into ACC_tgt
+//   operand   : F2 = log2 s - log2 a, the target shift and mass, then the target operand U
+//   gemm      : target sums into ACC_tgt (BF16)
+// dtr, wupd and dw run over the slots as they were before compaction, so the operands that the
+// violation and wupd kernels write row by slot need no re-gathering.
 // A sum that underflows (a row whose significant terms all lie more than ~2^-126 below the
 // problem's largest term, e.g. far from the support under a KL or TV datafit) is listed by the GEMM
 // epilogue and recomputed exactly (two-pass log-sum-exp for that row) by tc_fixup_kernel, which
-// runs after each GEMM and spreads the listed rows over the whole GPU.
+// runs after each apply and spreads the listed rows over the whole GPU.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -38,7 +45,12 @@ struct TcWorkspace {
   int2* fix_list;            // [batch x n] underflowed sums (problem, row) listed by a GEMM
   unsigned long long* fix_cnt;  // [2] list lengths: source GEMM, target GEMM
   unsigned long long fix_cap;
-  int ld;                    // row pitch of the BF16 operands (multiple of 64)
+  float *Dhi, *Dlo;          // [n][kp] dictionary as TF32 hi/lo (A operand of s = D w)
+  float *Dthi, *Dtlo;        // [k][ld] transposed dictionary as TF32 hi/lo (A operand of D^T r)
+  float *Whi, *Wlo;          // [batch][kp] weights by slot (B operand of s = D w)
+  float *Rhi, *Rlo;          // [batch][ld] log ratios by slot (B operand of D^T r)
+  int ld;                    // row pitch of the [.][n] operands (multiple of 64 elements)
+  int kp;                    // row pitch of the [.][k] operands (k_max rounded up to 4)
 };
 
 // A raw GEMM sum is a sum of positive terms, so it is >= 0.  A row the fix-up recomputed exactly
@@ -50,8 +62,8 @@ __device__ __forceinline__ float tc_log2_sum(float a, float m) {
 
 inline int tc_ld(int n) { return (n + 63) / 64 * 64; }
 
-inline size_t carve_tc_workspace(void* base, int n_max, int batch_max, TcWorkspace* ws) {
-  const int ld = tc_ld(n_max);
+inline size_t carve_tc_workspace(void* base, int n_max, int k_max, int batch_max, TcWorkspace* ws) {
+  const int ld = tc_ld(n_max), kp = (k_max + 3) / 4 * 4;
   size_t off = 0;
   char* b = static_cast<char*>(base);
   auto take = [&](size_t bytes) -> void* {
@@ -75,8 +87,46 @@ inline size_t carve_tc_workspace(void* base, int n_max, int batch_max, TcWorkspa
   w.fix_cap = (unsigned long long)batch_max * n_max;
   w.fix_list = (int2*)take(8 * (size_t)batch_max * n_max);
   w.fix_cnt = (unsigned long long*)take(64);
+  w.kp = kp;
+  w.Dhi = (float*)take(4 * (size_t)n_max * kp);
+  w.Dlo = (float*)take(4 * (size_t)n_max * kp);
+  w.Dthi = (float*)take(4 * (size_t)k_max * ld);
+  w.Dtlo = (float*)take(4 * (size_t)k_max * ld);
+  w.Whi = (float*)take(4 * (size_t)batch_max * kp);
+  w.Wlo = (float*)take(4 * (size_t)batch_max * kp);
+  w.Rhi = (float*)take(4 * (size_t)batch_max * ld);
+  w.Rlo = (float*)take(4 * (size_t)batch_max * ld);
   if (ws) *ws = w;
   return off;
+}
+
+// x = hi + lo with hi and lo rounded to TF32 (10 explicit mantissa bits each, round to nearest
+// with ties away, the rounding cvt.rna.tf32.f32 provides); hi + lo carries ~21 bits of x.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void tf32_split(float x, float* hi, float* lo) {
+  const float h = tf32_rna(x);
+  *hi = h;
+  *lo = tf32_rna(x - h);
+}
+
+// The dictionary D [n][k] as TF32 hi/lo, row-major [n][kp] and transposed [k][ld] (padding columns
+// are never read: the tensor maps stop at k and n).
+__global__ void tc_dsplit_kernel(const float* D, int n, int k, int kp, int ld, float* Dhi, float* Dlo, float* Dthi,
+                                 float* Dtlo) {
+  const size_t nk = (size_t)n * k;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e - (size_t)i * k);
+    float hi, lo;
+    tf32_split(D[e], &hi, &lo);
+    Dhi[(size_t)i * kp + j] = hi;
+    Dlo[(size_t)i * kp + j] = lo;
+    Dthi[(size_t)j * ld + i] = hi;
+    Dtlo[(size_t)j * ld + i] = lo;
+  }
 }
 
 // K = 2^{-(xt_i - xt_j)^2} as a BF16 hi/lo pair, [n][ld] (columns >= n left untouched: the
@@ -93,29 +143,12 @@ __global__ void kbuild_kernel(const float* xt, int n, int ld, __nv_bfloat16* Khi
   }
 }
 
-// max over a block of 256 threads
-__device__ __forceinline__ float block_max_f(float v, float* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : -CUDART_INF_F;
-  if (warp == 0)
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (threadIdx.x == 0) red[0] = v;
-  __syncthreads();
-  v = red[0];
-  __syncthreads();
-  return v;
-}
-
 // Write row `slot` of the operand: 2^{L_j - M} as BF16 hi + lo, where M = max_j L_j.  Returns M.
 __device__ __forceinline__ float write_operand(const float* L, int n, int ld, int slot, __nv_bfloat16* Vhi,
                                                __nv_bfloat16* Vlo, float* red) {
   float m = -CUDART_INF_F;
   for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, L[j]);
-  m = block_max_f(m, red);
+  m = block_max(m, red);
   if (!(m > -CUDART_INF_F)) m = 0.f;  // every term vanishes
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const float v = Prec<float>::exp2(L[j] - m);
@@ -226,9 +259,11 @@ __global__ void __launch_bounds__(256) tc_prep_src_kernel(TcIterArgs A) {
   if (threadIdx.x == 0) A.t.Msrc[A.it & 1][p] = m;
 }
 
-// Violation of the previous iteration's plan and the stopping decision (one CTA per active slot):
-// e = sum_i S_i |a_new_i / a_old_i - 1| / sum_i S_i from the raw sums.  The shift difference of
-// two nearby FP32 numbers is exact, so the ratio keeps FP32 relative precision.
+// Violation of the previous iteration's plan and the stopping decision (it > 0; one CTA per active
+// slot): e = sum_i S_i |a_new_i / a_old_i - 1| / sum_i S_i from the raw sums.  The shift difference
+// of two nearby FP32 numbers is exact, so the ratio keeps FP32 relative precision.  Every iteration
+// also writes the MM log ratios r_i = log2(a_i / s_i) (0 where s_i = 0) as the TF32 hi/lo row
+// `slot` of the D^T r operand.
 __global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
   using P = Prec<float>;
   __shared__ float red[32];
@@ -238,17 +273,26 @@ __global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
   const float* acc = A.t.ACC_src[cur] + (size_t)p * n;
   const float* acc_old = A.t.ACC_src[cur ^ 1] + (size_t)p * n;
   const float* S = A.S + (size_t)p * n;
+  float* rhi = A.t.Rhi + (size_t)slot * A.t.ld;
+  float* rlo = A.t.Rlo + (size_t)slot * A.t.ld;
   const float mc = A.t.Msrc[cur][p], mo = A.t.Msrc[cur ^ 1][p];
   const float f = P::exp2(mc - mo);
+  const bool check = A.it > 0;
   float part = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float s = S[i];
+    const float s = S[i], an = acc[i];
+    float r = 0.f;
     if (s > 0.f) {
-      const float an = acc[i], ao = acc_old[i];
-      const float ratio = (an > 0.f && ao > 0.f) ? an / ao * f : P::exp2(tc_log2_sum(an, mc) - tc_log2_sum(ao, mo));
-      part += s * fabsf(ratio - 1.f);
+      r = tc_log2_sum(an, mc) - P::log2(s);
+      if (check) {
+        const float ao = acc_old[i];
+        const float ratio = (an > 0.f && ao > 0.f) ? an / ao * f : P::exp2(tc_log2_sum(an, mc) - tc_log2_sum(ao, mo));
+        part += s * fabsf(ratio - 1.f);
+      }
     }
+    tf32_split(r, rhi + i, rlo + i);
   }
+  if (!check) return;
   part = block_sum(part, red);
   if (threadIdx.x == 0) {
     const float e = part / A.mass[p];
@@ -265,28 +309,21 @@ __global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
   }
 }
 
-// ---- register-tiled contractions with the dictionary (the MM step and the source step) ----------
+// ---- the MM step and the source step around the two TF32 dictionary GEMMs ----------------------
 //
-// dtr : NU[s][slot][j] = sum_{i in split s} D_ij r_i,  r_i = LA2_i - log2 S_i (rows with S_i = 0
-//       dropped).  CTA = 32 active slots x KP columns, 256 threads, register tile BPT problems x 4
-//       columns; rows staged 32 at a time; the row range is split DTR_SPLIT ways (deterministic
-//       partial sums, added in a fixed order by wupd).
-// wupd: w update of Table 2 from nu = log w + (ln2 / x_j) sum_s NU[s].
-// dw  : S = D w for 64 slots x 128 rows per CTA (register tile 8 problems x 4 rows, k staged 32 at
-//       a time), epilogue S, F2 = log2 S - LA2 and per-tile max(F2) and sum(S) partials.
-// opnd: per slot, reduce the partials (fixed order) and write the target operand row.
-constexpr int DTR_SPLIT = 4;
-constexpr int DW_ROWS = 128;
+// dtr gemm : NU[z][slot][j] = sum_{i in split z} D_ij r_slot,i   (A = D^T [k][ld], B = R [slot][ld])
+// wupd     : w update of Table 2 from nu = log w + (ln2 / x_j) sum_z NU[z] (splits added in order)
+// dw gemm  : S[p][i] = sum_j D_ij w_pj                           (A = D [n][kp], B = W [slot][kp])
+// operand  : per slot, F2, the shift max(F2) and mass sum(S), then the target operand row.
+constexpr int TC_MAX_SPLITS = 16;
 
 struct TcMMBuf {
-  float* NU;     // [DTR_SPLIT][batch][256]
-  float* PMAX;   // [batch][ptiles]
-  float* PMASS;  // [batch][ptiles]
-  int ptiles;    // ceil(n_max / DW_ROWS)
-  int stride;    // rows per split of NU (batch_max)
+  float* NU;      // [TC_MAX_SPLITS][batch_max][ldnu] partial sums of D^T r
+  int ldnu;       // k_max rounded up to 4
+  size_t plane;   // batch_max * ldnu: elements per split
 };
 
-inline size_t carve_tc_mm(void* base, int n_max, int batch_max, TcMMBuf* mb) {
+inline size_t carve_tc_mm(void* base, int k_max, int batch_max, TcMMBuf* mb) {
   size_t off = 0;
   char* b = static_cast<char*>(base);
   auto take = [&](size_t bytes) -> void* {
@@ -295,213 +332,65 @@ inline size_t carve_tc_mm(void* base, int n_max, int batch_max, TcMMBuf* mb) {
     return p;
   };
   TcMMBuf m;
-  m.ptiles = (n_max + DW_ROWS - 1) / DW_ROWS;
-  m.stride = batch_max;
-  m.NU = (float*)take(4 * (size_t)DTR_SPLIT * batch_max * 256);
-  m.PMAX = (float*)take(4 * (size_t)batch_max * m.ptiles);
-  m.PMASS = (float*)take(4 * (size_t)batch_max * m.ptiles);
+  m.ldnu = (k_max + 3) / 4 * 4;
+  m.plane = (size_t)batch_max * k_max;
+  m.NU = (float*)take(4 * (size_t)TC_MAX_SPLITS * m.plane);
   if (mb) *mb = m;
   return off;
 }
 
-template <int KP>
-__global__ void __launch_bounds__(256) tc_dtr_kernel(TcIterArgs A, TcMMBuf M) {
-  using P = Prec<float>;
-  constexpr int TB = 32, CH = 32, NT = 256;
-  constexpr int TJ = KP / 4, TBG = NT / TJ, BPT = TB / TBG;
-  static_assert(TJ * TBG == NT && TBG * BPT == TB, "tile");
-  __shared__ __align__(16) float Ds[CH][KP];
-  __shared__ __align__(16) float Rs[CH][TB];
-  __shared__ int prob[TB];
-  __shared__ float mcur[TB];
-  const int na = *A.n_active;
-  const int slot0 = blockIdx.x * TB;
-  if (slot0 >= na) return;
-  const int n = A.n, k = A.k, cur = A.it & 1, tid = threadIdx.x;
-  const int split = blockIdx.y;
-  const int i_beg = (int)((long long)n * split / DTR_SPLIT), i_end = (int)((long long)n * (split + 1) / DTR_SPLIT);
-  if (tid < TB) {
-    const int p = slot0 + tid < na ? A.active[slot0 + tid] : -1;
-    prob[tid] = p;
-    mcur[tid] = p >= 0 ? A.t.Msrc[cur][p] : 0.f;
-  }
-  const int tj = tid % TJ, tb = tid / TJ;
-  float acc[BPT][4];
-#pragma unroll
-  for (int q = 0; q < BPT; ++q)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
-  for (int i0 = i_beg; i0 < i_end; i0 += CH) {
-    __syncthreads();
-    for (int e = tid; e < CH * KP; e += NT) {
-      const int ii = e / KP, jj = e - ii * KP, i = i0 + ii;
-      Ds[ii][jj] = (i < i_end && jj < k) ? A.D[(size_t)i * k + jj] : 0.f;
-    }
-    for (int e = tid; e < CH * TB; e += NT) {
-      const int b = e / CH, ii = e - b * CH, i = i0 + ii, p = prob[b];
-      float r = 0.f;
-      if (p >= 0 && i < i_end) {
-        const size_t idx = (size_t)p * n + i;
-        const float s = A.S[idx];
-        if (s > 0.f) r = tc_log2_sum(A.t.ACC_src[cur][idx], mcur[b]) - P::log2(s);
-      }
-      Rs[ii][b] = r;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int ii = 0; ii < CH; ++ii) {
-      const float4 d = *reinterpret_cast<const float4*>(&Ds[ii][tj * 4]);
-      float rv[BPT];
-      if constexpr (BPT >= 4) {
-#pragma unroll
-        for (int q = 0; q < BPT; q += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(&Rs[ii][tb * BPT + q]);
-          rv[q] = v.x; rv[q + 1] = v.y; rv[q + 2] = v.z; rv[q + 3] = v.w;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < BPT; ++q) rv[q] = Rs[ii][tb * BPT + q];
-      }
-#pragma unroll
-      for (int q = 0; q < BPT; ++q) {
-        acc[q][0] = fmaf(d.x, rv[q], acc[q][0]);
-        acc[q][1] = fmaf(d.y, rv[q], acc[q][1]);
-        acc[q][2] = fmaf(d.z, rv[q], acc[q][2]);
-        acc[q][3] = fmaf(d.w, rv[q], acc[q][3]);
-      }
-    }
-  }
-  const int batch_stride = M.stride;
-#pragma unroll
-  for (int q = 0; q < BPT; ++q) {
-    const int slot = slot0 + tb * BPT + q;
-    if (slot >= na) continue;
-    float4* dst = reinterpret_cast<float4*>(M.NU + ((size_t)split * batch_stride + slot) * 256 + tj * 4);
-    *dst = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
-  }
-}
-
-__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M) {
+// One thread per (slot, j) of the slots before compaction.  A problem that has just stopped keeps
+// its weights; every slot writes its weight row as the TF32 hi/lo B operand of s = D w.
+__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, int splits) {
   using P = Prec<float>;
   const int na = *A.n_active, k = A.k;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int slot = e / k, j = e - slot * k;
   if (slot >= na) return;
   const int p = A.active[slot];
-  float sum = 0.f;
-#pragma unroll
-  for (int s = 0; s < DTR_SPLIT; ++s) sum += M.NU[((size_t)s * M.stride + slot) * 256 + j];
-  const float xj = A.xcol[j];
-  const float nu = P::log(A.W[(size_t)p * k + j]) + sum * float(kLn2) / xj;
-  float wn;
-  if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
-  else if (A.penalty == PEN_L2SQ) {
-    const float c = A.alpha / (A.eps * xj);
-    wn = wright_omega<float>(P::log(c) + nu) / c;
-  } else wn = P::exp(nu);
-  A.W[(size_t)p * k + j] = wn;
+  float wn = A.W[(size_t)p * k + j];
+  if (!A.done[p]) {
+    float sum = 0.f;
+    for (int z = 0; z < splits; ++z) sum += M.NU[z * M.plane + (size_t)slot * M.ldnu + j];
+    const float xj = A.xcol[j];
+    const float nu = P::log(wn) + sum * float(kLn2) / xj;
+    if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
+    else if (A.penalty == PEN_L2SQ) {
+      const float c = A.alpha / (A.eps * xj);
+      wn = wright_omega<float>(P::log(c) + nu) / c;
+    } else wn = P::exp(nu);
+    A.W[(size_t)p * k + j] = wn;
+  }
+  tf32_split(wn, A.t.Whi + (size_t)slot * A.t.kp + j, A.t.Wlo + (size_t)slot * A.t.kp + j);
 }
 
-__global__ void __launch_bounds__(256) tc_dw_kernel(TcIterArgs A, TcMMBuf M) {
+// One CTA per active slot (after compaction): F2_i = log2 S_i - log2 a_i (-inf where S_i = 0), the
+// target shift M' = max_i F2_i, the mass sum_i S_i, then U_i = 2^{F2_i - M'} as BF16 hi/lo.
+__global__ void __launch_bounds__(256) tc_operand_kernel(TcIterArgs A) {
   using P = Prec<float>;
-  constexpr int TB = 64, TR = DW_ROWS, KC = 32, NT = 256;
-  __shared__ __align__(16) float Dts[KC][TR];  // Dt chunk [j][i]
-  __shared__ __align__(16) float Ws[KC][TB];   // w chunk [j][b]
-  __shared__ int prob[TB];
-  __shared__ float mcur[TB];
-  const int na = *A.n_active;
-  const int slot0 = blockIdx.y * TB;
-  if (slot0 >= na) return;
-  const int n = A.n, k = A.k, cur = A.it & 1, tid = threadIdx.x, lane = tid & 31;
-  const int r0 = blockIdx.x * TR;
-  if (tid < TB) {
-    const int p = slot0 + tid < na ? A.active[slot0 + tid] : -1;
-    prob[tid] = p;
-    mcur[tid] = p >= 0 ? A.t.Msrc[cur][p] : 0.f;
-  }
-  const int ti = tid % 32, tb = tid / 32;  // rows r0 + 4 ti .. +3, problems 8 tb .. +7
-  float acc[8][4];
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
-  for (int j0 = 0; j0 < k; j0 += KC) {
-    __syncthreads();
-    for (int e = tid; e < KC * TR; e += NT) {
-      const int jj = e / TR, ii = e - jj * TR, j = j0 + jj, i = r0 + ii;
-      Dts[jj][ii] = (j < k && i < n) ? A.Dt[(size_t)j * n + i] : 0.f;
-    }
-    for (int e = tid; e < KC * TB; e += NT) {
-      const int b = e / KC, jj = e - b * KC, j = j0 + jj, p = prob[b];
-      Ws[jj][b] = (p >= 0 && j < k) ? A.W[(size_t)p * k + j] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int jj = 0; jj < KC; ++jj) {
-      const float4 d = *reinterpret_cast<const float4*>(&Dts[jj][ti * 4]);
-      const float4 wa = *reinterpret_cast<const float4*>(&Ws[jj][tb * 8]);
-      const float4 wb = *reinterpret_cast<const float4*>(&Ws[jj][tb * 8 + 4]);
-      const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        acc[q][0] = fmaf(d.x, wv[q], acc[q][0]);
-        acc[q][1] = fmaf(d.y, wv[q], acc[q][1]);
-        acc[q][2] = fmaf(d.z, wv[q], acc[q][2]);
-        acc[q][3] = fmaf(d.w, wv[q], acc[q][3]);
-      }
-    }
-  }
-  // epilogue: S (subnormal mass taken as 0), F2, per-tile max(F2) and sum(S)
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int b = tb * 8 + q, p = prob[b];
-    float fm = -CUDART_INF_F, ms = 0.f;
-    if (p >= 0) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = r0 + ti * 4 + c;
-        if (i >= n) continue;
-        const size_t idx = (size_t)p * n + i;
-        const float s = acc[q][c] < P::tiny() ? 0.f : acc[q][c];
-        A.S[idx] = s;
-        const float f2 = s > 0.f ? P::log2(s) - tc_log2_sum(A.t.ACC_src[cur][idx], mcur[b]) : P::ninf();
-        A.F2[idx] = f2;
-        fm = fmaxf(fm, f2);
-        ms += s;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
-      ms += __shfl_xor_sync(0xffffffffu, ms, o);
-    }
-    if (lane == 0 && p >= 0) {
-      M.PMAX[(size_t)p * M.ptiles + blockIdx.x] = fm;
-      M.PMASS[(size_t)p * M.ptiles + blockIdx.x] = ms;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256) tc_operand_kernel(TcIterArgs A, TcMMBuf M) {
-  using P = Prec<float>;
-  __shared__ float mshift;
+  __shared__ float red[32];
   const int slot = blockIdx.x;
   if (slot >= *A.n_active) return;
-  const int p = A.active[slot], n = A.n;
-  const int tiles = (n + DW_ROWS - 1) / DW_ROWS;
+  const int p = A.active[slot], n = A.n, cur = A.it & 1;
+  const float* S = A.S + (size_t)p * n;
+  const float* acc = A.t.ACC_src[cur] + (size_t)p * n;
+  float* F2 = A.F2 + (size_t)p * n;
+  const float mc = A.t.Msrc[cur][p];
+  float fm = -CUDART_INF_F, ms = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float s = S[i];
+    const float f2 = s > 0.f ? P::log2(s) - tc_log2_sum(acc[i], mc) : P::ninf();
+    F2[i] = f2;
+    fm = fmaxf(fm, f2);
+    ms += s;
+  }
+  fm = block_max(fm, red);
+  ms = block_sum(ms, red);
+  const float m = fm > -CUDART_INF_F ? fm : 0.f;
   if (threadIdx.x == 0) {
-    float m = -CUDART_INF_F, ms = 0.f;
-    for (int t = 0; t < tiles; ++t) {
-      m = fmaxf(m, M.PMAX[(size_t)p * M.ptiles + t]);
-      ms += M.PMASS[(size_t)p * M.ptiles + t];
-    }
-    if (!(m > -CUDART_INF_F)) m = 0.f;
-    mshift = m;
     A.mass[p] = ms;
     A.t.Mtgt[p] = m;
   }
-  __syncthreads();
-  const float m = mshift;
-  const float* F2 = A.F2 + (size_t)p * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float v = P::exp2(F2[i] - m);
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -532,12 +421,12 @@ __global__ void tc_finalize_kernel(FinArgs<float> F, const float* ACC_tgt, const
   }
 }
 
-// Run Algorithm 1 with tensor-core applies (float buffers; x, D, y, w, g as in solve_device).
-// Returns cudaErrorLaunchTimeout when a GEMM reported an expired wait.
+// Run Algorithm 1 with tensor-core applies and dictionary contractions (float buffers; x, D, y, w,
+// g as in solve_device).  Returns cudaErrorLaunchTimeout when a GEMM reported an expired wait.
 inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, const TcWorkspace& tw,
-                                   const TcMMBuf& mb,
-                                   const SolveParams& sp, const float* x, const float* D, const float* y, float* w,
-                                   float* g, float* t_out, int* iters_out, float* err_out, int* status_out) {
+                                   const TcMMBuf& mb, const SolveParams& sp, const float* x, const float* D,
+                                   const float* y, float* w, float* g, float* t_out, int* iters_out, float* err_out,
+                                   int* status_out) {
   const int batch = sp.batch, n = sp.n, k = sp.k;
   const double eps_ln2 = sp.eps * kLn2;
   PrepArgs<float> pa;
@@ -560,6 +449,9 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   L.begin(KIND_OTHER);
   kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo);
   L.end();
+  L.begin(KIND_OTHER);
+  tc_dsplit_kernel<<<1184, 256, 0, L.stream>>>(D, n, k, tw.kp, tw.ld, tw.Dhi, tw.Dlo, tw.Dthi, tw.Dtlo);
+  L.end();
   cudaError_t e = cudaMemsetAsync(tw.err, 0, sizeof(int), L.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(tw.fix_cnt, 0, 2 * sizeof(unsigned long long), L.stream);
   if (e != cudaSuccess) return e;
@@ -573,58 +465,67 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   ta.y = y; ta.D = D; ta.Dt = ws.Dt; ta.xcol = ws.xcol; ta.G2 = ws.G2; ta.S = ws.S; ta.F2 = ws.F2; ta.W = ws.W;
   ta.mass = ws.mass; ta.err = ws.err; ta.done = ws.done; ta.iters = ws.iters; ta.status = ws.status; ta.t = tw;
 
-  tc::GemmArgs gs{nullptr, ws.active, ws.n_active, n, batch, n, n, tw.err, tw.fix_list, nullptr,
-                  (unsigned long long)batch * n};
+  // the applies K V^T (BF16): M = bins, N = slots mapped to problems, reduction over bins
+  tc::GemmArgs ga{};
+  ga.col_map = ws.active; ga.n_cols = ws.n_active; ga.M = n; ga.N = batch; ga.Kd = n; ga.ld_out = n;
+  ga.err = tw.err; ga.fix_list = tw.fix_list; ga.fix_cap = (unsigned long long)batch * n; ga.splits = 1;
+  // D^T r (TF32): M = dictionary columns, N = slots (partial sums by slot), reduction over bins split
+  tc::GemmArgs gr{};
+  gr.out = mb.NU; gr.n_cols = ws.n_active; gr.M = k; gr.N = batch; gr.Kd = n; gr.ld_out = mb.ldnu; gr.err = tw.err;
+  gr.splits = tc::choose_splits(((k + tc::BM - 1) / tc::BM) * ((batch + tc::BN - 1) / tc::BN),
+                                (n + tc::KindTraits<tc::KIND_TF32>::BK - 1) / tc::KindTraits<tc::KIND_TF32>::BK);
+  gr.split_stride = mb.plane;
+  // s = D w (TF32): M = bins, N = slots mapped to problems, reduction over dictionary columns
+  tc::GemmArgs gw{};
+  gw.out = ws.S; gw.col_map = ws.active; gw.n_cols = ws.n_active; gw.M = n; gw.N = batch; gw.Kd = k;
+  gw.ld_out = n; gw.err = tw.err; gw.flush_tiny = 1; gw.splits = 1;
+
   for (int it = 0;; ++it) {
     ta.it = it;
     L.begin(KIND_MM);
     tc_prep_src_kernel<<<batch, 256, 0, L.stream>>>(ta);
     L.end();
-    gs.out = tw.ACC_src[it & 1];
-    gs.fix_cnt = tw.fix_cnt;
+    ga.out = tw.ACC_src[it & 1];
+    ga.fix_cnt = tw.fix_cnt;
     L.begin(KIND_APPLY);
-    e = tc::launch_gemm3(tw.Khi, tw.Klo, tw.Vhi, tw.Vlo, n, batch, n, tw.ld, gs, L.stream);
+    e = tc::launch_gemm3<tc::KIND_BF16>(tw.Khi, tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n, batch, n, ga, L.stream);
     L.end();
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
-    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, gs.fix_cap, n, ws.xt,
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, ga.fix_cap, n, ws.xt,
                                                     ws.G2, tw.ACC_src[it & 1], tw.Msrc[it & 1]);
     L.end();
+    L.begin(KIND_MM);
+    tc_violation_kernel<<<batch, 256, 0, L.stream>>>(ta);
+    L.end();
+    if (it >= sp.max_iter) break;
+    L.begin(KIND_MM);
+    e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dthi, tw.Dtlo, tw.ld, tw.Rhi, tw.Rlo, tw.ld, k, batch, n, gr, L.stream);
+    L.end();
+    if (e != cudaSuccess) return e;
+    L.begin(KIND_MM);
+    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits);
+    L.end();
+    L.begin(KIND_MM);
+    e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
+    L.end();
+    if (e != cudaSuccess) return e;
     if (it > 0) {
-      L.begin(KIND_MM);
-      tc_violation_kernel<<<batch, 256, 0, L.stream>>>(ta);
-      L.end();
       L.begin(KIND_COMPACT);
       compact_kernel<<<1, 1024, 0, L.stream>>>(ws.active, ws.n_active, ws.done);
       L.end();
     }
-    if (it >= sp.max_iter) break;
     L.begin(KIND_MM);
-    {
-      const dim3 gA((batch + 31) / 32, DTR_SPLIT);
-      if (k <= 32) tc_dtr_kernel<32><<<gA, 256, 0, L.stream>>>(ta, mb);
-      else if (k <= 64) tc_dtr_kernel<64><<<gA, 256, 0, L.stream>>>(ta, mb);
-      else if (k <= 128) tc_dtr_kernel<128><<<gA, 256, 0, L.stream>>>(ta, mb);
-      else tc_dtr_kernel<256><<<gA, 256, 0, L.stream>>>(ta, mb);
-    }
+    tc_operand_kernel<<<batch, 256, 0, L.stream>>>(ta);
     L.end();
-    L.begin(KIND_MM);
-    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb);
-    L.end();
-    L.begin(KIND_MM);
-    tc_dw_kernel<<<dim3((n + DW_ROWS - 1) / DW_ROWS, (batch + 63) / 64), 256, 0, L.stream>>>(ta, mb);
-    L.end();
-    L.begin(KIND_MM);
-    tc_operand_kernel<<<batch, 256, 0, L.stream>>>(ta, mb);
-    L.end();
-    gs.out = tw.ACC_tgt;
-    gs.fix_cnt = tw.fix_cnt + 1;
+    ga.out = tw.ACC_tgt;
+    ga.fix_cnt = tw.fix_cnt + 1;
     L.begin(KIND_APPLY);
-    e = tc::launch_gemm3(tw.Khi, tw.Klo, tw.Vhi, tw.Vlo, n, batch, n, tw.ld, gs, L.stream);
+    e = tc::launch_gemm3<tc::KIND_BF16>(tw.Khi, tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n, batch, n, ga, L.stream);
     L.end();
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
-    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 1, tw.fix_cnt, gs.fix_cap, n, ws.xt,
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 1, tw.fix_cnt, ga.fix_cap, n, ws.xt,
                                                     ws.F2, tw.ACC_tgt, tw.Mtgt);
     L.end();
     if ((it + 1) % sp.poll_every == 0) {
