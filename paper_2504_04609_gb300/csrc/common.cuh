@@ -28,6 +28,11 @@ template <> struct Prec<float> {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
   }
+  static __device__ __forceinline__ float rcp(float v) {  // rcp.approx.ftz.f32: within 1 ulp
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+  }
   static __device__ __forceinline__ float exp(float v) { return ::expf(v); }
   static __device__ __forceinline__ float expm1(float v) { return ::expm1f(v); }
   static __device__ __forceinline__ float log(float v) { return ::logf(v); }
@@ -54,9 +59,9 @@ template <> struct Prec<double> {
 //   w <- w (1 + z - log w) / (1 + w)
 // (the iteration underlying Lawrence, Corless & Jeffrey, ACM TOMS 38(3), 2012).  Start:
 // e^z e^{-e^z} for z < -1 (w = e^{z - w}), z - log z + log z / z for z > 3 (asymptotic series),
-// and 1 + (z-1)/2 + (z-1)^2/16 (Taylor expansion at z = 1, where w = 1) in between.  Three
-// steps reach FP32 rounding and five FP64 over all finite z (checked against scipy's
-// wrightomega in the tests).  Returns 0 for z = -inf and e^z below the underflow threshold.
+// and 1 + (z-1)/2 + (z-1)^2/16 (Taylor expansion at z = 1, where w = 1) in between.  Five steps
+// reach FP64 rounding over all finite z.  Returns 0 for z = -inf and e^z below the underflow
+// threshold.  The FP32 specialisation below runs three steps on the MUFU approximations.
 template <typename T>
 __device__ __forceinline__ T wright_omega(T z) {
   using P = Prec<T>;
@@ -74,6 +79,30 @@ __device__ __forceinline__ T wright_omega(T z) {
   }
 #pragma unroll
   for (int it = 0; it < P::kOmegaIters; ++it) w = w * (T(1) + z - P::log(w)) / (T(1) + w);
+  return w;
+}
+
+// FP32: the same start and three Newton steps, with log w = ln2 lg2(w) (lg2.approx, absolute error
+// about 2^-22) and the division as a multiply by rcp.approx.  Newton corrects the errors of every
+// step but the last, whose log error moves w by a relative ~1e-7 / (1 + w): FP32 rounding.
+template <>
+__device__ __forceinline__ float wright_omega<float>(float z) {
+  using P = Prec<float>;
+  constexpr float ln2 = 0.693147180559945309f, log2e = 1.442695040888963407f;
+  if (!(z > P::kUnderflowZ)) return (z == z) ? P::exp(z) : z;  // also maps -inf to 0
+  float w;
+  if (z < -1.f) {
+    const float ez = P::exp2(z * log2e);
+    w = ez * P::exp2(-ez * log2e);
+  } else if (z > 3.f) {
+    const float lz = P::log2(z) * ln2;
+    w = z - lz + lz * P::rcp(z);
+  } else {
+    const float d = z - 1.f;
+    w = 1.f + d * 0.5f + d * d * 0.0625f;
+  }
+#pragma unroll
+  for (int it = 0; it < P::kOmegaIters; ++it) w = w * (1.f + z - P::log2(w) * ln2) * P::rcp(1.f + w);
   return w;
 }
 

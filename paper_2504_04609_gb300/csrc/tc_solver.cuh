@@ -143,22 +143,6 @@ __global__ void kbuild_kernel(const float* xt, int n, int ld, __nv_bfloat16* Khi
   }
 }
 
-// Write row `slot` of the operand: 2^{L_j - M} as BF16 hi + lo, where M = max_j L_j.  Returns M.
-__device__ __forceinline__ float write_operand(const float* L, int n, int ld, int slot, __nv_bfloat16* Vhi,
-                                               __nv_bfloat16* Vlo, float* red) {
-  float m = -CUDART_INF_F;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, L[j]);
-  m = block_max(m, red);
-  if (!(m > -CUDART_INF_F)) m = 0.f;  // every term vanishes
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const float v = Prec<float>::exp2(L[j] - m);
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    Vhi[(size_t)slot * ld + j] = hi;
-    Vlo[(size_t)slot * ld + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
-  }
-  return m;
-}
-
 // Exact fix-up of the sums a GEMM listed as underflowed, one CTA of 256 threads per listed
 // (problem p, row i) so that a row costs a few memory round trips, not n / 32:
 //   L = log2 sum_j 2^(in_pj - (xt_i - xt_j)^2)     (two passes over j: max, then sum)
@@ -226,45 +210,128 @@ struct TcIterArgs {
   TcWorkspace t;
 };
 
-// Datafit step from the previous target sums (it > 0), then the source operand.
-__global__ void __launch_bounds__(256) tc_prep_src_kernel(TcIterArgs A) {
+// ---- per-problem row kernels (one CTA per active slot) -----------------------------------------
+// With EPT > 0 the row lives in registers: thread t holds bins j = e * NT + t (e < EPT), so each
+// load instruction of a warp is one contiguous 128-byte segment and every load of a pass is issued
+// before its first use; n <= EPT * NT.  EPT = 0 streams the row through global memory (any n).
+// tc_row_cfg picks the smallest register configuration that holds n.
+enum { ROW_256x4 = 0, ROW_256x8 = 1, ROW_256x16 = 2, ROW_1024x16 = 3, ROW_STREAM = 4 };
+inline int tc_row_cfg(int n) {
+  return n <= 1024 ? ROW_256x4 : n <= 2048 ? ROW_256x8 : n <= 4096 ? ROW_256x16 : n <= 16384 ? ROW_1024x16 : ROW_STREAM;
+}
+#define TC_ROW_LAUNCH(KERNEL, CFG, GRID, STREAM, ...)                                       \
+  do {                                                                                      \
+    switch (CFG) {                                                                          \
+      case ROW_256x4: KERNEL<256, 4><<<(GRID), 256, 0, (STREAM)>>>(__VA_ARGS__); break;     \
+      case ROW_256x8: KERNEL<256, 8><<<(GRID), 256, 0, (STREAM)>>>(__VA_ARGS__); break;     \
+      case ROW_256x16: KERNEL<256, 16><<<(GRID), 256, 0, (STREAM)>>>(__VA_ARGS__); break;   \
+      case ROW_1024x16: KERNEL<1024, 16><<<(GRID), 1024, 0, (STREAM)>>>(__VA_ARGS__); break; \
+      default: KERNEL<256, 0><<<(GRID), 256, 0, (STREAM)>>>(__VA_ARGS__); break;            \
+    }                                                                                       \
+  } while (0)
+
+// Datafit step (Table 1) in log2 units: the new target potential from log2 of the target sum v and
+// the target bin y.
+__device__ __forceinline__ float tc_datafit(const TcIterArgs& A, float v, float yv) {
+  using P = Prec<float>;
+  switch (A.datafit) {
+    case DF_BALANCED: return P::log2(yv) - v;
+    case DF_KL: return A.kl_coef * (P::log2(yv) - v);
+    case DF_TV: return fminf(fmaxf(P::log2(yv) - v, -A.tv_bound), A.tv_bound);
+    default: {
+      const float z = A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
+      return (A.lam_over_eps * yv - wright_omega<float>(z)) * float(kLog2e);
+    }
+  }
+}
+
+__device__ __forceinline__ void tc_store_operand(float v, __nv_bfloat16* hi_row, __nv_bfloat16* lo_row, int j) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  hi_row[j] = hi;
+  lo_row[j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Datafit step from the previous target sums (it > 0), then the source operand row
+// V_j = 2^{G2_j - M} with M = max_j G2_j (0 when every term vanishes).
+template <int NT, int EPT>
+__global__ void __launch_bounds__(NT) tc_prep_src_kernel(TcIterArgs A) {
   using P = Prec<float>;
   __shared__ float red[32];
   const int slot = blockIdx.x;
   if (slot >= *A.n_active) return;
   const int p = A.active[slot], n = A.n;
   float* G2 = A.G2 + (size_t)p * n;
-  if (A.it > 0) {
-    const float* acc = A.t.ACC_tgt + (size_t)p * n;
-    const float* y = A.y + (size_t)p * n;
-    const float mt = A.t.Mtgt[p];
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const float v = tc_log2_sum(acc[j], mt);
-      const float yv = y[j];
-      float gn;
-      switch (A.datafit) {
-        case DF_BALANCED: gn = P::log2(yv) - v; break;
-        case DF_KL: gn = A.kl_coef * (P::log2(yv) - v); break;
-        case DF_TV: gn = fminf(fmaxf(P::log2(yv) - v, -A.tv_bound), A.tv_bound); break;
-        default: {
-          const float z = A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
-          gn = (A.lam_over_eps * yv - wright_omega<float>(z)) * float(kLog2e);
-        }
+  const float* acc = A.t.ACC_tgt + (size_t)p * n;
+  const float* y = A.y + (size_t)p * n;
+  const float mt = A.t.Mtgt[p];
+  __nv_bfloat16* vhi = A.t.Vhi + (size_t)slot * A.t.ld;
+  __nv_bfloat16* vlo = A.t.Vlo + (size_t)slot * A.t.ld;
+  float m = -CUDART_INF_F;
+  if constexpr (EPT > 0) {
+    float g[EPT];
+    if (A.it > 0) {
+      float a[EPT], yv[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int j = e * NT + threadIdx.x;
+        a[e] = j < n ? acc[j] : 0.f;
+        yv[e] = j < n ? y[j] : 0.f;
       }
-      G2[j] = gn;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int j = e * NT + threadIdx.x;
+        g[e] = tc_datafit(A, tc_log2_sum(a[e], mt), yv[e]);
+        if (j < n) G2[j] = g[e];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int j = e * NT + threadIdx.x;
+        g[e] = j < n ? G2[j] : -CUDART_INF_F;
+      }
     }
-    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      if (e * NT + threadIdx.x < n) m = fmaxf(m, g[e]);
+    m = block_max(m, red);
+    if (!(m > -CUDART_INF_F)) m = 0.f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int j = e * NT + threadIdx.x;
+      if (j < n) tc_store_operand(P::exp2(g[e] - m), vhi, vlo, j);
+    }
+  } else {
+    for (int j = threadIdx.x; j < n; j += NT) {
+      const float g = A.it > 0 ? tc_datafit(A, tc_log2_sum(acc[j], mt), y[j]) : G2[j];
+      if (A.it > 0) G2[j] = g;
+      m = fmaxf(m, g);
+    }
+    m = block_max(m, red);
+    if (!(m > -CUDART_INF_F)) m = 0.f;
+    for (int j = threadIdx.x; j < n; j += NT) tc_store_operand(P::exp2(G2[j] - m), vhi, vlo, j);
   }
-  const float m = write_operand(G2, n, A.t.ld, slot, A.t.Vhi, A.t.Vlo, red);
   if (threadIdx.x == 0) A.t.Msrc[A.it & 1][p] = m;
 }
 
-// Violation of the previous iteration's plan and the stopping decision (it > 0; one CTA per active
-// slot): e = sum_i S_i |a_new_i / a_old_i - 1| / sum_i S_i from the raw sums.  The shift difference
-// of two nearby FP32 numbers is exact, so the ratio keeps FP32 relative precision.  Every iteration
+// Violation of the previous iteration's plan and the stopping decision (it > 0):
+// e = sum_i S_i |a_new_i / a_old_i - 1| / sum_i S_i from the raw sums.  The shift difference of
+// two nearby FP32 numbers is exact, so the ratio keeps FP32 relative precision.  Every iteration
 // also writes the MM log ratios r_i = log2(a_i / s_i) (0 where s_i = 0) as the TF32 hi/lo row
 // `slot` of the D^T r operand.
-__global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
+__device__ __forceinline__ float tc_violation_term(float s, float an, float ao, float mc, float mo, float f,
+                                                   bool check, float* r) {
+  using P = Prec<float>;
+  *r = 0.f;
+  if (!(s > 0.f)) return 0.f;
+  const float la = tc_log2_sum(an, mc);
+  *r = la - P::log2(s);
+  if (!check) return 0.f;
+  const float ratio = (an > 0.f && ao > 0.f) ? an / ao * f : P::exp2(la - tc_log2_sum(ao, mo));
+  return s * fabsf(ratio - 1.f);
+}
+
+template <int NT, int EPT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) tc_violation_kernel(TcIterArgs A) {
   using P = Prec<float>;
   __shared__ float red[32];
   const int slot = blockIdx.x;
@@ -279,18 +346,28 @@ __global__ void __launch_bounds__(256) tc_violation_kernel(TcIterArgs A) {
   const float f = P::exp2(mc - mo);
   const bool check = A.it > 0;
   float part = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float s = S[i], an = acc[i];
-    float r = 0.f;
-    if (s > 0.f) {
-      r = tc_log2_sum(an, mc) - P::log2(s);
-      if (check) {
-        const float ao = acc_old[i];
-        const float ratio = (an > 0.f && ao > 0.f) ? an / ao * f : P::exp2(tc_log2_sum(an, mc) - tc_log2_sum(ao, mo));
-        part += s * fabsf(ratio - 1.f);
-      }
+  if constexpr (EPT > 0) {
+    float s[EPT], an[EPT], ao[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int j = e * NT + threadIdx.x;
+      s[e] = j < n ? S[j] : 0.f;
+      an[e] = j < n ? acc[j] : 0.f;
+      ao[e] = (check && j < n) ? acc_old[j] : 0.f;
     }
-    tf32_split(r, rhi + i, rlo + i);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int j = e * NT + threadIdx.x;
+      float r;
+      part += tc_violation_term(s[e], an[e], ao[e], mc, mo, f, check, &r);
+      if (j < n) tf32_split(r, rhi + j, rlo + j);
+    }
+  } else {
+    for (int j = threadIdx.x; j < n; j += NT) {
+      float r;
+      part += tc_violation_term(S[j], acc[j], check ? acc_old[j] : 0.f, mc, mo, f, check, &r);
+      tf32_split(r, rhi + j, rlo + j);
+    }
   }
   if (!check) return;
   part = block_sum(part, red);
@@ -340,8 +417,9 @@ inline size_t carve_tc_mm(void* base, int k_max, int batch_max, TcMMBuf* mb) {
 }
 
 // One thread per (slot, j) of the slots before compaction.  A problem that has just stopped keeps
-// its weights; every slot writes its weight row as the TF32 hi/lo B operand of s = D w.
-__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, int splits) {
+// its weights (and with update = 0 every problem does); every slot writes its weight row as the
+// TF32 hi/lo B operand of s = D w.
+__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, int splits, int update) {
   using P = Prec<float>;
   const int na = *A.n_active, k = A.k;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,7 +427,7 @@ __global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, i
   if (slot >= na) return;
   const int p = A.active[slot];
   float wn = A.W[(size_t)p * k + j];
-  if (!A.done[p]) {
+  if (update && !A.done[p]) {
     float sum = 0.f;
     for (int z = 0; z < splits; ++z) sum += M.NU[z * M.plane + (size_t)slot * M.ldnu + j];
     const float xj = A.xcol[j];
@@ -366,7 +444,8 @@ __global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, i
 
 // One CTA per active slot (after compaction): F2_i = log2 S_i - log2 a_i (-inf where S_i = 0), the
 // target shift M' = max_i F2_i, the mass sum_i S_i, then U_i = 2^{F2_i - M'} as BF16 hi/lo.
-__global__ void __launch_bounds__(256) tc_operand_kernel(TcIterArgs A) {
+template <int NT, int EPT>
+__global__ void __launch_bounds__(NT) tc_operand_kernel(TcIterArgs A) {
   using P = Prec<float>;
   __shared__ float red[32];
   const int slot = blockIdx.x;
@@ -375,27 +454,57 @@ __global__ void __launch_bounds__(256) tc_operand_kernel(TcIterArgs A) {
   const float* S = A.S + (size_t)p * n;
   const float* acc = A.t.ACC_src[cur] + (size_t)p * n;
   float* F2 = A.F2 + (size_t)p * n;
+  __nv_bfloat16* vhi = A.t.Vhi + (size_t)slot * A.t.ld;
+  __nv_bfloat16* vlo = A.t.Vlo + (size_t)slot * A.t.ld;
   const float mc = A.t.Msrc[cur][p];
   float fm = -CUDART_INF_F, ms = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float s = S[i];
-    const float f2 = s > 0.f ? P::log2(s) - tc_log2_sum(acc[i], mc) : P::ninf();
-    F2[i] = f2;
-    fm = fmaxf(fm, f2);
-    ms += s;
-  }
-  fm = block_max(fm, red);
-  ms = block_sum(ms, red);
-  const float m = fm > -CUDART_INF_F ? fm : 0.f;
-  if (threadIdx.x == 0) {
-    A.mass[p] = ms;
-    A.t.Mtgt[p] = m;
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float v = P::exp2(F2[i] - m);
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    A.t.Vhi[(size_t)slot * A.t.ld + i] = hi;
-    A.t.Vlo[(size_t)slot * A.t.ld + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  if constexpr (EPT > 0) {
+    float f2[EPT];
+    {
+      float sv[EPT], av[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int j = e * NT + threadIdx.x;
+        sv[e] = j < n ? S[j] : 0.f;
+        av[e] = j < n ? acc[j] : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int j = e * NT + threadIdx.x;
+        f2[e] = sv[e] > 0.f ? P::log2(sv[e]) - tc_log2_sum(av[e], mc) : P::ninf();
+        if (j < n) F2[j] = f2[e];
+        fm = fmaxf(fm, f2[e]);
+        ms += sv[e];
+      }
+    }
+    fm = block_max(fm, red);
+    ms = block_sum(ms, red);
+    const float m = fm > -CUDART_INF_F ? fm : 0.f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int j = e * NT + threadIdx.x;
+      if (j < n) tc_store_operand(P::exp2(f2[e] - m), vhi, vlo, j);
+    }
+    if (threadIdx.x == 0) {
+      A.mass[p] = ms;
+      A.t.Mtgt[p] = m;
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const float s = S[i];
+      const float f2 = s > 0.f ? P::log2(s) - tc_log2_sum(acc[i], mc) : P::ninf();
+      F2[i] = f2;
+      fm = fmaxf(fm, f2);
+      ms += s;
+    }
+    fm = block_max(fm, red);
+    ms = block_sum(ms, red);
+    const float m = fm > -CUDART_INF_F ? fm : 0.f;
+    for (int i = threadIdx.x; i < n; i += NT) tc_store_operand(P::exp2(F2[i] - m), vhi, vlo, i);
+    if (threadIdx.x == 0) {
+      A.mass[p] = ms;
+      A.t.Mtgt[p] = m;
+    }
   }
 }
 
@@ -444,9 +553,6 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   colsum_kernel<float><<<(k + 7) / 8, 256, 0, L.stream>>>(ws.Dt, ws.xcol, n, k);
   L.end();
   L.begin(KIND_OTHER);
-  source_init_kernel<float><<<batch, 256, 0, L.stream>>>(ws.Dt, ws.W, ws.S, ws.mass, n, k);
-  L.end();
-  L.begin(KIND_OTHER);
   kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo);
   L.end();
   L.begin(KIND_OTHER);
@@ -479,11 +585,22 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   tc::GemmArgs gw{};
   gw.out = ws.S; gw.col_map = ws.active; gw.n_cols = ws.n_active; gw.M = n; gw.N = batch; gw.Kd = k;
   gw.ld_out = n; gw.err = tw.err; gw.flush_tiny = 1; gw.splits = 1;
+  const int row_cfg = tc_row_cfg(n);
+
+  // the initial source marginal s = D w0, through the same operand and GEMM as every iteration
+  // (the mass sum_i s_i is first needed by the violation at it = 1 and set by the operand kernel)
+  L.begin(KIND_OTHER);
+  tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, 0, 0);
+  L.end();
+  L.begin(KIND_OTHER);
+  e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
+  L.end();
+  if (e != cudaSuccess) return e;
 
   for (int it = 0;; ++it) {
     ta.it = it;
     L.begin(KIND_MM);
-    tc_prep_src_kernel<<<batch, 256, 0, L.stream>>>(ta);
+    TC_ROW_LAUNCH(tc_prep_src_kernel, row_cfg, batch, L.stream, ta);
     L.end();
     ga.out = tw.ACC_src[it & 1];
     ga.fix_cnt = tw.fix_cnt;
@@ -496,7 +613,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
                                                     ws.G2, tw.ACC_src[it & 1], tw.Msrc[it & 1]);
     L.end();
     L.begin(KIND_MM);
-    tc_violation_kernel<<<batch, 256, 0, L.stream>>>(ta);
+    TC_ROW_LAUNCH(tc_violation_kernel, row_cfg, batch, L.stream, ta);
     L.end();
     if (it >= sp.max_iter) break;
     L.begin(KIND_MM);
@@ -504,7 +621,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     L.end();
     if (e != cudaSuccess) return e;
     L.begin(KIND_MM);
-    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits);
+    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1);
     L.end();
     L.begin(KIND_MM);
     e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
@@ -516,7 +633,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
       L.end();
     }
     L.begin(KIND_MM);
-    tc_operand_kernel<<<batch, 256, 0, L.stream>>>(ta);
+    TC_ROW_LAUNCH(tc_operand_kernel, row_cfg, batch, L.stream, ta);
     L.end();
     ga.out = tw.ACC_tgt;
     ga.fix_cnt = tw.fix_cnt + 1;
