@@ -61,7 +61,7 @@ template <> struct Prec<double> {
 // e^z e^{-e^z} for z < -1 (w = e^{z - w}), z - log z + log z / z for z > 3 (asymptotic series),
 // and 1 + (z-1)/2 + (z-1)^2/16 (Taylor expansion at z = 1, where w = 1) in between.  Five steps
 // reach FP64 rounding over all finite z.  Returns 0 for z = -inf and e^z below the underflow
-// threshold.  The FP32 specialisation below runs three steps on the MUFU approximations.
+// threshold.  wright_omega_fast below runs the FP32 steps on the MUFU approximations.
 template <typename T>
 __device__ __forceinline__ T wright_omega(T z) {
   using P = Prec<T>;
@@ -82,11 +82,12 @@ __device__ __forceinline__ T wright_omega(T z) {
   return w;
 }
 
-// FP32: the same start and three Newton steps, with log w = ln2 lg2(w) (lg2.approx, absolute error
-// about 2^-22) and the division as a multiply by rcp.approx.  Newton corrects the errors of every
-// step but the last, whose log error moves w by a relative ~1e-7 / (1 + w): FP32 rounding.
-template <>
-__device__ __forceinline__ float wright_omega<float>(float z) {
+// FP32 variant for kernels that evaluate omega once per bin: the same start and three Newton
+// steps, with log w = ln2 lg2(w) (lg2.approx, absolute error about 2^-22) and the division as a
+// multiply by rcp.approx.  Newton corrects the errors of every step but the last, whose log error
+// moves w by a relative ~1e-7 / (1 + w): FP32 rounding.  (Kernels that need omega only once per
+// weight keep wright_omega<float>.)
+__device__ __forceinline__ float wright_omega_fast(float z) {
   using P = Prec<float>;
   constexpr float ln2 = 0.693147180559945309f, log2e = 1.442695040888963407f;
   if (!(z > P::kUnderflowZ)) return (z == z) ? P::exp(z) : z;  // also maps -inf to 0

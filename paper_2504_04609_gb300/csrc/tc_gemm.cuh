@@ -9,15 +9,20 @@
 //   KIND_TF32 (kind::tf32, FP32 containers rounded to TF32): ~21 bits; the dictionary contractions
 //             D w (A = D, B = the weights) and D^T r (A = D^T, B = the log ratios).
 // Accumulation is FP32 in tensor memory (TMEM); the epilogue stores FP32 sums, optionally through a
-// column map, with an optional split of the reduction over blockIdx.z (each split stores its own
-// partial sums, added later in a fixed order).
+// column map, with an optional split of the reduction (each split stores its own partial sums,
+// added later in a fixed order).
 //
-// One CTA computes a 128 x 256 output tile over its share of the reduction:
-//   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, 2-stage ring)
-//   warp 1 lane 0: MMA issuer  (3 x 4 tcgen05.mma per 128-byte k block)
-//   warps 4..7   : epilogue    (tcgen05.ld 32x32b, one TMEM lane quarter per warp)
+// Persistent kernel, one CTA per SM; work units (128 x 128 output tile, reduction split) are dealt
+// round-robin over the CTAs:
+//   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, 3-stage ring that runs
+//                  on across units)
+//   warp 1 lane 0: MMA issuer  (3 x 4 tcgen05.mma per 128-byte k block) into one of two TMEM
+//                  accumulators, so the epilogue of unit i overlaps the MMAs of unit i + 1
+//   warps 4..7   : epilogue    (tcgen05.ld 32x32b, one TMEM lane quarter per warp; 64 columns at a
+//                  time through a 32 KiB staging buffer and one bulk copy per output column)
 // Every wait on an mbarrier is bounded (about 2 s of %globaltimer); on expiry the CTA records an
-// error in *err, stops issuing work, waits boundedly for its committed MMAs and frees its TMEM.
+// error in *err, stops issuing work, lets its issued copies land, waits boundedly for its
+// committed MMAs and frees its TMEM.
 #pragma once
 
 #include <cuda.h>
@@ -28,13 +33,15 @@ namespace otlm {
 namespace tc {
 
 enum { KIND_BF16 = 0, KIND_TF32 = 1 };
-constexpr int BM = 128, BN = 256, BK_BYTES = 128, STAGES = 2;
+constexpr int BM = 128, BN = 128, BK_BYTES = 128, STAGES = 3;
 constexpr int A_TILE = BM * BK_BYTES;                     // 16 KiB
-constexpr int B_TILE = BN * BK_BYTES;                     // 32 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;      // 96 KiB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int B_TILE = BN * BK_BYTES;                     // 16 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;      // 64 KiB
+constexpr int EPI_BYTES = 64 * BM * 4;                    // 32 KiB: 64 output columns of 128 rows
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + 128;
 constexpr int THREADS = 256;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 2 * BN;                    // two accumulators (double buffer)
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 constexpr unsigned long long WAIT_NS = 2000000000ull;    // bounded waits: 2 s
 
 enum { ERR_NONE = 0, ERR_WAIT_TMA = 1, ERR_WAIT_MMA = 2, ERR_WAIT_ACC = 3 };
@@ -142,13 +149,26 @@ struct GemmArgs {
   unsigned long long* fix_cnt;   // entries this launch appended to fix_list
   unsigned long long fix_cap;    // capacity of fix_list (M x N covers every element)
   int flush_tiny;      // store sums below FLT_MIN as 0
-  int splits;          // the reduction is split into `splits` ranges of k blocks (blockIdx.z); >= 1
+  int splits;          // the reduction is split into `splits` ranges of k blocks; >= 1
   size_t split_stride; // elements between the partial-sum planes of consecutive splits
   int bulk;            // set by launch_gemm3: every output column segment is 16-byte aligned and a
                        // multiple of 16 bytes long, so the tile leaves through shared memory as
                        // one bulk copy per column
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Named barrier 1 over the four epilogue warps with an OR of `v`: every warp gets the same answer.
+__device__ __forceinline__ bool bar_or_epi(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v))
+      : "memory");
+  return r != 0;
+}
 __device__ __forceinline__ void bulk_store(float* gdst, uint32_t ssrc, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
                : "memory");
@@ -161,28 +181,48 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr int BK = KindTraits<KIND>::BK;
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int ncols = g.n_cols ? *g.n_cols : g.N;
-  if (n0 >= ncols) return;  // the whole CTA leaves before any barrier or TMEM use
-  float* const out = g.out + blockIdx.z * g.split_stride;
+  const int mt = (g.M + BM - 1) / BM, nt = (g.N + BN - 1) / BN;
+  const int units = mt * nt * g.splits;
+  const int nkb_all = (g.Kd + BK - 1) / BK;
+  // work unit u -> output tile (m0, n0) and reduction split z (m fastest)
+  auto coords = [&](int u, int* m0, int* n0, int* z) {
+    *m0 = (u % mt) * BM;
+    const int r = u / mt;
+    *n0 = (r % nt) * BN;
+    *z = r / nt;
+  };
+  // split z's k blocks (the host keeps splits <= blocks, so every split has at least one)
+  auto krange = [&](int z, int* kb0, int* nkb) {
+    *kb0 = static_cast<int>(static_cast<long long>(nkb_all) * z / g.splits);
+    *nkb = static_cast<int>(static_cast<long long>(nkb_all) * (z + 1) / g.splits) - *kb0;
+  };
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);  // full[2], empty[2], acc
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
-  int* fail = reinterpret_cast<int*>(bars + 9);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), acc_bar = smem_u32(bars + 2 * STAGES);
-  const uint32_t tiles = smem_u32(base);
-  auto a_hi = [&](int s) { return tiles + s * STAGE_BYTES; };
-  auto a_lo = [&](int s) { return tiles + s * STAGE_BYTES + A_TILE; };
-  auto b_hi = [&](int s) { return tiles + s * STAGE_BYTES + 2 * A_TILE; };
-  auto b_lo = [&](int s) { return tiles + s * STAGE_BYTES + 2 * A_TILE + B_TILE; };
+  float* const stage_out = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);  // [64 columns][128 rows]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES + EPI_BYTES);
+  // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  int* fail = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t ring = smem_u32(base), stage_s = smem_u32(stage_out);
+  auto a_hi = [&](int s) { return ring + s * STAGE_BYTES; };
+  auto a_lo = [&](int s) { return ring + s * STAGE_BYTES + A_TILE; };
+  auto b_hi = [&](int s) { return ring + s * STAGE_BYTES + 2 * A_TILE; };
+  auto b_lo = [&](int s) { return ring + s * STAGE_BYTES + 2 * A_TILE + B_TILE; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
     *fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -196,121 +236,169 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // this split's k blocks (the host keeps splits <= blocks, so every split has at least one)
-  const int nkb_all = (g.Kd + BK - 1) / BK;
-  const int kb0 = static_cast<int>(static_cast<long long>(nkb_all) * blockIdx.z / g.splits);
-  const int nkb = static_cast<int>(static_cast<long long>(nkb_all) * (blockIdx.z + 1) / g.splits) - kb0;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
+    // ---- TMA producer: the ring runs on across work units ----
     int last_round[STAGES];
     for (int s = 0; s < STAGES; ++s) last_round[s] = -1;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, r = kb / STAGES;
-      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (r - 1) & 1)) {
-        atomicCAS(g.err, 0, ERR_WAIT_MMA);
-        atomicExch(fail, 1);
-        break;
+    unsigned gk = 0;  // k blocks issued by this CTA
+    bool stop = false;
+    for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+      int m0, n0, z, kb0, nkb;
+      coords(u, &m0, &n0, &z);
+      if (n0 >= ncols) continue;
+      krange(z, &kb0, &nkb);
+      for (int kb = 0; kb < nkb; ++kb, ++gk) {
+        const int s = gk % STAGES, r = gk / STAGES;
+        if (gk >= STAGES && !mbar_wait(empty0 + 8 * s, (r - 1) & 1)) {
+          atomicCAS(g.err, 0, ERR_WAIT_MMA);
+          atomicExch(fail, 1);
+          stop = true;
+          break;
+        }
+        if (*(volatile int*)fail) {
+          stop = true;
+          break;
+        }
+        const int kc = (kb0 + kb) * BK;
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kc, m0);
+        tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kc, m0);
+        tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kc, n0);
+        tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kc, n0);
+        last_round[s] = r;
       }
-      if (*(volatile int*)fail) break;
-      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-      const int kc = (kb0 + kb) * BK;
-      tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kc, m0);
-      tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kc, m0);
-      tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kc, n0);
-      tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kc, n0);
-      last_round[s] = r;
     }
     // on an error path, let the copies already issued land before the CTA releases its memory
     if (*(volatile int*)fail)
       for (int s = 0; s < STAGES; ++s)
         if (last_round[s] >= 0) (void)mbar_wait(full0 + 8 * s, last_round[s] & 1);
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
+    // ---- MMA issuer: unit i accumulates into TMEM columns (i & 1) * BN ----
     constexpr uint32_t id = idesc<KIND>(BM, BN);
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, r = kb / STAGES;
-      if (!mbar_wait(full0 + 8 * s, r & 1)) {
-        atomicCAS(g.err, 0, ERR_WAIT_TMA);
+    unsigned gk = 0;
+    int i = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+      int m0, n0, z, kb0, nkb;
+      coords(u, &m0, &n0, &z);
+      if (n0 >= ncols) continue;
+      krange(z, &kb0, &nkb);
+      const int b = i & 1, use = i >> 1;
+      if (use >= 1 && !mbar_wait(acce0 + 8 * b, (use - 1) & 1)) {  // the epilogue has drained buffer b
+        atomicCAS(g.err, 0, ERR_WAIT_ACC);
         atomicExch(fail, 1);
         break;
       }
       tc_fence_after();
+      const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb, ++gk) {
+        const int s = gk % STAGES, r = gk / STAGES;
+        if (!mbar_wait(full0 + 8 * s, r & 1)) {
+          atomicCAS(g.err, 0, ERR_WAIT_TMA);
+          atomicExch(fail, 1);
+          stop = true;
+          break;
+        }
+        tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < BK_BYTES / 32; ++kk) {
-        const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
-        const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
-        umma<KIND>(tmem, ah, bh, id, issued);
-        umma<KIND>(tmem, ah, bl, id, 1);
-        umma<KIND>(tmem, al, bh, id, 1);
-        issued = 1;
+        for (int kk = 0; kk < BK_BYTES / 32; ++kk) {
+          const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
+          const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
+          umma<KIND>(d, ah, bh, id, issued);
+          umma<KIND>(d, ah, bl, id, 1);
+          umma<KIND>(d, al, bh, id, 1);
+          issued = 1;
+        }
+        umma_commit(empty0 + 8 * s);
       }
-      umma_commit(empty0 + 8 * s);
+      if (stop) break;
+      umma_commit(accf0 + 8 * b);  // fires once the unit's MMAs have completed
+      ++i;
     }
-    umma_commit(acc_bar);  // fires once every MMA issued above has completed
+    umma_commit(drain);  // fires once every MMA issued above has completed: TMEM may be released
+    (void)mbar_wait(drain, 0);
   } else if (warp >= 4) {
-    // ---- epilogue: TMEM -> registers -> problem-major FP32 rows ----
-    const bool ok = mbar_wait(acc_bar, 0);
-    if (!ok) atomicCAS(g.err, 0, ERR_WAIT_ACC);
-    tc_fence_after();
-    const int q = warp & 3;
-    const int row = m0 + q * 32 + lane;
-    const int ncol_tile = min(BN, ncols - n0);
-    // With `bulk`, the operand ring (idle once every MMA has completed) holds the tile column by
-    // column: stage[c][r], 128 rows = 512 bytes per column, written conflict-free by a warp.
-    float* const stage = reinterpret_cast<float*>(base);
-    if (ok && !*(volatile int*)fail) {
-      for (int c0 = 0; c0 < ncol_tile; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
-        unsigned low = 0;  // columns whose sum is below FLT_MIN (including an empty sum)
+    // ---- epilogue: TMEM -> registers -> problem-major FP32 rows, 64 columns at a time ----
+    const int q = warp & 3, et = threadIdx.x - 128;
+    int i = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      int m0, n0, z;
+      coords(u, &m0, &n0, &z);
+      if (n0 >= ncols) continue;
+      const int b = i & 1, use = i >> 1;
+      const bool ok = mbar_wait(accf0 + 8 * b, use & 1);
+      if (!ok) atomicCAS(g.err, 0, ERR_WAIT_ACC);
+      if (bar_or_epi(!ok || *(volatile int*)fail)) {  // the four warps leave together
+        atomicExch(fail, 1);
+        break;
+      }
+      tc_fence_after();
+      float* const out = g.out + z * g.split_stride;
+      const int row = m0 + q * 32 + lane;
+      const int ncol_tile = min(BN, ncols - n0);
+      const int rows = min(BM, g.M - m0);
+      for (int h = 0; h < BN / 64; ++h) {
+        if (g.bulk) {
+          if (et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging is free again
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        for (int c0 = h * 64; c0 < h * 64 + 64 && c0 < ncol_tile; c0 += 16) {
+          uint32_t v[16];
+          __syncwarp();
+          tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN + c0), v);
+          unsigned low = 0;  // columns whose sum is below FLT_MIN (including an empty sum)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int col = n0 + c0 + c;
-          const bool in = col < ncols && row < g.M;
-          float val = __uint_as_float(v[c]);
-          low |= (in && !(val >= 1.17549435e-38f)) ? (1u << c) : 0u;
-          if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
-          if (g.bulk) {
-            stage[(c0 + c) * BM + q * 32 + lane] = val;
-          } else if (in) {
-            const int o = g.col_map ? g.col_map[col] : col;
-            out[static_cast<size_t>(o) * g.ld_out + row] = val;
+          for (int c = 0; c < 16; ++c) {
+            const int col = n0 + c0 + c;
+            const bool in = col < ncols && row < g.M;
+            float val = __uint_as_float(v[c]);
+            low |= (in && !(val >= 1.17549435e-38f)) ? (1u << c) : 0u;
+            if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
+            if (g.bulk) {
+              stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;
+            } else if (in) {
+              const int o = g.col_map ? g.col_map[col] : col;
+              out[static_cast<size_t>(o) * g.ld_out + row] = val;
+            }
+          }
+          if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
+            for (; low; low &= low - 1) {
+              const int col = n0 + c0 + __ffs(low) - 1;
+              const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
+              if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
+            }
           }
         }
-        if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
-          for (; low; low &= low - 1) {
-            const int col = n0 + c0 + __ffs(low) - 1;
-            const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
-            if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
+        if (h == BN / 64 - 1) {  // every TMEM read of buffer b is done: hand it back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        }
+        if (g.bulk) {
+          // the generic-proxy writes become visible to the bulk-copy (async) proxy, then one thread
+          // per column sends rows m0 .. m0 + rows - 1 of that column
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          const int c = h * 64 + et;
+          if (et < 64 && c < ncol_tile) {
+            const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
+            bulk_store(out + static_cast<size_t>(o) * g.ld_out + m0, stage_s + static_cast<uint32_t>(et) * (BM * 4),
+                       static_cast<uint32_t>(rows) * 4u);
           }
+          if (et < 64) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
       }
+      ++i;
     }
-    if (g.bulk) {
-      // the generic-proxy writes above become visible to the bulk-copy (async) proxy, then the
-      // four epilogue warps meet; each thread sends whole columns (rows m0 .. m0 + rows - 1)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (ok && !*(volatile int*)fail) {
-        const int rows = min(BM, g.M - m0);
-        const uint32_t bytes = static_cast<uint32_t>(rows) * 4u;
-        for (int c = threadIdx.x - 128; c < ncol_tile; c += 128) {
-          const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
-          bulk_store(out + static_cast<size_t>(o) * g.ld_out + m0, tiles + static_cast<uint32_t>(c) * (BM * 4), bytes);
-        }
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory may be released
-      }
-    }
+    if (g.bulk && et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
+    __syncwarp();
     tc_fence_after();
-    // on an error path make sure no committed MMA is still writing the accumulator
-    if (*(volatile int*)fail) (void)mbar_wait(acc_bar, 0);
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
@@ -350,6 +438,17 @@ inline bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 152;
+  }
+  return sms;
+}
+
 // Launch the three-term GEMM: A* [M][lda] (M x Kd used), B* [N][ldb] (N x Kd used); the row
 // pitches are multiples of 16 bytes and the bases 16-byte aligned (checked by the map encoder).
 template <int KIND>
@@ -371,18 +470,20 @@ inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, int lda, con
   if (!make_map<KIND>(&ta_hi, A_hi, M, Kd, lda, BM) || !make_map<KIND>(&ta_lo, A_lo, M, Kd, lda, BM) ||
       !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, BN) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, BN))
     return cudaErrorInvalidValue;
-  const dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, args.splits);
+  const long long units = static_cast<long long>((M + BM - 1) / BM) * ((N + BN - 1) / BN) * args.splits;
+  const int grid = static_cast<int>(units < num_sms() ? units : num_sms());  // persistent: one CTA per SM
   gemm3_kernel<KIND><<<grid, THREADS, SMEM_BYTES, stream>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
   return cudaGetLastError();
 }
 
 // Splits of a reduction of `nkb` k blocks over `tiles` output tiles that minimise
-// (waves of CTAs on 152 SMs) x (k blocks per split), at most 16.
+// (work units per SM, rounded up) x (k blocks per split), at most 16.
 inline int choose_splits(int tiles, int nkb) {
+  const int sms = num_sms();
   int best = 1;
   long long best_cost = -1;
   for (int s = 1; s <= 16 && s <= nkb; ++s) {
-    const long long waves = (static_cast<long long>(tiles) * s + 151) / 152;
+    const long long waves = (static_cast<long long>(tiles) * s + sms - 1) / sms;
     const long long cost = waves * ((nkb + s - 1) / s);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;

@@ -240,7 +240,7 @@ __device__ __forceinline__ float tc_datafit(const TcIterArgs& A, float v, float 
     case DF_TV: return fminf(fmaxf(P::log2(yv) - v, -A.tv_bound), A.tv_bound);
     default: {
       const float z = A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
-      return (A.lam_over_eps * yv - wright_omega<float>(z)) * float(kLog2e);
+      return (A.lam_over_eps * yv - wright_omega_fast(z)) * float(kLog2e);
     }
   }
 }
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, i
     if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
     else if (A.penalty == PEN_L2SQ) {
       const float c = A.alpha / (A.eps * xj);
-      wn = wright_omega<float>(P::log(c) + nu) / c;
+      wn = wright_omega_fast(P::log(c) + nu) / c;
     } else wn = P::exp(nu);
     A.W[(size_t)p * k + j] = wn;
   }
