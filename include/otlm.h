@@ -197,7 +197,10 @@ int otlm_ws_gradients(otlm_ws w, int batch, const float* y, const float* target,
 int otlm_ws_train_step(otlm_ws w, int batch, const float* y, const float* target, double lr,
                        double weight_decay, float* loss_out);
 /* Warm start for otlm_solve: g0 [batch][n] = eps * predicted g/eps, w0 [batch][k] = exp(predicted
- * log w); a non-finite prediction falls back to the cold start (g0 = 0, w0 = cold_w). */
+ * log w); a non-finite prediction falls back to the cold start (g0 = 0, w0 = cold_w).  The forward
+ * pass runs on the tensor cores (BF16 weights times activations carried as BF16 hi/lo pairs, FP32
+ * accumulation: ~16 bits, against the FP32-activation forward pass of training); if one of its
+ * GEMMs gives up a bounded wait, every row falls back to the cold start. */
 int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const float* cold_w, float* g0,
                     float* w0);
 

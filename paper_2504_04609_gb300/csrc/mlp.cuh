@@ -8,9 +8,10 @@
 //             KL datafit) are masked out of the loss.
 //   loss      mean over unmasked entries of (z - t_norm)^2
 // Weights are stored in BF16 for the forward pass (FP32 accumulation) with FP32 master copies
-// updated by AdamW.  All contractions go through one register-tiled SIMT kernel with strided
+// updated by AdamW.  Training contractions go through one register-tiled SIMT kernel with strided
 // operands (C = A B with A(m,k), B(k,n) given by element strides), which covers the forward pass
-// (B = W^T), the input gradient (B = W) and the weight gradient (A = dH^T).
+// (B = W^T), the input gradient (B = W) and the weight gradient (A = dH^T).  Inference runs the
+// forward pass on the tcgen05 GEMM (below).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -208,16 +209,68 @@ __global__ void init_kernel(float* p, size_t count, float a, unsigned long long 
   }
 }
 
+// ---- tensor-core forward pass (inference) ------------------------------------------------------
+// Each layer is Z = H W^T on gemm3_kernel<KIND_BF16> with A = W (the BF16 weights; their lo part
+// is an all-zero buffer, so the three hi/lo products are W times the activations to ~16 bits) and
+// B = the activations as a BF16 hi/lo pair, K-major with a row pitch padded to 8 elements (TMA
+// rows are 16-byte multiples).  Z may be split over the reduction (partial-sum planes); the
+// activation kernel adds the planes in order, the bias and GELU, and writes the next operand.
+
+// Weights of one layer, [out][in] FP32 -> BF16 with the row pitch inp.
+__global__ void pad_bf16_kernel(const float* W, int dout, int din, int inp, __nv_bfloat16* out) {
+  const size_t total = (size_t)dout * din;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int o = (int)(e / din), i = (int)(e - (size_t)o * din);
+    out[(size_t)o * inp + i] = __float2bfloat16_rn(W[e]);
+  }
+}
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  *hi = h;
+  *lo = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// features as the first operand: [n y / sum(y), log sum(y)] as BF16 hi/lo, row pitch inp.
+__global__ void features_split_kernel(const float* y, int n, int inp, __nv_bfloat16* hhi, __nv_bfloat16* hlo) {
+  __shared__ float red[32];
+  const int b = blockIdx.x;
+  float s = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += y[(size_t)b * n + i];
+  s = block_sum(s, red);
+  const float inv = s > 0.f ? (float)n / s : 0.f;
+  const size_t row = (size_t)b * inp;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) split_bf16(y[(size_t)b * n + i] * inv, hhi + row + i, hlo + row + i);
+  if (threadIdx.x == 0) split_bf16(s > 0.f ? logf(s) : 0.f, hhi + row + n, hlo + row + n);
+}
+
+// v = sum over the `splits` partial-sum planes of Z [rows][dout] + bias; hidden layers write
+// GELU(v) as the next BF16 hi/lo operand (row pitch outp), the last layer writes v to zout.
+__global__ void act_split_kernel(const float* Z, int splits, size_t plane, int rows, int dout, const float* bias,
+                                 __nv_bfloat16* ohi, __nv_bfloat16* olo, int outp, float* zout) {
+  const size_t total = (size_t)rows * dout;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / dout), f = (int)(e - (size_t)b * dout);
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += Z[z * plane + e];
+    v += bias[f];
+    if (zout) zout[e] = v;
+    else split_bf16(gelu(v), ohi + (size_t)b * outp + f, olo + (size_t)b * outp + f);
+  }
+}
+
 // predictions -> warm start: g0 = eps * (z * std + mean) for the first n outputs (the potential
 // g / eps), w0 = exp(z * std + mean) for the last k (log w); non-finite predictions fall back to
-// the cold start (g0 = 0, w0 = cold_w) so that a bad network can only cost iterations.
+// the cold start (g0 = 0, w0 = cold_w) so that a bad network can only cost iterations, and so does
+// every row when *fail is set (a tensor-core GEMM of the forward pass gave up a wait).
 __global__ void decode_kernel(const float* z, const float* mean, const float* std_, int rows, int n, int k, float eps,
-                              const float* cold_w, float* g0, float* w0) {
+                              const float* cold_w, float* g0, float* w0, const int* fail) {
   const int cols = n + k;
   const size_t total = (size_t)rows * cols;
+  const bool failed = fail && *fail;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / cols), j = (int)(e % cols);
-    const float v = z[e] * std_[j] + mean[j];
+    const float v = failed ? CUDART_NAN_F : z[e] * std_[j] + mean[j];
     if (j < n) {
       g0[(size_t)b * n + j] = isfinite(v) ? eps * v : 0.f;
     } else {

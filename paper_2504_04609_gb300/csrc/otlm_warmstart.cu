@@ -8,8 +8,11 @@
 
 #include "../../include/otlm.h"
 #include "mlp.cuh"
+#include "tc_gemm.cuh"
 
 using namespace otlm::mlp;
+
+constexpr int TC_MAX_SPLITS = 16;
 
 struct otlm_ws_ctx {
   int n = 0, k = 0, H = 0, batch_max = 0;
@@ -24,6 +27,16 @@ struct otlm_ws_ctx {
   float* dh[2] = {};
   float *mean = nullptr, *stdv = nullptr, *part = nullptr, *loss_scale = nullptr;
   long long step = 0;
+  // tensor-core forward pass (inference): padded BF16 weights, a zero lo part, activations as BF16
+  // hi/lo pairs (ping-pong), split partial sums, and the GEMMs' error flag
+  int inp[LAYERS] = {};            // row pitch of layer l's input operand (d[l] rounded up to 8)
+  int dmax = 0;                    // widest layer output
+  __nv_bfloat16* W16p[LAYERS] = {};
+  __nv_bfloat16* zero16 = nullptr;
+  __nv_bfloat16 *Hhi[2] = {}, *Hlo[2] = {};
+  float* Zs = nullptr;             // [TC_MAX_SPLITS][batch_max][dmax]
+  int* tc_err = nullptr;
+  bool tc_dirty = true;            // W16p is stale (weights changed since the last refresh)
 };
 
 namespace {
@@ -69,6 +82,39 @@ void backward(otlm_ws_ctx* w, int batch, const float* y, const float* target) {
   }
 }
 
+// Forward pass on the tensor cores into w->act[LAYERS] (inference only: no pre-activations).
+cudaError_t forward_tc(otlm_ws_ctx* w, int batch, const float* y) {
+  cudaStream_t s = w->stream;
+  if (w->tc_dirty) {
+    for (int l = 0; l < LAYERS; ++l)
+      pad_bf16_kernel<<<1184, 256, 0, s>>>(w->P + w->woff[l], w->d[l + 1], w->d[l], w->inp[l], w->W16p[l]);
+    w->tc_dirty = false;
+  }
+  cudaError_t e = cudaMemsetAsync(w->tc_err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  features_split_kernel<<<batch, 256, 0, s>>>(y, w->n, w->inp[0], w->Hhi[0], w->Hlo[0]);
+  const size_t plane = (size_t)w->batch_max * w->dmax;
+  int cur = 0;
+  for (int l = 0; l < LAYERS; ++l) {
+    const int din = w->d[l], dout = w->d[l + 1];
+    otlm::tc::GemmArgs g{};
+    g.out = w->Zs; g.M = dout; g.N = batch; g.Kd = din; g.ld_out = dout; g.err = w->tc_err;
+    g.splits = otlm::tc::choose_splits(((dout + otlm::tc::BM - 1) / otlm::tc::BM) * ((batch + otlm::tc::BN - 1) / otlm::tc::BN),
+                                       (din + 63) / 64);
+    if (g.splits > TC_MAX_SPLITS) g.splits = TC_MAX_SPLITS;
+    g.split_stride = plane;
+    e = otlm::tc::launch_gemm3<otlm::tc::KIND_BF16>(w->W16p[l], w->zero16, w->inp[l], w->Hhi[cur], w->Hlo[cur],
+                                                    w->inp[l], dout, batch, din, g, s);
+    if (e != cudaSuccess) return e;
+    const bool last = l == LAYERS - 1;
+    act_split_kernel<<<1184, 256, 0, s>>>(w->Zs, g.splits, plane, batch, dout, w->P + w->boff[l],
+                                          last ? nullptr : w->Hhi[cur ^ 1], last ? nullptr : w->Hlo[cur ^ 1],
+                                          last ? 0 : w->inp[l + 1], last ? w->act[LAYERS] : nullptr);
+    cur ^= 1;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -101,6 +147,18 @@ int otlm_ws_create(otlm_ws* out, int n, int k, int width, int batch_max, unsigne
   for (int l = 1; l < LAYERS; ++l) actb += align256(4 * (size_t)batch_max * d[l]);
   actb += 2 * align256(4 * (size_t)batch_max * dmax);
   bytes += actb + 2 * align256(4 * (size_t)(n + k)) + align256(4 * 2 * LOSS_PARTS) + 256;
+  size_t w16b = 0, zero_elems = 0;
+  int maxp = 0;
+  for (int l = 0; l < LAYERS; ++l) {
+    w->inp[l] = (d[l] + 7) / 8 * 8;
+    w16b += align256(2 * (size_t)d[l + 1] * w->inp[l]);
+    const size_t el = (size_t)d[l + 1] * w->inp[l];
+    zero_elems = zero_elems > el ? zero_elems : el;
+    maxp = maxp > w->inp[l] ? maxp : w->inp[l];
+    w->dmax = w->dmax > d[l + 1] ? w->dmax : d[l + 1];
+  }
+  bytes += w16b + align256(2 * zero_elems) + 4 * align256(2 * (size_t)batch_max * maxp) +
+           align256(4 * (size_t)TC_MAX_SPLITS * batch_max * w->dmax) + 256;
   if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
     delete w;
     return OTLM_ENOMEM;
@@ -120,8 +178,19 @@ int otlm_ws_create(otlm_ws* out, int n, int k, int width, int batch_max, unsigne
   w->stdv = (float*)take(4 * (size_t)(n + k));
   w->part = (float*)take(4 * 2 * LOSS_PARTS);
   w->loss_scale = (float*)take(256);
+  for (int l = 0; l < LAYERS; ++l) w->W16p[l] = (__nv_bfloat16*)take(2 * (size_t)d[l + 1] * w->inp[l]);
+  w->zero16 = (__nv_bfloat16*)take(2 * zero_elems);
+  for (int c = 0; c < 2; ++c) {
+    w->Hhi[c] = (__nv_bfloat16*)take(2 * (size_t)batch_max * maxp);
+    w->Hlo[c] = (__nv_bfloat16*)take(2 * (size_t)batch_max * maxp);
+  }
+  w->Zs = (float*)take(4 * (size_t)TC_MAX_SPLITS * batch_max * w->dmax);
+  w->tc_err = (int*)take(256);
   cudaStream_t s = w->stream;
-  cudaError_t e = cudaMemsetAsync(w->P, 0, 4 * off, s);
+  // the zero lo part of the weights, and zero padding columns of the weights and activations
+  // (never read past the tensor maps' extents, cleared all the same)
+  cudaError_t e = cudaMemsetAsync(w->W16p[0], 0, w16b + align256(2 * zero_elems) + 4 * align256(2 * (size_t)batch_max * maxp), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->P, 0, 4 * off, s);
   for (int l = 0; l < LAYERS && e == cudaSuccess; ++l) {
     const float a = std::sqrt(6.f / (float)(d[l] + d[l + 1]));
     init_kernel<<<1184, 256, 0, s>>>(w->P + w->woff[l], (size_t)d[l + 1] * d[l], a, seed + 0x1000000ull * (l + 1));
@@ -174,6 +243,7 @@ int otlm_ws_set_params(otlm_ws w, const float* in) {
   if (cudaMemcpyAsync(w->P, in, 4 * w->nparams, cudaMemcpyDeviceToDevice, w->stream) != cudaSuccess)
     return OTLM_ECUDA;
   to_bf16_kernel<<<1184, 256, 0, w->stream>>>(w->P, w->P16, w->nparams);
+  w->tc_dirty = true;
   return cudaGetLastError() == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
@@ -197,6 +267,7 @@ int otlm_ws_train_step(otlm_ws w, int batch, const float* y, const float* target
   const float bc1 = 1.f - std::pow(b1, (float)w->step), bc2 = 1.f - std::pow(b2, (float)w->step);
   adamw_kernel<<<1184, 256, 0, w->stream>>>(w->P, w->G, w->M, w->V, w->P16, w->nparams, (float)lr, b1, b2, 1e-8f,
                                             (float)weight_decay, bc1, bc2);
+  w->tc_dirty = true;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, w->loss_scale, 4, cudaMemcpyDeviceToDevice, w->stream);
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
@@ -204,9 +275,9 @@ int otlm_ws_train_step(otlm_ws w, int batch, const float* y, const float* target
 
 int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const float* cold_w, float* g0, float* w0) {
   if (!w || !y || !cold_w || !g0 || !w0 || batch < 1 || batch > w->batch_max || !(eps > 0)) return OTLM_EINVAL;
-  forward(w, batch, y);
+  if (forward_tc(w, batch, y) != cudaSuccess) return OTLM_ECUDA;
   decode_kernel<<<1184, 256, 0, w->stream>>>(w->act[LAYERS], w->mean, w->stdv, batch, w->n, w->k, (float)eps, cold_w,
-                                             g0, w0);
+                                             g0, w0, w->tc_err);
   return cudaGetLastError() == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 

@@ -451,8 +451,11 @@ inline int num_sms() {
 
 // Launch the three-term GEMM: A* [M][lda] (M x Kd used), B* [N][ldb] (N x Kd used); the row
 // pitches are multiples of 16 bytes and the bases 16-byte aligned (checked by the map encoder).
+// Internal linkage on purpose: every translation unit that includes this header registers its
+// own copy of gemm3_kernel, and the dynamic shared-memory attribute has to be set on the copy
+// that the unit launches, so each unit keeps its own "attribute set" flag.
 template <int KIND>
-inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, int lda, const void* B_hi, const void* B_lo,
+static inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, int lda, const void* B_hi, const void* B_lo,
                                 int ldb, int M, int N, int Kd, const GemmArgs& args, cudaStream_t stream) {
   static bool attr = false;
   if (!attr) {
