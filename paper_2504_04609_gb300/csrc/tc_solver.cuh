@@ -34,6 +34,11 @@
 
 namespace otlm {
 
+// Small batches leave the applies with fewer 128 x 128 output tiles than SMs (a single target at
+// n = 8192 has 64), so for batches up to TC_SMALL_BATCH the reduction of each apply is split into up
+// to TC_APPLY_SPLITS ranges whose partial sums are added by tc_split_reduce_kernel.
+constexpr int TC_SMALL_BATCH = 64, TC_APPLY_SPLITS = 16;
+
 struct TcWorkspace {
   __nv_bfloat16 *Khi, *Klo;  // [n][ld]
   __nv_bfloat16 *Vhi, *Vlo;  // [batch][ld], rows in active-slot order (source and target operands)
@@ -51,6 +56,7 @@ struct TcWorkspace {
   float *Rhi, *Rlo;          // [batch][ld] log ratios by slot (B operand of D^T r)
   int ld;                    // row pitch of the [.][n] operands (multiple of 64 elements)
   int kp;                    // row pitch of the [.][k] operands (k_max rounded up to 4)
+  float* ACCP;               // [TC_APPLY_SPLITS][min(batch_max, TC_SMALL_BATCH) x n] split partial sums
 };
 
 // A raw GEMM sum is a sum of positive terms, so it is >= 0.  A row the fix-up recomputed exactly
@@ -87,6 +93,8 @@ inline size_t carve_tc_workspace(void* base, int n_max, int k_max, int batch_max
   w.fix_cap = (unsigned long long)batch_max * n_max;
   w.fix_list = (int2*)take(8 * (size_t)batch_max * n_max);
   w.fix_cnt = (unsigned long long*)take(64);
+  w.ACCP = (float*)take(4 * (size_t)TC_APPLY_SPLITS * (batch_max < TC_SMALL_BATCH ? batch_max : TC_SMALL_BATCH) *
+                        n_max);
   w.kp = kp;
   w.Dhi = (float*)take(4 * (size_t)n_max * kp);
   w.Dlo = (float*)take(4 * (size_t)n_max * kp);
@@ -140,6 +148,26 @@ __global__ void kbuild_kernel(const float* xt, int n, int ld, __nv_bfloat16* Khi
     const __nv_bfloat16 hi = __float2bfloat16_rn(k);
     Khi[(size_t)i * ld + j] = hi;
     Klo[(size_t)i * ld + j] = __float2bfloat16_rn(k - __bfloat162float(hi));
+  }
+}
+
+// Split applies: the problem's sums are the partial-sum planes added in order; sums below FLT_MIN
+// are listed for the fix-up as the GEMM epilogue lists them when the reduction is not split.
+__global__ void tc_split_reduce_kernel(const float* part, int splits, size_t plane, const int* active,
+                                       const int* n_active, int n, float* acc, int2* fix_list,
+                                       unsigned long long* fix_cnt, unsigned long long fix_cap) {
+  const size_t total = (size_t)(*n_active) * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(e / n), i = (int)(e - (size_t)slot * n);
+    const int p = active[slot];
+    const size_t idx = (size_t)p * n + i;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[z * plane + idx];
+    acc[idx] = s;
+    if (!(s >= 1.17549435e-38f)) {
+      const unsigned long long f = atomicAdd(fix_cnt, 1ull);
+      if (f < fix_cap) fix_list[f] = make_int2(p, i);
+    }
   }
 }
 
@@ -575,6 +603,31 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   tc::GemmArgs ga{};
   ga.col_map = ws.active; ga.n_cols = ws.n_active; ga.M = n; ga.N = batch; ga.Kd = n; ga.ld_out = n;
   ga.err = tw.err; ga.fix_list = tw.fix_list; ga.fix_cap = (unsigned long long)batch * n; ga.splits = 1;
+  {
+    const int units = ((n + tc::BM - 1) / tc::BM) * ((batch + tc::BN - 1) / tc::BN);
+    if (batch <= TC_SMALL_BATCH && units < tc::num_sms()) {
+      ga.splits = tc::choose_splits(units, (n + tc::KindTraits<tc::KIND_BF16>::BK - 1) / tc::KindTraits<tc::KIND_BF16>::BK);
+      if (ga.splits > TC_APPLY_SPLITS) ga.splits = TC_APPLY_SPLITS;
+    }
+    ga.split_stride = (size_t)batch * n;
+    if (ga.splits > 1) ga.fix_list = nullptr;  // listed by tc_split_reduce_kernel instead
+  }
+  const int red_grid = (int)(((size_t)batch * n + 255) / 256 < 1184 ? ((size_t)batch * n + 255) / 256 : 1184);
+  // one apply into `acc` (counting underflows into `cnt`): split partial sums are added afterwards
+  auto apply = [&](float* acc, unsigned long long* cnt) -> cudaError_t {
+    ga.out = ga.splits > 1 ? tw.ACCP : acc;
+    ga.fix_cnt = cnt;
+    L.begin(KIND_APPLY);
+    cudaError_t r = tc::launch_gemm3<tc::KIND_BF16>(tw.Khi, tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n, batch, n, ga,
+                                                    L.stream);
+    if (r == cudaSuccess && ga.splits > 1) {
+      tc_split_reduce_kernel<<<red_grid, 256, 0, L.stream>>>(tw.ACCP, ga.splits, ga.split_stride, ws.active,
+                                                              ws.n_active, n, acc, tw.fix_list, cnt, ga.fix_cap);
+      r = cudaGetLastError();
+    }
+    L.end();
+    return r;
+  };
   // D^T r (TF32): M = dictionary columns, N = slots (partial sums by slot), reduction over bins split
   tc::GemmArgs gr{};
   gr.out = mb.NU; gr.n_cols = ws.n_active; gr.M = k; gr.N = batch; gr.Kd = n; gr.ld_out = mb.ldnu; gr.err = tw.err;
@@ -602,11 +655,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     L.begin(KIND_MM);
     TC_ROW_LAUNCH(tc_prep_src_kernel, row_cfg, batch, L.stream, ta);
     L.end();
-    ga.out = tw.ACC_src[it & 1];
-    ga.fix_cnt = tw.fix_cnt;
-    L.begin(KIND_APPLY);
-    e = tc::launch_gemm3<tc::KIND_BF16>(tw.Khi, tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n, batch, n, ga, L.stream);
-    L.end();
+    e = apply(tw.ACC_src[it & 1], tw.fix_cnt);
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
     tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, ga.fix_cap, n, ws.xt,
@@ -635,11 +684,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     L.begin(KIND_MM);
     TC_ROW_LAUNCH(tc_operand_kernel, row_cfg, batch, L.stream, ta);
     L.end();
-    ga.out = tw.ACC_tgt;
-    ga.fix_cnt = tw.fix_cnt + 1;
-    L.begin(KIND_APPLY);
-    e = tc::launch_gemm3<tc::KIND_BF16>(tw.Khi, tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n, batch, n, ga, L.stream);
-    L.end();
+    e = apply(tw.ACC_tgt, tw.fix_cnt + 1);
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
     tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 1, tw.fix_cnt, ga.fix_cap, n, ws.xt,

@@ -135,7 +135,7 @@ def initial_weights(y: np.ndarray, D: np.ndarray) -> np.ndarray:
     return (y.sum(axis=-1)[..., None] / (k * col)) * np.ones(y.shape[:-1] + (k,))
 
 
-# Workload catalogue: the five configurations the solver is measured on, by what they are.
+# Workload catalogue: the configurations the solver is measured on, by what they are.
 WORKLOADS = {
     "single_fp64_n200": dict(id=1, B=1, n=200, k=10, nnz=3, eps=1e-2, datafit="kl", lam=1.0,
                              penalty="l2sq", alpha=1e-3, iters=500, dtype=np.float64),
@@ -150,4 +150,8 @@ WORKLOADS = {
                               iters=2000, tol=1e-5, dtype=np.float32),
     "warmstart_n2048_kl_l2sq": dict(id=5, n=2048, k=64, nnz=5, eps=5e-3, datafit="kl", lam=1.0,
                                     penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
+    # one target on a fine grid: the stored kernel (1 GiB as BF16 hi/lo) is streamed from HBM twice
+    # per iteration; the same datafit and penalty as the n=4096 batch
+    "hbm_single_n16384_l2_l2sq": dict(id=6, B=1, n=16384, k=128, nnz=5, eps=1e-2, datafit="l2", lam=1.0,
+                                      penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
 }

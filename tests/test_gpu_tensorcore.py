@@ -43,8 +43,9 @@ def _oracle(d, p, eps, lam, alpha, datafit, penalty, iters, tol=0.0):
     ("tv", "l1", 5e-2, 1.0, 1e-2),
 ])
 def test_tensorcore_trajectory_parity_small(datafit, penalty, eps, lam, alpha):
-    """9 problems (one partial 256-column tile), n = 300 (three 128-row tiles, ragged; reduction
-    over five 64-wide blocks with a zero-filled tail), k = 12, 30 iterations."""
+    """9 problems (one partial 128-column tile; a batch this small splits each apply's reduction),
+    n = 300 (three 128-row tiles, ragged; reduction over five 64-wide blocks with a zero-filled
+    tail), k = 12, 30 iterations."""
     d = spectra.batch(31, 9, 300, 12, 3)
     r = _solve(d, eps, lam, alpha, datafit, penalty, 30)
     assert np.all(r["status"] == api.MAX_ITER) and np.all(r["iters"] == 30)
@@ -101,3 +102,15 @@ def test_tensorcore_underflowing_rows_are_fixed_up_exactly():
         o = _oracle(d, p, 1e-3, 1.0, 1e-3, "kl", "l2sq", 20)
         assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
         assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
+
+
+def test_single_target_streamed_kernel_parity():
+    """One target at n = 8192 (the stored kernel, 256 MiB as BF16 hi/lo, is larger than L2 and
+    streamed by every apply; the single column splits each apply's reduction over 16 ranges),
+    k = 64, 6 iterations against the oracle's trajectory."""
+    d = spectra.batch(34, 1, 8192, 64, 5)
+    r = _solve(d, 1e-2, 1.0, 1e-3, "l2", "l2sq", 6)
+    assert r["status"][0] == api.MAX_ITER and r["iters"][0] == 6
+    o = _oracle(d, 0, 1e-2, 1.0, 1e-3, "l2", "l2sq", 6)
+    assert rel_l1(r["w"][0], o["w"]) <= TOL, rel_l1(r["w"][0], o["w"])
+    assert rel_l1(r["t"][0], o["t"]) <= TOL, rel_l1(r["t"][0], o["t"])
