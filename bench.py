@@ -656,7 +656,9 @@ def run_single_hbm(args, rank, world, local_rank):
                    "path": "tensor-core applies with the reduction split over 16 ranges (small batch)",
                    "l2": "the stored kernel (1 GiB) is larger than L2", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "gemm3_kernel<KIND_BF16> + tc_split_reduce_kernel (one apply)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": 1081.6e6, "traffic_note": "GEMM 1079.5 MB read + 1.2 MB written, split reduce "
+                                                          "0.9 MB read (ncu, profiles/hbm_single_n16384.md)",
                      "launch_ms_avg": launch_ms, "bytes_per_launch": 4.0 * n * n,
                      "peak_basis": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in _peaks() else "fallback 6.8 TB/s"},
         "kernel_ms_per_step": {kk: v[0] for kk, v in timing.items()},
