@@ -575,7 +575,8 @@ __global__ void prep_kernel(PrepArgs<T> A) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nk = (size_t)A.n * A.k, bn = (size_t)A.batch * A.n, bk = (size_t)A.batch * A.k;
-  for (size_t e = tid; e < (size_t)A.n; e += stride) A.xt[e] = A.x[e] * A.xscale;
+  if (A.x)  // NULL when the cost is given as a dense matrix
+    for (size_t e = tid; e < (size_t)A.n; e += stride) A.xt[e] = A.x[e] * A.xscale;
   for (size_t e = tid; e < nk; e += stride) {
     const size_t i = e / A.k, j = e - i * A.k;
     A.Dt[j * A.n + i] = A.D[e];

@@ -78,9 +78,10 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
   return sp;
 }
 
+// C: dense cost [n][n] (tensor-core handles only) or NULL for the grid cost from x
 template <typename T>
-int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* D, const void* y, void* w, void* g,
-              void* t_out, int* iters_out, void* err_out, int* status_out) {
+int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* C, const void* D, const void* y, void* w,
+              void* g, void* t_out, int* iters_out, void* err_out, int* status_out) {
   Workspace<T> ws;
   otlm::carve_workspace<T>(h->ws, h->cfg.n_max, h->cfg.k_max, h->cfg.batch_max, &ws);
   Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
@@ -93,7 +94,7 @@ int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* D, 
     otlm::TcMMBuf mb;
     otlm::carve_tc_mm(static_cast<char*>(h->ws) + base + tcb, h->cfg.k_max, h->cfg.batch_max, &mb);
     e = otlm::solve_device_tc(L, reinterpret_cast<const Workspace<float>&>(ws), tw, mb, sp, (const float*)x,
-                              (const float*)D, (const float*)y, (float*)w, (float*)g, (float*)t_out, iters_out,
+                              (const float*)C, (const float*)D, (const float*)y, (float*)w, (float*)g, (float*)t_out, iters_out,
                               (float*)err_out, status_out);
   } else {
     e = otlm::solve_device<T>(L, ws, sp, (const T*)x, (const T*)D, (const T*)y, (T*)w, (T*)g, (T*)t_out, iters_out,
@@ -275,8 +276,19 @@ int otlm_solve(otlm_handle h, int batch, int n, int k, const void* x, const void
   if (rc != OTLM_OK) return rc;
   const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
   if (h->cfg.precision == OTLM_PREC_FP64)
-    return run_solve<double>(h, sp, x, D, y, w, g, t_out, iters_out, err_out, status_out);
-  return run_solve<float>(h, sp, x, D, y, w, g, t_out, iters_out, err_out, status_out);
+    return run_solve<double>(h, sp, x, nullptr, D, y, w, g, t_out, iters_out, err_out, status_out);
+  return run_solve<float>(h, sp, x, nullptr, D, y, w, g, t_out, iters_out, err_out, status_out);
+}
+
+int otlm_solve_cost(otlm_handle h, int batch, int n, int k, const float* C, const float* D, const float* y,
+                    double eps, double lam, double alpha, float* w, float* g, float* t_out, int* iters_out,
+                    float* err_out, int* status_out) {
+  if (!h || !C || !D || !y || !w) return OTLM_EINVAL;
+  if (h->cfg.precision != OTLM_PREC_BF16_TC) return OTLM_EUNSUPPORTED;
+  int rc = check_problem(h, batch, n, k, eps, lam, alpha);
+  if (rc != OTLM_OK) return rc;
+  const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
+  return run_solve<float>(h, sp, nullptr, C, D, y, w, g, t_out, iters_out, err_out, status_out);
 }
 
 int otlm_solve_host(otlm_handle h, int batch, int n, int k, const void* x, const void* D, const void* y, double eps,

@@ -41,6 +41,10 @@ constexpr int EPI_BYTES = 64 * BM * 4;                    // 32 KiB: 64 output c
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + 128;
 constexpr int THREADS = 256;
 constexpr uint32_t TMEM_COLS = 2 * BN;                    // two accumulators (double buffer)
+// Sums below 2^-90 (relative to the operand's shift) are listed for an exact recomputation: their
+// terms' BF16 lo parts (2^-9 below the hi parts) and hi x lo products approach FP32's subnormal
+// range, where they flush to zero; above 2^-90 every term that matters keeps all its bits.
+constexpr float EXACT_BELOW = 8.0779356694631609e-28f;    // 2^-90
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 constexpr unsigned long long WAIT_NS = 2000000000ull;    // bounded waits: 2 s
 
@@ -145,7 +149,7 @@ struct GemmArgs {
   const int* n_cols;   // number of valid columns on the device; nullptr: N
   int M, N, Kd, ld_out;
   int* err;            // first error code of any CTA (0: none)
-  int2* fix_list;                // sums below FLT_MIN as (output row, row); nullptr: not recorded
+  int2* fix_list;                // sums below EXACT_BELOW as (output row, row); nullptr: not recorded
   unsigned long long* fix_cnt;   // entries this launch appended to fix_list
   unsigned long long fix_cap;    // capacity of fix_list (M x N covers every element)
   int flush_tiny;      // store sums below FLT_MIN as 0
@@ -348,13 +352,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint32_t v[16];
           __syncwarp();
           tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN + c0), v);
-          unsigned low = 0;  // columns whose sum is below FLT_MIN (including an empty sum)
+          unsigned low = 0;  // columns whose sum is below EXACT_BELOW (including an empty sum)
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const int col = n0 + c0 + c;
             const bool in = col < ncols && row < g.M;
             float val = __uint_as_float(v[c]);
-            low |= (in && !(val >= 1.17549435e-38f)) ? (1u << c) : 0u;
+            low |= (in && !(val >= EXACT_BELOW)) ? (1u << c) : 0u;
             if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
             if (g.bulk) {
               stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;

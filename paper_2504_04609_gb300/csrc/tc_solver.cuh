@@ -20,10 +20,11 @@
 //   gemm      : target sums into ACC_tgt (BF16)
 // dtr, wupd and dw run over the slots as they were before compaction, so the operands that the
 // violation and wupd kernels write row by slot need no re-gathering.
-// A sum that underflows (a row whose significant terms all lie more than ~2^-126 below the
-// problem's largest term, e.g. far from the support under a KL or TV datafit) is listed by the GEMM
-// epilogue and recomputed exactly (two-pass log-sum-exp for that row) by tc_fixup_kernel, which
-// runs after each apply and spreads the listed rows over the whole GPU.
+// A sum below 2^-90 of the problem's shift (a row whose significant terms all lie far below the
+// problem's largest term, e.g. far from the support under a KL or TV datafit; there the BF16 lo
+// parts and products reach FP32's subnormal range and flush, down to a sum that underflows
+// entirely) is listed by the GEMM epilogue and recomputed exactly (two-pass log-sum-exp for that
+// row) by tc_fixup_kernel, which runs after each apply and spreads the listed rows over the GPU.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -41,6 +42,7 @@ constexpr int TC_SMALL_BATCH = 64, TC_APPLY_SPLITS = 16;
 
 struct TcWorkspace {
   __nv_bfloat16 *Khi, *Klo;  // [n][ld]
+  __nv_bfloat16 *Kthi, *Ktlo;  // [n][ld] K^T, built only for a dense (possibly non-symmetric) cost
   __nv_bfloat16 *Vhi, *Vlo;  // [batch][ld], rows in active-slot order (source and target operands)
   float* ACC_src[2];         // [batch][n] raw source sums, ping-pong by iteration parity
   float* ACC_tgt;            // [batch][n] raw target sums
@@ -81,6 +83,8 @@ inline size_t carve_tc_workspace(void* base, int n_max, int k_max, int batch_max
   w.ld = ld;
   w.Khi = (__nv_bfloat16*)take(2 * (size_t)n_max * ld);
   w.Klo = (__nv_bfloat16*)take(2 * (size_t)n_max * ld);
+  w.Kthi = (__nv_bfloat16*)take(2 * (size_t)n_max * ld);
+  w.Ktlo = (__nv_bfloat16*)take(2 * (size_t)n_max * ld);
   w.Vhi = (__nv_bfloat16*)take(2 * (size_t)batch_max * ld);
   w.Vlo = (__nv_bfloat16*)take(2 * (size_t)batch_max * ld);
   w.ACC_src[0] = (float*)take(4 * (size_t)batch_max * n_max);
@@ -151,8 +155,9 @@ __global__ void kbuild_kernel(const float* xt, int n, int ld, __nv_bfloat16* Khi
   }
 }
 
-// Split applies: the problem's sums are the partial-sum planes added in order; sums below FLT_MIN
-// are listed for the fix-up as the GEMM epilogue lists them when the reduction is not split.
+// Split applies: the problem's sums are the partial-sum planes added in order; sums below
+// tc::EXACT_BELOW are listed for the fix-up as the GEMM epilogue lists them when the reduction is
+// not split.
 __global__ void tc_split_reduce_kernel(const float* part, int splits, size_t plane, const int* active,
                                        const int* n_active, int n, float* acc, int2* fix_list,
                                        unsigned long long* fix_cnt, unsigned long long fix_cap) {
@@ -164,25 +169,76 @@ __global__ void tc_split_reduce_kernel(const float* part, int splits, size_t pla
     float s = 0.f;
     for (int z = 0; z < splits; ++z) s += part[z * plane + idx];
     acc[idx] = s;
-    if (!(s >= 1.17549435e-38f)) {
+    if (!(s >= tc::EXACT_BELOW)) {
       const unsigned long long f = atomicAdd(fix_cnt, 1ull);
       if (f < fix_cap) fix_list[f] = make_int2(p, i);
     }
   }
 }
 
+// K = 2^{-C_ij c} (c = 1 / (eps ln2)) and its transpose from a dense cost C [n][n] (row i = source
+// bin, column j = target bin; +inf allowed: no transport), both as BF16 hi/lo [n][ld].  32 x 32
+// tiles through shared memory keep the reads of C and the writes of both matrices coalesced.
+__global__ void __launch_bounds__(256) kdense_kernel(const float* C, int n, int ld, float c, __nv_bfloat16* Khi,
+                                                     __nv_bfloat16* Klo, __nv_bfloat16* Kthi, __nv_bfloat16* Ktlo) {
+  __shared__ float tile[32][33];
+  const int tiles = (n + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x) {
+    const int i0 = (t / tiles) * 32, j0 = (t % tiles) * 32;
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int i = i0 + r, j = j0 + tx;
+      float kv = 0.f;
+      if (i < n && j < n) {
+        kv = Prec<float>::exp2(-C[(size_t)i * n + j] * c);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(kv);
+        Khi[(size_t)i * ld + j] = hi;
+        Klo[(size_t)i * ld + j] = __float2bfloat16_rn(kv - __bfloat162float(hi));
+      }
+      tile[r][tx] = kv;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {  // row j0 + r of K^T = column j0 + r of K
+      const int j = j0 + r, i = i0 + tx;
+      if (i < n && j < n) {
+        const float kv = tile[tx][r];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(kv);
+        Kthi[(size_t)j * ld + i] = hi;
+        Ktlo[(size_t)j * ld + i] = __float2bfloat16_rn(kv - __bfloat162float(hi));
+      }
+    }
+  }
+}
+
 // Exact fix-up of the sums a GEMM listed as underflowed, one CTA of 256 threads per listed
 // (problem p, row i) so that a row costs a few memory round trips, not n / 32:
-//   L = log2 sum_j 2^(in_pj - (xt_i - xt_j)^2)     (two passes over j: max, then sum)
+//   L = log2 sum_j 2^(in_pj - cost_ij)     (two passes over j: max, then sum; cost in log2 units)
 // stored as the negative offset L - M_p (decoded by tc_log2_sum); an empty sum stays 0.  in = G2
 // and M = Msrc for the source sums, in = F2 and M = Mtgt for the target sums.  The source and
 // target GEMMs count into fix_cnt[0] and fix_cnt[1]; each fix-up reads its own count and clears the
 // other, which the next GEMM appends to.  With nothing listed every CTA leaves after one load.
 constexpr int TC_FIX_GRID = 4 * 152;
 
+// The exponent of term j of row i in log2 units: the grid cost (xt_i - xt_j)^2, or a dense cost
+// C c read along row i (trans = 0) or column i (trans = 1: a target sum of the transposed kernel).
+struct TcCost {
+  const float* xt;  // scaled grid, when C is NULL
+  const float* C;   // dense cost [n][n] or NULL
+  float c;          // 1 / (eps ln2)
+  int trans;
+  __device__ __forceinline__ float operator()(int i, int j, int n) const {
+    if (!C) {
+      const float d = xt[i] - xt[j];
+      return d * d;
+    }
+    return (trans ? C[(size_t)j * n + i] : C[(size_t)i * n + j]) * c;
+  }
+};
+
 __global__ void __launch_bounds__(256) tc_fixup_kernel(const int2* list, const unsigned long long* cnt,
                                                        unsigned long long* cnt_next, unsigned long long cap, int n,
-                                                       const float* xt, const float* in, float* acc,
+                                                       TcCost cost, const float* in, float* acc,
                                                        const float* mshift) {
   using P = Prec<float>;
   __shared__ float red[32];
@@ -191,21 +247,14 @@ __global__ void __launch_bounds__(256) tc_fixup_kernel(const int2* list, const u
   for (unsigned long long e = blockIdx.x; e < c; e += gridDim.x) {
     const int2 pi = list[e];
     const float* inp = in + (size_t)pi.x * n;
-    const float xi = xt[pi.y];
     float mx = -CUDART_INF_F;
 #pragma unroll 4
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const float d = xi - xt[j];
-      mx = fmaxf(mx, inp[j] - d * d);
-    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, inp[j] - cost(pi.y, j, n));
     mx = block_max(mx, red);
     float sum = 0.f;
     if (mx > -CUDART_INF_F) {
 #pragma unroll 4
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const float d = xi - xt[j];
-        sum += P::exp2((inp[j] - mx) - d * d);
-      }
+      for (int j = threadIdx.x; j < n; j += blockDim.x) sum += P::exp2((inp[j] - mx) - cost(pi.y, j, n));
     }
     sum = block_sum(sum, red);
     if (threadIdx.x == 0) {
@@ -561,7 +610,8 @@ __global__ void tc_finalize_kernel(FinArgs<float> F, const float* ACC_tgt, const
 // Run Algorithm 1 with tensor-core applies and dictionary contractions (float buffers; x, D, y, w,
 // g as in solve_device).  Returns cudaErrorLaunchTimeout when a GEMM reported an expired wait.
 inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, const TcWorkspace& tw,
-                                   const TcMMBuf& mb, const SolveParams& sp, const float* x, const float* D,
+                                   const TcMMBuf& mb, const SolveParams& sp, const float* x, const float* C,
+                                   const float* D,
                                    const float* y, float* w, float* g, float* t_out, int* iters_out, float* err_out,
                                    int* status_out) {
   const int batch = sp.batch, n = sp.n, k = sp.k;
@@ -581,7 +631,10 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   colsum_kernel<float><<<(k + 7) / 8, 256, 0, L.stream>>>(ws.Dt, ws.xcol, n, k);
   L.end();
   L.begin(KIND_OTHER);
-  kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo);
+  if (C)
+    kdense_kernel<<<2048, 256, 0, L.stream>>>(C, n, tw.ld, float(1.0 / eps_ln2), tw.Khi, tw.Klo, tw.Kthi, tw.Ktlo);
+  else
+    kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo);
   L.end();
   L.begin(KIND_OTHER);
   tc_dsplit_kernel<<<1184, 256, 0, L.stream>>>(D, n, k, tw.kp, tw.ld, tw.Dhi, tw.Dlo, tw.Dthi, tw.Dtlo);
@@ -612,14 +665,17 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     ga.split_stride = (size_t)batch * n;
     if (ga.splits > 1) ga.fix_list = nullptr;  // listed by tc_split_reduce_kernel instead
   }
+  const TcCost cost_src{ws.xt, C, float(1.0 / eps_ln2), 0}, cost_tgt{ws.xt, C, float(1.0 / eps_ln2), 1};
   const int red_grid = (int)(((size_t)batch * n + 255) / 256 < 1184 ? ((size_t)batch * n + 255) / 256 : 1184);
   // one apply into `acc` (counting underflows into `cnt`): split partial sums are added afterwards
-  auto apply = [&](float* acc, unsigned long long* cnt) -> cudaError_t {
+  // the source apply reads K, the target apply K^T (the same matrix for the symmetric grid cost)
+  auto apply = [&](float* acc, unsigned long long* cnt, bool target) -> cudaError_t {
     ga.out = ga.splits > 1 ? tw.ACCP : acc;
     ga.fix_cnt = cnt;
+    const bool kt = target && C;
     L.begin(KIND_APPLY);
-    cudaError_t r = tc::launch_gemm3<tc::KIND_BF16>(tw.Khi, tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n, batch, n, ga,
-                                                    L.stream);
+    cudaError_t r = tc::launch_gemm3<tc::KIND_BF16>(kt ? tw.Kthi : tw.Khi, kt ? tw.Ktlo : tw.Klo, tw.ld, tw.Vhi,
+                                                    tw.Vlo, tw.ld, n, batch, n, ga, L.stream);
     if (r == cudaSuccess && ga.splits > 1) {
       tc_split_reduce_kernel<<<red_grid, 256, 0, L.stream>>>(tw.ACCP, ga.splits, ga.split_stride, ws.active,
                                                               ws.n_active, n, acc, tw.fix_list, cnt, ga.fix_cap);
@@ -655,11 +711,11 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     L.begin(KIND_MM);
     TC_ROW_LAUNCH(tc_prep_src_kernel, row_cfg, batch, L.stream, ta);
     L.end();
-    e = apply(tw.ACC_src[it & 1], tw.fix_cnt);
+    e = apply(tw.ACC_src[it & 1], tw.fix_cnt, false);
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
-    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, ga.fix_cap, n, ws.xt,
-                                                    ws.G2, tw.ACC_src[it & 1], tw.Msrc[it & 1]);
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, ga.fix_cap, n,
+                                                    cost_src, ws.G2, tw.ACC_src[it & 1], tw.Msrc[it & 1]);
     L.end();
     L.begin(KIND_MM);
     TC_ROW_LAUNCH(tc_violation_kernel, row_cfg, batch, L.stream, ta);
@@ -684,11 +740,11 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     L.begin(KIND_MM);
     TC_ROW_LAUNCH(tc_operand_kernel, row_cfg, batch, L.stream, ta);
     L.end();
-    e = apply(tw.ACC_tgt, tw.fix_cnt + 1);
+    e = apply(tw.ACC_tgt, tw.fix_cnt + 1, true);
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
-    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 1, tw.fix_cnt, ga.fix_cap, n, ws.xt,
-                                                    ws.F2, tw.ACC_tgt, tw.Mtgt);
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 1, tw.fix_cnt, ga.fix_cap, n,
+                                                    cost_tgt, ws.F2, tw.ACC_tgt, tw.Mtgt);
     L.end();
     if ((it + 1) % sp.poll_every == 0) {
       e = cudaMemcpyAsync(L.host_flag, ws.n_active, sizeof(int), cudaMemcpyDeviceToHost, L.stream);

@@ -21,7 +21,7 @@ DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3}
 PENALTY = {"none": 0, "l1": 1, "l2sq": 2}
 PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 
-EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_host", "otlm_objective",
+EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm_solve_host", "otlm_objective",
            "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged",
            "otlm_tune_ragged", "otlm_ws_create", "otlm_ws_destroy", "otlm_ws_num_params", "otlm_ws_set_normalization",
            "otlm_ws_get_params", "otlm_ws_set_params", "otlm_ws_gradients", "otlm_ws_train_step", "otlm_ws_predict",
@@ -55,6 +55,8 @@ def lib() -> ctypes.CDLL:
         L.otlm_solve.restype = i
         L.otlm_solve_host.argtypes = solve_args
         L.otlm_solve_host.restype = i
+        L.otlm_solve_cost.argtypes = solve_args
+        L.otlm_solve_cost.restype = i
         L.otlm_objective.argtypes = [vp, i, i, i, vp, vp, vp, d, d, d, vp, vp, vp, vp]
         L.otlm_objective.restype = i
         L.otlm_launch_count.argtypes = [vp]
@@ -167,6 +169,16 @@ class Handle:
         rc = lib().otlm_solve(self._h, B, n, k, _ptr(x), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),
                               _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
         _check(rc, "otlm_solve")
+        return SolveResult(w, g, t_out, iters, err, status)
+
+    def solve_cost(self, C, D, y, eps, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):
+        """otlm_solve_cost: a dense cost C [n][n] (torch CUDA tensor; row = source bin, column = target
+        bin, need not be symmetric, +inf forbids a pair) instead of a grid; tensor-core handles only."""
+        B, n = y.shape
+        k = D.shape[1]
+        rc = lib().otlm_solve_cost(self._h, B, n, k, _ptr(C), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),
+                                   _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
+        _check(rc, "otlm_solve_cost")
         return SolveResult(w, g, t_out, iters, err, status)
 
     def solve_host(self, x, D, y, eps, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):

@@ -114,3 +114,81 @@ def test_single_target_streamed_kernel_parity():
     o = _oracle(d, 0, 1e-2, 1.0, 1e-3, "l2", "l2sq", 6)
     assert rel_l1(r["w"][0], o["w"]) <= TOL, rel_l1(r["w"][0], o["w"])
     assert rel_l1(r["t"][0], o["t"]) <= TOL, rel_l1(r["t"][0], o["t"])
+
+
+def _dense_cost(kind, x):
+    xs = np.asarray(x, dtype=np.float64)
+    if kind == "nonstationary":  # rho (x_i - x_j)^2 / x_i^2 on a grid shifted away from 0: C != C^T
+        g = 0.25 + xs
+        return 0.5 * (g[:, None] - g[None, :]) ** 2 / g[:, None] ** 2
+    if kind == "truncated":  # the squared distance, forbidden beyond 0.3
+        C = (xs[:, None] - xs[None, :]) ** 2
+        C[np.abs(xs[:, None] - xs[None, :]) > 0.3] = np.inf
+        return C
+    return (xs[:, None] - xs[None, :]) ** 2
+
+
+@pytest.mark.parametrize("kind,datafit,penalty,eps", [
+    ("nonstationary", "kl", "l2sq", 2e-2),
+    ("nonstationary", "l2", "l1", 2e-2),
+    ("truncated", "kl", "l2sq", 1e-2),
+])
+def test_dense_cost_trajectory_parity(kind, datafit, penalty, eps):
+    """otlm_solve_cost with a cost matrix instead of a grid: the source apply uses K, the target
+    apply K^T (a non-symmetric cost makes them differ; +inf entries forbid pairs).  7 problems,
+    n = 300, k = 12, 25 iterations against the oracle's trajectory on the same FP64 cost.  Under
+    the truncated cost some KL targets leave a source bin with no reachable target bin (a_i = 0
+    while s_i > 0), where the MM step is undefined: the oracle returns NaN there and the solver
+    must report OTLM_NONFINITE for exactly those problems."""
+    d = spectra.batch(35, 7, 300, 12, 3)
+    C64 = _dense_cost(kind, d["x"])
+    lam, alpha, T = 1.0, 1e-3 if penalty == "l2sq" else 1e-2, 25
+    dev = "cuda"
+    C = torch.tensor(C64.astype(np.float32), device=dev)
+    D, y = (torch.tensor(d[k], device=dev) for k in ("D", "y"))
+    w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=torch.float32, device=dev)
+    B, n = y.shape
+    h = api.Handle(n, 12, B, "bf16tc", datafit, penalty, T, 0.0, poll_every=4)
+    t = torch.empty_like(y)
+    it = torch.empty(B, dtype=torch.int32, device=dev)
+    st = torch.empty(B, dtype=torch.int32, device=dev)
+    h.solve_cost(C, D, y, eps, lam, alpha, w, None, t, it, None, st)
+    torch.cuda.synchronize()
+    h.close()
+    status = st.cpu().numpy()
+    compared = 0
+    for p in range(B):
+        yp = d["y"][p].astype(np.float64)
+        o = oracle.solve_log(C64, d["D"].astype(np.float64), yp, eps, lam, alpha, datafit, penalty,
+                             spectra.initial_weights(yp, d["D"].astype(np.float64)), T)
+        if not np.all(np.isfinite(o["w"])):
+            assert status[p] == api.NONFINITE, (p, status[p])
+            continue
+        assert status[p] == api.MAX_ITER, (p, status[p])
+        assert rel_l1(w[p].cpu().numpy(), o["w"]) <= TOL, (p, rel_l1(w[p].cpu().numpy(), o["w"]))
+        assert rel_l1(t[p].cpu().numpy(), o["t"]) <= TOL, (p, rel_l1(t[p].cpu().numpy(), o["t"]))
+        compared += 1
+    assert compared >= 5
+
+
+def test_dense_cost_of_the_grid_matches_the_grid_solve():
+    """The squared-distance cost given as a matrix reproduces the grid solve (both within the 1e-5
+    bar of each other); a non-tensor-core handle refuses the dense cost."""
+    d = spectra.batch(36, 5, 256, 8, 3)
+    g = _solve(d, 1e-2, 1.0, 1e-3, "l2", "l2sq", 20)
+    dev = "cuda"
+    C = torch.tensor(_dense_cost("grid", d["x"]).astype(np.float32), device=dev)
+    D, y = (torch.tensor(d[k], device=dev) for k in ("D", "y"))
+    w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=torch.float32, device=dev)
+    t = torch.empty_like(y)
+    h = api.Handle(256, 8, 5, "bf16tc", "l2", "l2sq", 20, 0.0, poll_every=4)
+    h.solve_cost(C, D, y, 1e-2, 1.0, 1e-3, w, None, t)
+    torch.cuda.synchronize()
+    h.close()
+    for p in range(5):
+        assert rel_l1(w[p].cpu().numpy(), g["w"][p]) <= TOL
+        assert rel_l1(t[p].cpu().numpy(), g["t"][p]) <= TOL
+    h32 = api.Handle(256, 8, 5, "fp32", "l2", "l2sq", 20, 0.0)
+    with pytest.raises(api.OTLMError):
+        h32.solve_cost(C, D, y, 1e-2, 1.0, 1e-3, w)
+    h32.close()
