@@ -131,7 +131,7 @@ int otlm_solve(otlm_handle h, int batch, int n, int k,
 /* Same as otlm_solve for a cost given as a dense matrix instead of a grid: C [n][n] (device,
  * row-major, FP32) is the cost of moving mass from source bin i (row) to target bin j (column),
  * shared by the batch; it need not be symmetric (e.g. the non-stationary cost rho (x_i - x_j)^2 /
- * x_i^2 of the paper's application section), and +inf forbids a pair (a truncated cost).  Both
+ * x_i^2 of the muonic X-ray spectra appendix), and +inf forbids a pair (a truncated cost).  Both
  * kernel applies of Algorithm 1 follow Q_ij = u2_i K_ij u1_j with K = exp(-C / eps): the source
  * apply uses K, the target apply K^T, built once per call (BF16 hi/lo) in the workspace.
  * Tensor-core handles only (OTLM_PREC_BF16_TC; otherwise OTLM_EUNSUPPORTED); errors as

@@ -121,6 +121,11 @@ def _dense_cost(kind, x):
     if kind == "nonstationary":  # rho (x_i - x_j)^2 / x_i^2 on a grid shifted away from 0: C != C^T
         g = 0.25 + xs
         return 0.5 * (g[:, None] - g[None, :]) ** 2 / g[:, None] ** 2
+    if kind == "muonic":  # the non-stationary cost truncated at a largest shift (both at once)
+        g = 0.25 + xs
+        C = 0.5 * (g[:, None] - g[None, :]) ** 2 / g[:, None] ** 2
+        C[np.abs(g[:, None] - g[None, :]) > 0.3] = np.inf
+        return C
     if kind == "truncated":  # the squared distance, forbidden beyond 0.3
         C = (xs[:, None] - xs[None, :]) ** 2
         C[np.abs(xs[:, None] - xs[None, :]) > 0.3] = np.inf
@@ -132,6 +137,7 @@ def _dense_cost(kind, x):
     ("nonstationary", "kl", "l2sq", 2e-2),
     ("nonstationary", "l2", "l1", 2e-2),
     ("truncated", "kl", "l2sq", 1e-2),
+    ("muonic", "tv", "l1", 2e-2),
 ])
 def test_dense_cost_trajectory_parity(kind, datafit, penalty, eps):
     """otlm_solve_cost with a cost matrix instead of a grid: the source apply uses K, the target
