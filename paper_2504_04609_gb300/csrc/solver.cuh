@@ -139,18 +139,46 @@ template <typename T> struct TileFor;
 #endif
 template <> struct TileFor<float> {
   using type = ApplyTile<float, OTLM_F32_RB, OTLM_F32_RI, OTLM_F32_WB, 1, OTLM_F32_TJ>;
+  // small batches x grids: half the rows per CTA, twice the CTAs, half the accumulators per thread
+  using small = ApplyTile<float, OTLM_F32_RB, OTLM_F32_RI / 2, OTLM_F32_WB, 1, OTLM_F32_TJ>;
 };
 template <> struct TileFor<double> { using type = ApplyTile<double, 2, 2, 2, 2, 32>; };
 
 // first = true: no previous sums exist yet, shift by the diagonal term.
-template <typename T, int EPI>
-void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n) {
-  using Cfg = typename TileFor<T>::type;
+inline int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 152;
+  }
+  return sms;
+}
+
+template <typename T, typename Cfg, int EPI>
+void launch_apply_cfg(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n) {
   const dim3 grid((n + Cfg::TI - 1) / Cfg::TI, (batch + Cfg::TB - 1) / Cfg::TB);
   L.begin(KIND_APPLY);
   if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG><<<grid, Cfg::NT, 0, L.stream>>>(a);
   else apply_kernel<T, Cfg, EPI, SHIFT_PREV><<<grid, Cfg::NT, 0, L.stream>>>(a);
   L.end();
+}
+
+// The FP32 apply takes the half-height tile when the default tile would give fewer than eight CTAs
+// per SM (at n = 1024 x 1024 problems it gives 512 CTAs, 3.4 per SM at four resident: a quarter of
+// the warps the exponent unit needs to stay busy).
+template <typename T, int EPI>
+void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n) {
+  using Cfg = typename TileFor<T>::type;
+  if constexpr (sizeof(T) == 4) {
+    const long long ctas = (long long)((n + Cfg::TI - 1) / Cfg::TI) * ((batch + Cfg::TB - 1) / Cfg::TB);
+    if (ctas < 8LL * sm_count()) {
+      launch_apply_cfg<T, typename TileFor<T>::small, EPI>(L, a, first, batch, n);
+      return;
+    }
+  }
+  launch_apply_cfg<T, Cfg, EPI>(L, a, first, batch, n);
 }
 
 template <typename T>

@@ -99,8 +99,10 @@ def test_fp64_parity_matches_oracle_tightly(datafit, penalty, eps, lam, alpha):
 
 def test_stopping_rule_matches_oracle():
     """tol = 1e-5: every problem stops at the oracle's iteration (a problem whose violation sits
-    within 0.2 % of tol at the deciding check may differ by one), and its state matches the oracle
-    run for the GPU's own iteration count."""
+    within 1 % of tol at the deciding check may differ by one: each bin's ratio a_new / a_old is an
+    FP32 sum of n = 256 terms, ~sqrt(n) 2^-24 = 1e-6 of noise against |ratio - 1| ~ 1e-5, so the
+    FP32 violation resolves tol to about 1 %), and its state matches the oracle run for the GPU's
+    own iteration count."""
     d = spectra.batch(13, 6, 256, 16, 3)
     eps, lam, alpha = 5e-3, 1.0, 1e-2
     r = _gpu_solve(d, eps, lam, alpha, "kl", "l1", 2000, tol=1e-5)
@@ -109,7 +111,7 @@ def test_stopping_rule_matches_oracle():
         gi = int(r["iters"][p])
         assert r["status"][p] == api.CONVERGED
         if gi != o["iters"]:
-            near = np.abs(o["err_hist"] / 1e-5 - 1) < 2e-3
+            near = np.abs(o["err_hist"] / 1e-5 - 1) < 1e-2
             assert abs(gi - o["iters"]) == 1 and near.any(), (p, gi, o["iters"])
         o2 = _oracle(d, p, eps, lam, alpha, "kl", "l1", gi)
         assert rel_l1(r["w"][p], o2["w"]) <= TOL32
