@@ -259,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
     peak_tf = float(peaks.get("bf16_tflops_sustained", 1700.0))
     roofline = {"bound": "tensor", "kernel": "gemm3_kernel<KIND_BF16> (tcgen05 K V^T, BF16 hi/lo, FP32 accumulate)",
                 "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": 586.6e6, "launch_ms_avg": g_ms / max(g_cnt, 1),
+                "traffic": 574.0e6, "launch_ms_avg": g_ms / max(g_cnt, 1),
                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained",
                 "issued_tensor_tflops": 3 * achieved_tf, "issued_frac": 3 * achieved_tf / peak_tf,
@@ -663,7 +663,7 @@ def run_single_hbm(args, rank, world, local_rank):
                    "l2": "the stored kernel (1 GiB) is larger than L2", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "gemm3_kernel<KIND_BF16> + tc_split_reduce_kernel (one apply)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": 1081.6e6, "traffic_note": "GEMM 1079.5 MB read + 1.2 MB written, split reduce "
+                     "traffic": 1082.8e6, "traffic_note": "GEMM 1081.2 MB read + 0.8 MB written, split reduce "
                                                           "0.9 MB read (ncu, profiles/hbm_single_n16384.md)",
                      "launch_ms_avg": launch_ms, "bytes_per_launch": 4.0 * n * n,
                      "peak_basis": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in _peaks() else "fallback 6.8 TB/s"},
