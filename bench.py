@@ -47,6 +47,31 @@ def _peaks():
 
 
 # ------------------------------------------------------------------------------------------------
+# replicas: each rank solves its own shard of the workload's problem stream; the only cross-rank
+# steps are the timing barrier and the max of the timings (no collective on the data path)
+# ------------------------------------------------------------------------------------------------
+
+def shard_first(rank: int, per_rank: int) -> int:
+    """Index of rank `rank`'s first problem: ranks solve disjoint, consecutive shards."""
+    return rank * per_rank
+
+
+def max_over_ranks(values, world: int, device="cpu"):
+    """Element-wise max of per-rank timings (the slowest rank sets the whole-job time)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Problems per second of the whole job: every rank's problems over the slowest rank's time."""
+    return per_rank * world * steps / seconds
+
+
+# ------------------------------------------------------------------------------------------------
 # CPU oracle sample (also the reference arm); runs in a child process pinned to one thread
 # ------------------------------------------------------------------------------------------------
 
@@ -153,7 +178,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     c = spectra.WORKLOADS[args.workload]
     B, n, k = c["B"], c["n"], c["k"]
-    d = spectra.batch(c["id"], B, n, k, c["nnz"], first=rank * B)
+    d = spectra.batch(c["id"], B, n, k, c["nnz"], first=shard_first(rank, B))
     x = torch.tensor(d["x"], device=dev)
     D = torch.tensor(d["D"], device=dev)
     y = torch.tensor(d["y"], device=dev)
@@ -236,16 +261,13 @@ def run_ours(args, rank, world, local_rank):
     h2d = hx.numel() * 4 + hD.numel() * 4 + hy.numel() * 4 + hw.numel() * 4
     d2h = hw.numel() * 4 + ht.numel() * 4 + B * 4 * 3
 
-    vals = torch.tensor([tc["ms"], fp["ms"], e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    tc_ms, fp_ms, e2e_s = (float(v) for v in vals)
+    tc_ms, fp_ms, e2e_s = max_over_ranks([tc["ms"], fp["ms"], e2e_s], world, dev)
     if rank != 0:
         return None
 
     fp_steps = max(1, min(args.steps, 3))
-    value = B * world * args.steps / (tc_ms / 1e3)
-    fp_value = B * world * fp_steps / (fp_ms / 1e3)
+    value = whole_job_rate(B, world, args.steps, tc_ms / 1e3)
+    fp_value = whole_job_rate(B, world, fp_steps, fp_ms / 1e3)
     peaks = _peaks()
 
     # tensor-core path: the GEMM apply; algorithmic work is 2 n^2 flops per problem per apply
@@ -306,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
         "plain_fp32": plain,
         "roofline": roofline,
         "kernel_ms_per_step": {kk: v[0] for kk, v in tc["timing"].items()},
-        "e2e": {"value": B * world * e2e_steps / e2e_s, "unit": "problems/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(B, world, e2e_steps, e2e_s), "unit": "problems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": tc["launches"],
         "clocks": tc["clocks"],
@@ -332,7 +354,7 @@ def run_ragged(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     c = spectra.WORKLOADS[args.workload]
     B = c["count"]
-    probs = spectra.ragged(c["id"], B, first=rank * B)
+    probs = spectra.ragged(c["id"], B, first=shard_first(rank, B))
     rb = api.ragged_batch(probs, device=dev)
     w0_np = np.concatenate([spectra.initial_weights(p["y"], p["D"]) for p in probs]).astype(np.float32)
     w0 = torch.tensor(w0_np, device=dev)
@@ -401,10 +423,7 @@ def run_ragged(args, rank, world, local_rank):
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h.close()
-    vals = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms, e2e_s = float(vals[0]), float(vals[1])
+    ms, e2e_s = max_over_ranks([ms, e2e_s], world, dev)
     if rank != 0:
         return None
     exps_step = float(np.sum(n_np.astype(np.float64) ** 2 * (2 * it_np + 1)))
@@ -415,7 +434,7 @@ def run_ragged(args, rank, world, local_rank):
     d2h = (hw.numel() + ht.numel() + hit.numel()) * 4
     out = {
         "metric": "OTLM problems solved/s to 1e-5 marginal tol, uneven batch (n ~ U{256..4096}) in one persistent launch",
-        "value": B * world * args.steps / (ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+        "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
         "config": {"workload": args.workload, "problems_per_gpu": B, "n": "U{256..4096}", "k": "U{8..128}",
@@ -430,7 +449,7 @@ def run_ragged(args, rank, world, local_rank):
                      "launch_ms_avg": timing["apply"][0] / max(timing["apply"][1], 1),
                      "note": "algorithmic exp2 = sum_p n_p^2 (2 iters_p + 1); the kernel also runs the MM and "
                              "source steps, so the fraction is a lower bound for the apply itself"},
-        "e2e": {"value": B * world * max(1, args.steps) / e2e_s, "unit": "problems/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(B, world, max(1, args.steps), e2e_s), "unit": "problems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -576,7 +595,7 @@ def run_single_hbm(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     c = spectra.WORKLOADS[args.workload]
     B, n, k = c["B"], c["n"], c["k"]
-    d = spectra.batch(c["id"], B, n, k, c["nnz"], first=rank * B)
+    d = spectra.batch(c["id"], B, n, k, c["nnz"], first=shard_first(rank, B))
     x, D, y = (torch.tensor(d[key], device=dev) for key in ("x", "D", "y"))
     w0_np = spectra.initial_weights(d["y"], d["D"]).astype(np.float32)
     w0 = torch.tensor(w0_np, device=dev)
@@ -638,10 +657,7 @@ def run_single_hbm(args, rank, world, local_rank):
         step_host()
     e2e_s = time.perf_counter() - t0
     h.close()
-    vals = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms, e2e_s = (float(v) for v in vals)
+    ms, e2e_s = max_over_ranks([ms, e2e_s], world, dev)
     if rank != 0:
         return None
 
@@ -653,7 +669,7 @@ def run_single_hbm(args, rank, world, local_rank):
     peak = float(_peaks().get("hbm_gbs", 6800.0))
     out = {
         "metric": "single-target OTLM solves/s to 1e-5 marginal tol at n=16384 (stored kernel streamed from HBM)",
-        "value": B * world * args.steps / (ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+        "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 tensor (hi/lo split) + f32",
         "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
@@ -668,7 +684,7 @@ def run_single_hbm(args, rank, world, local_rank):
                      "launch_ms_avg": launch_ms, "bytes_per_launch": 4.0 * n * n,
                      "peak_basis": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in _peaks() else "fallback 6.8 TB/s"},
         "kernel_ms_per_step": {kk: v[0] for kk, v in timing.items()},
-        "e2e": {"value": B * world * max(1, args.steps) / e2e_s, "unit": "problems/s",
+        "e2e": {"value": whole_job_rate(B, world, max(1, args.steps), e2e_s), "unit": "problems/s",
                 "h2d_bytes_per_step": (hx.numel() + hD.numel() + hy.numel() + hw.numel()) * 4,
                 "d2h_bytes_per_step": (hw.numel() + ht.numel() + 3 * B) * 4},
         "gpu_launches": launches, "clocks": clk.summary()}
