@@ -19,9 +19,16 @@ Readings of passages the paper leaves garbled or open:
       (ln w_j + c_j w_j = nu_j); R(w) = (alpha/2)||w||^2.
   A8  "not converged" (Algorithm 1): source-marginal violation
       e = ||u2 * (K u1) - X w||_1 / ||X w||_1, measured with the u1 of the next iteration.
+  A6  Table 2, elastic net alpha l1 + (beta/2) l2^2: Table 2 prints the prefactor alpha/beta and a
+      y_j inside the sum; App. A's stationarity condition ln w_j + gamma_j w_j = nu_j with
+      gamma_j = beta/(eps x_j) and nu_j shifted by -alpha/(eps x_j) is followed instead:
+      w_j = W0(gamma_j e^{nu_j - alpha/(eps x_j)}) / gamma_j.
   A11 zeros: rows with (X w)_i = 0 contribute nothing to the MM sum (0 log 0 = 0), y_j = 0
       gives u1_j = 0 under the KL datafit.
-Poisson (Table 1, last row) and elastic net (Table 2, last row) are not implemented.
+  A18 more than one MM step per outer iteration (Sec. 4.2 allows running the MM iteration for
+      prox_{alpha P}(K u1 | X) longer than one step): every inner step uses the same a = K u1 and
+      its own previous w; the source step u2 = X w / a follows the last inner step.
+Poisson (Table 1, last row) is not implemented.
 """
 from __future__ import annotations
 
@@ -29,7 +36,7 @@ import numpy as np
 from scipy.special import lambertw, logsumexp, wrightomega
 
 DATAFITS = ("balanced", "kl", "tv", "l2")
-PENALTIES = ("none", "l1", "l2sq")
+PENALTIES = ("none", "l1", "l2sq", "elastic")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -87,6 +94,14 @@ def penalty_value(penalty, w):
     raise ValueError(penalty)
 
 
+def penalty_term(penalty, w, alpha, beta=0.0):
+    """The weighted penalty of the objective: alpha R(w) for none / l1 / l2sq, and
+    alpha ||w||_1 + (beta/2) ||w||^2 for the elastic net (Table 2, last row)."""
+    if penalty == "elastic":
+        return alpha * penalty_value("l1", w) + beta * penalty_value("l2sq", w)
+    return alpha * penalty_value(penalty, w)
+
+
 def prox_datafit(datafit, s, y, eps, lam):
     """prox^KL_{lam L}(s | y), Table 1, linear form."""
     s = np.asarray(s, dtype=np.float64)
@@ -110,8 +125,8 @@ def _Z(X, w_prev):
         return np.where(num > 0, num / den, 0.0)
 
 
-def mm_step(penalty, a, w_prev, X, eps, alpha):
-    """One MM step wMMstep^KL_P(a, Z | X), Table 2 with the App. A readings A3-A5.
+def mm_step(penalty, a, w_prev, X, eps, alpha, beta=0.0):
+    """One MM step wMMstep^KL_P(a, Z | X), Table 2 with the App. A readings A3-A6.
 
     `a` takes the place of y in Table 2 (Algorithm 1 calls it with K u1).  With
     L_j = sum_i X_ij log(Z_ij a_i / X_ij) (terms with X_ij = 0 dropped, 0 log 0 = 0) and the
@@ -119,6 +134,7 @@ def mm_step(penalty, a, w_prev, X, eps, alpha):
         none : w_j = exp(L_j / x_j)
         l1   : w_j = exp(L_j / x_j - alpha / (eps x_j))
         l2sq : w_j = W0(c_j exp(L_j / x_j)) / c_j,   c_j = alpha / (eps x_j)
+        elastic: w_j = W0(g_j exp(L_j / x_j - alpha / (eps x_j))) / g_j,   g_j = beta / (eps x_j)
     """
     X = np.asarray(X, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
@@ -135,10 +151,13 @@ def mm_step(penalty, a, w_prev, X, eps, alpha):
     if penalty == "l2sq":
         c = alpha / (eps * x)
         return lambert_w0(c * np.exp(nu)) / c
+    if penalty == "elastic":
+        gam = beta / (eps * x)
+        return lambert_w0(gam * np.exp(nu - alpha / (eps * x))) / gam
     raise ValueError(penalty)
 
 
-def mm_step_log(penalty, log_a, w_prev, X, eps, alpha):
+def mm_step_log(penalty, log_a, w_prev, X, eps, alpha, beta=0.0):
     """The same MM step written with log a instead of a (for kernels that underflow).
 
     Since Z_ij a_i / X_ij = w'_j a_i / s_i with s = X w' (wherever X_ij > 0), Table 2's
@@ -161,14 +180,19 @@ def mm_step_log(penalty, log_a, w_prev, X, eps, alpha):
         c = alpha / (eps * x)
         out = wright_omega(np.log(c) + nu) / c
         return np.where(np.isneginf(nu), 0.0, out)
+    if penalty == "elastic":
+        gam = beta / (eps * x)
+        out = wright_omega(np.log(gam) + nu - alpha / (eps * x)) / gam
+        return np.where(np.isneginf(nu), 0.0, out)
     raise ValueError(penalty)
 
 
-def majorizer_G(w, w_prev, a, X, eps, alpha, penalty):
+def majorizer_G(w, w_prev, a, X, eps, alpha, penalty, beta=0.0):
     """G(w, w') of Eq. (obj_nnsx_majorized), with a in place of y.
 
     G = eps sum_ij Z_ij ( (X_ij w_j / Z_ij) log(X_ij w_j / (Z_ij a_i)) - X_ij w_j / Z_ij + a_i )
-        + alpha R(w),   summed over the pairs with Z_ij > 0.
+        + alpha R(w)   (the elastic net's alpha l1 + (beta/2) l2^2 for "elastic"),
+    summed over the pairs with Z_ij > 0.
     """
     X = np.asarray(X, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
@@ -181,12 +205,12 @@ def majorizer_G(w, w_prev, a, X, eps, alpha, penalty):
             q = X[i, j] * w[j] / Z[i, j]
             term = (q * np.log(q / a[i]) if q > 0 else 0.0) - q + a[i]
             total += Z[i, j] * term
-    return eps * total + alpha * penalty_value(penalty, w)
+    return eps * total + penalty_term(penalty, w, alpha, beta)
 
 
-def prox_objective_V(w, a, X, eps, alpha, penalty):
+def prox_objective_V(w, a, X, eps, alpha, penalty, beta=0.0):
     """V(w) = alpha R(w) + eps KL(X w || a), the objective of Eq. (ProxP) (Sec. 4.1)."""
-    return alpha * penalty_value(penalty, w) + eps * generalized_kl(np.asarray(X) @ np.asarray(w), a)
+    return penalty_term(penalty, w, alpha, beta) + eps * generalized_kl(np.asarray(X) @ np.asarray(w), a)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -198,11 +222,13 @@ def marginal_violation(s, u2, a):
     return float(np.sum(np.abs(u2 * a - s)) / np.sum(s))
 
 
-def solve(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0):
+def solve(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, beta=0.0, mm_steps=1):
     """Algorithm 1 (Scaling Algorithm for OTLM) in the linear domain, FP64.
 
-    Per iteration, in the paper's order: a = K u1; Z from the previous w; w <- wMMstep(a, Z|X);
-    u2 = X w / a; b = K^T u2; v2 = prox_L(b | y); u1 = v2 / b.
+    Per iteration, in the paper's order: a = K u1; Z from the previous w; w <- wMMstep(a, Z|X)
+    (`mm_steps` times with the same a, reading A18; one step in Algorithm 1);
+    u2 = X w / a; b = K^T u2; v2 = prox_L(b | y); u1 = v2 / b.  `beta` is the elastic net's
+    squared-l2 weight (ignored by the other penalties).
     Before every iteration after the first, the source-marginal violation of the current plan
     (reading A8) is measured with the new a = K u1; when tol > 0 and it is <= tol the loop
     stops and the state of the last completed iteration is returned (tol <= 0: run n_iter).
@@ -229,7 +255,8 @@ def solve(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0):
                 break
         if it == n_iter:
             break
-        w = mm_step(penalty, a, w, X, eps, alpha)
+        for _ in range(mm_steps):
+            w = mm_step(penalty, a, w, X, eps, alpha, beta)
         s = X @ w
         u2 = s / a
         b = K.T @ u2
@@ -265,12 +292,13 @@ def _log_datafit_potential(datafit, log_b, y, eps, lam):
     raise ValueError(datafit)
 
 
-def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g0=None):
+def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g0=None, beta=0.0, mm_steps=1):
     """Algorithm 1 with the scalings carried as potentials g = eps log u1, f = eps log u2.
 
     log (K u1)_i = LSE_j((g_j - C_ij)/eps), log (K^T u2)_j = LSE_i((f_i - C_ij)/eps); the MM step
     is `mm_step_log`; f = eps (log X w - log K u1) (-inf where X w = 0); g from
-    `_log_datafit_potential`.  Same stopping rule and outputs as `solve`, plus f, g, log_a.
+    `_log_datafit_potential`.  Same stopping rule, `beta`, `mm_steps` and outputs as `solve`, plus
+    f, g, log_a.
     """
     C = np.asarray(C, dtype=np.float64)
     X = np.asarray(X, dtype=np.float64)
@@ -293,7 +321,8 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
                 break
         if it == n_iter:
             break
-        w = mm_step_log(penalty, log_a, w, X, eps, alpha)
+        for _ in range(mm_steps):
+            w = mm_step_log(penalty, log_a, w, X, eps, alpha, beta)
         s = X @ w
         with np.errstate(divide="ignore"):
             f = eps * (np.log(s) - log_a)
@@ -312,7 +341,7 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
 # Objective (reading A1) and a Fenchel dual lower bound
 # ---------------------------------------------------------------------------------------------
 
-def primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty):
+def primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty, beta=0.0):
     """eps KL(Q || K) + lam L(Q^T 1 | y) + alpha R(w) (Eq. OTLM, reading A1).
 
     The caller guarantees Q 1 = X w (the constraint of the second form of Eq. OTLM).
@@ -320,7 +349,8 @@ def primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty):
     K = gibbs_kernel(C, eps)
     t = np.asarray(Q).sum(axis=0)
     lt = datafit_loss(datafit, t, y)
-    return eps * generalized_kl(Q, K) + (lam * lt if datafit != "balanced" else lt) + alpha * penalty_value(penalty, w)
+    return (eps * generalized_kl(Q, K) + (lam * lt if datafit != "balanced" else lt)
+            + penalty_term(penalty, w, alpha, beta))
 
 
 def _F2_conj_neg(datafit, g, y, lam):
@@ -345,8 +375,12 @@ def _F2_conj_neg(datafit, g, y, lam):
     raise ValueError(datafit)
 
 
-def _F1_conj_neg(penalty, f, X, alpha):
+def _F1_conj_neg(penalty, f, X, alpha, beta=0.0):
     """F1*(-f) = (alpha R + indicator(w >= 0))^*(-X^T f), F1(s) = alpha P_R(s | X) (Eq. P).
+
+    Per column, sup_{w >= 0} (v w - h(w)) with v = -(X^T f)_j: 0 or +inf for h = alpha w (v <= alpha)
+    and h = 0 (v <= 0); v+^2 / (2 alpha) for h = alpha w^2 / 2; (v - alpha)+^2 / (2 beta) for the
+    elastic net h = alpha w + beta w^2 / 2.
 
     Rows of X that are entirely zero do not enter X^T f (0 * (-inf) taken as 0).
     """
@@ -362,10 +396,12 @@ def _F1_conj_neg(penalty, f, X, alpha):
         return 0.0 if np.all(v <= alpha + slack) else np.inf
     if penalty == "l2sq":
         return float(np.sum(np.maximum(v, 0.0) ** 2) / (2 * alpha))
+    if penalty == "elastic":
+        return float(np.sum(np.maximum(v - alpha, 0.0) ** 2) / (2 * beta))
     raise ValueError(penalty)
 
 
-def dual_objective(f, g, C, X, y, eps, lam, alpha, datafit, penalty):
+def dual_objective(f, g, C, X, y, eps, lam, alpha, datafit, penalty, beta=0.0):
     """D(f, g) = -F1*(-f) - F2*(-g) - eps sum_ij K_ij (e^{(f_i + g_j)/eps} - 1).
 
     For the l1 / unpenalised cases a constant shift f <- f + c 1 (c >= 0, the smallest that makes
@@ -392,10 +428,10 @@ def dual_objective(f, g, C, X, y, eps, lam, alpha, datafit, penalty):
     with np.errstate(invalid="ignore", over="ignore"):
         E = np.exp((f[:, None] + g[None, :]) / eps)
     ent = eps * float(np.sum(K * E) - np.sum(K))
-    return -_F1_conj_neg(penalty, f, X, alpha) - _F2_conj_neg(datafit, g, y, lam) - ent
+    return -_F1_conj_neg(penalty, f, X, alpha, beta) - _F2_conj_neg(datafit, g, y, lam) - ent
 
 
-def objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty):
+def objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty, beta=0.0):
     """Primal value, dual value and their plan, evaluated from a solver state (w, g).
 
     From (w, g): a = K u1 (u1 = e^{g/eps}), s = X w, f = eps log(s / a); the plan
@@ -413,8 +449,8 @@ def objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty):
     with np.errstate(divide="ignore"):
         f = eps * (np.log(s) - log_a)
     Q = np.exp((f[:, None] + g[None, :] - C) / eps)
-    P = primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty)
+    P = primal_objective(Q, w, C, y, eps, lam, alpha, datafit, penalty, beta)
     log_b = logsumexp((f[:, None] - C) / eps, axis=0)
     g_next = _log_datafit_potential(datafit, log_b, y, eps, lam)
-    Dv = dual_objective(f, g_next, C, X, y, eps, lam, alpha, datafit, penalty)
+    Dv = dual_objective(f, g_next, C, X, y, eps, lam, alpha, datafit, penalty, beta)
     return P, Dv, Q

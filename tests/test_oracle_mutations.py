@@ -20,14 +20,14 @@ def _fails(fn, *args):
 def test_transposed_kernel_is_caught(monkeypatch):
     good = ot.gibbs_kernel
     monkeypatch.setattr(ot, "gibbs_kernel", lambda C, eps: good(C, eps).T)
-    assert _fails(pins.test_brute_force_tiny_instance, "kl", "l2sq")
+    assert _fails(pins.test_brute_force_tiny_instance, "kl", "l2sq", 1)
 
 
 def test_wrong_l1_sign_is_caught(monkeypatch):
     good = ot.mm_step
 
-    def bad(penalty, a, w_prev, X, eps, alpha):
-        return good(penalty, a, w_prev, X, eps, -alpha if penalty == "l1" else alpha)
+    def bad(penalty, a, w_prev, X, eps, alpha, beta=0.0):
+        return good(penalty, a, w_prev, X, eps, -alpha if penalty == "l1" else alpha, beta)
     monkeypatch.setattr(ot, "mm_step", bad)
     monkeypatch.setattr(pins.oracle, "mm_step", bad)
     assert _fails(pins.test_mm_step_minimises_majorizer, "l1")
@@ -46,7 +46,7 @@ def test_swapped_kl_prox_exponents_are_caught(monkeypatch):
 
 def test_dropped_column_mass_in_mm_is_caught(monkeypatch):
     """nu_j without the 1/x_j factor: a dropped term that unit-mass columns would hide."""
-    def bad(penalty, a, w_prev, X, eps, alpha):
+    def bad(penalty, a, w_prev, X, eps, alpha, beta=0.0):
         X = np.asarray(X, dtype=float)
         Z = ot._Z(X, np.asarray(w_prev, dtype=float))
         with np.errstate(divide="ignore", invalid="ignore"):
@@ -75,9 +75,62 @@ def test_wrong_tv_clamp_is_caught(monkeypatch):
 def test_broken_dual_is_caught(monkeypatch, which):
     good = ot.dual_objective
 
-    def bad(f, g, C, X, y, eps, lam, alpha, datafit, penalty):
+    def bad(f, g, C, X, y, eps, lam, alpha, datafit, penalty, beta=0.0):
         if which == "f_sign":
-            return good(-np.asarray(f), g, C, X, y, eps, lam, alpha, datafit, penalty)
-        return good(f, g, C, X, y, eps, lam, alpha, datafit, penalty) + 0.1
+            return good(-np.asarray(f), g, C, X, y, eps, lam, alpha, datafit, penalty, beta)
+        return good(f, g, C, X, y, eps, lam, alpha, datafit, penalty, beta) + 0.1
     monkeypatch.setattr(ot, "dual_objective", bad)
     assert _fails(pins.test_invariants_along_the_trajectory, "kl", "l2sq")
+
+
+def test_table2_elastic_prefactor_is_caught(monkeypatch):
+    """Table 2 as printed (prefactor alpha/beta, no column mass in gamma): App. A's stationarity
+    condition must reject it."""
+    good = ot.mm_step
+
+    def bad(penalty, a, w_prev, X, eps, alpha, beta=0.0):
+        if penalty != "elastic":
+            return good(penalty, a, w_prev, X, eps, alpha, beta)
+        X = np.asarray(X, dtype=float)
+        x = X.sum(axis=0)
+        nu = np.log(good("none", a, w_prev, X, eps, 0.0))
+        return (alpha / beta) * ot.lambert_w0((beta / alpha) / x * np.exp(nu - alpha / (eps * x)))
+    monkeypatch.setattr(pins.oracle, "mm_step", bad)
+    assert _fails(pins.test_elastic_step_solves_its_stationarity_condition)
+
+
+def test_elastic_without_the_l1_shift_is_caught(monkeypatch):
+    good = ot.mm_step
+
+    def bad(penalty, a, w_prev, X, eps, alpha, beta=0.0):
+        if penalty == "elastic":
+            return good("l2sq", a, w_prev, X, eps, beta)
+        return good(penalty, a, w_prev, X, eps, alpha, beta)
+    monkeypatch.setattr(pins.oracle, "mm_step", bad)
+    assert _fails(pins.test_mm_step_minimises_majorizer, "elastic")
+
+
+def test_inner_steps_with_a_stale_source_ratio_are_caught(monkeypatch):
+    """Inner MM steps that keep the first step's Z (the previous w) instead of their own: the
+    limit is no longer the weight prox."""
+    good = ot.mm_step
+    state = {}
+
+    def bad(penalty, a, w_prev, X, eps, alpha, beta=0.0):
+        key = id(a)
+        if state.get("key") != key:
+            state["key"], state["w0"] = key, np.asarray(w_prev, dtype=float).copy()
+        return good(penalty, a, state["w0"], X, eps, alpha, beta)
+    monkeypatch.setattr(ot, "mm_step", bad)
+    assert _fails(pins.test_many_inner_mm_steps_give_the_weight_prox, "elastic")
+
+
+def test_wrong_elastic_conjugate_is_caught(monkeypatch):
+    good = ot._F1_conj_neg
+
+    def bad(penalty, f, X, alpha, beta=0.0):
+        if penalty == "elastic":
+            return good("l2sq", f, X, beta)
+        return good(penalty, f, X, alpha, beta)
+    monkeypatch.setattr(ot, "_F1_conj_neg", bad)
+    assert _fails(pins.test_invariants_along_the_trajectory, "kl", "elastic")

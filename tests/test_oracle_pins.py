@@ -7,12 +7,13 @@ operand in the oracle fails at least one of them (see also test_oracle_mutations
 """
 import numpy as np
 import pytest
-from scipy.optimize import minimize, minimize_scalar
+from scipy.optimize import brentq, minimize, minimize_scalar
 
 import oracle
 import spectra
 
 EPS = 2e-2
+BETA = 0.04  # the elastic net's squared-l2 weight; ignored by the other penalties
 
 
 def _tiny(n=5, k=2, seed=0, symmetric=False):
@@ -112,7 +113,7 @@ def test_log_potential_equals_linear_prox(datafit):
 
 # --- Table 2 / App. A: the MM step --------------------------------------------------------------
 
-@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq", "elastic"])
 def test_mm_step_minimises_majorizer(penalty):
     """G(w, w') is separable in w_j: coordinate-wise 1-D minimisation must give the MM step."""
     X, _, _ = _tiny(n=6, k=3, seed=2)
@@ -121,32 +122,32 @@ def test_mm_step_minimises_majorizer(penalty):
     a = rng.uniform(0.1, 1.0, 6)
     w_prev = rng.uniform(0.2, 2.0, 3)
     alpha = 0.05
-    w = oracle.mm_step(penalty, a, w_prev, X, EPS, alpha)
+    w = oracle.mm_step(penalty, a, w_prev, X, EPS, alpha, BETA)
     for j in range(3):
         def obj(lv, j=j):
             ww = w.copy()
             ww[j] = np.exp(lv)
-            return oracle.majorizer_G(ww, w_prev, a, X, EPS, alpha, penalty)
+            return oracle.majorizer_G(ww, w_prev, a, X, EPS, alpha, penalty, BETA)
         res = minimize_scalar(obj, bounds=(np.log(w[j]) - 3, np.log(w[j]) + 3), method="bounded",
                               options=dict(xatol=1e-12))
         assert np.exp(res.x) == pytest.approx(w[j], rel=1e-6)
 
 
-@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq", "elastic"])
 def test_majorizer_majorises_and_touches(penalty):
     X, _, _ = _tiny(n=6, k=3, seed=4)
     rng = np.random.default_rng(6)
     a = rng.uniform(0.1, 1.0, 6)
     w_prev = rng.uniform(0.2, 2.0, 3)
-    V = lambda w: oracle.prox_objective_V(w, a, X, EPS, 0.05, penalty)  # noqa: E731
-    G = lambda w: oracle.majorizer_G(w, w_prev, a, X, EPS, 0.05, penalty)  # noqa: E731
+    V = lambda w: oracle.prox_objective_V(w, a, X, EPS, 0.05, penalty, BETA)  # noqa: E731
+    G = lambda w: oracle.majorizer_G(w, w_prev, a, X, EPS, 0.05, penalty, BETA)  # noqa: E731
     assert G(w_prev) == pytest.approx(V(w_prev), rel=1e-13)
     for _ in range(30):
         w = rng.uniform(0.0, 3.0, 3)
         assert G(w) >= V(w) - 1e-13
 
 
-@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq", "elastic"])
 def test_repeated_mm_steps_decrease_V_to_the_proxP_minimum(penalty):
     """MM on Eq. (ProxP) with a fixed: V non-increasing, and the limit minimises V over w >= 0."""
     X, _, _ = _tiny(n=7, k=3, seed=8)
@@ -154,26 +155,71 @@ def test_repeated_mm_steps_decrease_V_to_the_proxP_minimum(penalty):
     a = rng.uniform(0.2, 1.0, 7)
     alpha = 0.01
     w = np.ones(3)
-    vals = [oracle.prox_objective_V(w, a, X, EPS, alpha, penalty)]
+    vals = [oracle.prox_objective_V(w, a, X, EPS, alpha, penalty, BETA)]
     for _ in range(4000):
-        w = oracle.mm_step(penalty, a, w, X, EPS, alpha)
-        vals.append(oracle.prox_objective_V(w, a, X, EPS, alpha, penalty))
+        w = oracle.mm_step(penalty, a, w, X, EPS, alpha, BETA)
+        vals.append(oracle.prox_objective_V(w, a, X, EPS, alpha, penalty, BETA))
     assert np.all(np.diff(vals) <= 1e-13 * np.abs(vals[:-1]) + 1e-16)
-    res = minimize(lambda lw: oracle.prox_objective_V(np.exp(lw), a, X, EPS, alpha, penalty),
+    res = minimize(lambda lw: oracle.prox_objective_V(np.exp(lw), a, X, EPS, alpha, penalty, BETA),
                    np.log(w) + 0.3, method="Nelder-Mead", options=dict(xatol=1e-12, fatol=1e-15, maxiter=20000))
     assert vals[-1] <= res.fun + 1e-12
     np.testing.assert_allclose(w, np.exp(res.x), rtol=1e-4)
 
 
-@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq"])
+@pytest.mark.parametrize("penalty", ["none", "l1", "l2sq", "elastic"])
 def test_mm_step_log_equals_linear(penalty):
     X, _, _ = _tiny(n=8, k=4, seed=10)
     X[2, :2] = 0.0
     rng = np.random.default_rng(11)
     a = rng.uniform(0.1, 1.0, 8)
     w_prev = rng.uniform(0.2, 2.0, 4)
-    np.testing.assert_allclose(oracle.mm_step_log(penalty, np.log(a), w_prev, X, EPS, 0.03),
-                               oracle.mm_step(penalty, a, w_prev, X, EPS, 0.03), rtol=1e-13)
+    np.testing.assert_allclose(oracle.mm_step_log(penalty, np.log(a), w_prev, X, EPS, 0.03, BETA),
+                               oracle.mm_step(penalty, a, w_prev, X, EPS, 0.03, BETA), rtol=1e-13)
+
+
+def test_elastic_step_solves_its_stationarity_condition():
+    """App. A: with w~_j the unpenalised MM step, the elastic-net step is the root of
+    eps x_j ln(w_j / w~_j) + alpha + beta w_j = 0 (found here by bisection on ln w_j); alpha = 0
+    gives the squared-l2 step with weight beta, and beta -> 0 the l1 step."""
+    X, _, _ = _tiny(n=6, k=3, seed=14)
+    X[:, 2] *= 2.5  # a column of mass 2.5: a prefactor that forgets x_j lands elsewhere
+    rng = np.random.default_rng(15)
+    a = rng.uniform(0.1, 1.0, 6)
+    w_prev = rng.uniform(0.2, 2.0, 3)
+    alpha, beta = 0.05, 0.3
+    x = X.sum(axis=0)
+    w = oracle.mm_step("elastic", a, w_prev, X, EPS, alpha, beta)
+    wt = oracle.mm_step("none", a, w_prev, X, EPS, 0.0)
+    for j in range(3):
+        def h(lv, j=j):
+            return EPS * x[j] * (lv - np.log(wt[j])) + alpha + beta * np.exp(lv)
+        lo = np.log(wt[j]) - (alpha + beta * wt[j]) / (EPS * x[j]) - 1.0
+        root = brentq(h, lo, np.log(wt[j]), xtol=1e-15, rtol=1e-15)
+        assert w[j] == pytest.approx(np.exp(root), rel=1e-11)
+    np.testing.assert_allclose(oracle.mm_step("elastic", a, w_prev, X, EPS, 0.0, beta),
+                               oracle.mm_step("l2sq", a, w_prev, X, EPS, beta), rtol=1e-13)
+    np.testing.assert_allclose(oracle.mm_step("elastic", a, w_prev, X, EPS, alpha, 1e-12),
+                               oracle.mm_step("l1", a, w_prev, X, EPS, alpha), rtol=1e-8)
+
+
+@pytest.mark.parametrize("penalty", ["l1", "elastic"])
+def test_many_inner_mm_steps_give_the_weight_prox(penalty):
+    """Reading A18 with many inner steps: the weights after the first outer iteration minimise
+    V(w) = eps KL(X w | a) + penalty over w >= 0 for a = K 1 (u1 starts at 1); V and a are written
+    out here and minimised by a generic bounded optimiser."""
+    X, y, C = _tiny(n=6, k=3, seed=16)
+    eps, alpha = 0.05, 0.02
+    r = oracle.solve(C, X, y, eps, 1.0, alpha, "kl", penalty, np.ones(3), 1, beta=BETA, mm_steps=20000)
+    a = np.exp(-C / eps) @ np.ones(6)
+
+    def V(w):
+        s = X @ w
+        pen = alpha * w.sum() + (0.5 * BETA * (w * w).sum() if penalty == "elastic" else 0.0)
+        return eps * np.sum(s * np.log(s / a) - s + a) + pen
+    res = minimize(V, r["w"] * 1.3, method="L-BFGS-B", bounds=[(1e-12, None)] * 3,
+                   options=dict(ftol=1e-16, gtol=1e-13, maxiter=20000))
+    assert V(r["w"]) <= res.fun + 1e-13
+    np.testing.assert_allclose(r["w"], res.x, rtol=1e-5)
 
 
 # --- Algorithm 1 --------------------------------------------------------------------------------
@@ -205,7 +251,7 @@ def test_balanced_single_column_reduces_to_sinkhorn():
     np.testing.assert_allclose(r["s"], mu, rtol=1e-9)
 
 
-def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty):
+def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty, beta=0.0):
     """Minimise eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w) s.t. Q 1 = X w, Q >= 0, w >= 0,
     with Q_ij = (X w)_i softmax_j(theta_i), w = exp(eta); gradients by torch autograd (FP64)."""
     import torch
@@ -222,8 +268,11 @@ def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty):
             L = torch.sum(t * torch.log(t / yt) - t + yt)
         else:
             L = 0.5 * torch.sum((t - yt) ** 2)
-        R = torch.sum(w) if penalty == "l1" else 0.5 * torch.sum(w * w)
-        return eps * kl + lam * L + alpha * R
+        if penalty == "elastic":
+            pen = alpha * torch.sum(w) + 0.5 * beta * torch.sum(w * w)
+        else:
+            pen = alpha * (torch.sum(w) if penalty == "l1" else 0.5 * torch.sum(w * w))
+        return eps * kl + lam * L + pen
 
     def fg(zn):
         z = torch.tensor(zn, dtype=torch.float64, requires_grad=True)
@@ -236,15 +285,19 @@ def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty):
     return np.exp(res.x[n * n:]), res.fun
 
 
-@pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("l2", "l1"), ("kl", "l1"), ("l2", "l2sq")])
-def test_brute_force_tiny_instance(datafit, penalty):
+@pytest.mark.parametrize("datafit,penalty,mm_steps", [("kl", "l2sq", 1), ("l2", "l1", 1), ("kl", "l1", 1),
+                                                      ("l2", "l2sq", 1), ("kl", "elastic", 1), ("l2", "elastic", 3),
+                                                      ("kl", "l1", 4)])
+def test_brute_force_tiny_instance(datafit, penalty, mm_steps):
     """Same convex problem solved by a generic optimiser; C is not symmetric, so a transposed
-    K or a swapped marginal in Algorithm 1 lands on a different w."""
+    K or a swapped marginal in Algorithm 1 lands on a different w.  Several inner MM steps per
+    outer iteration (reading A18) change the path, not the optimum."""
     X, y, C = _tiny(n=5, k=2, seed=13)
     eps, lam, alpha = 0.05, 1.0, 0.02
-    r = oracle.solve(C, X, y, eps, lam, alpha, datafit, penalty, np.ones(2), 20000, tol=1e-15)
-    w_bf, P_bf = _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty)
-    P = oracle.primal_objective(r["Q"], r["w"], C, y, eps, lam, alpha, datafit, penalty)
+    r = oracle.solve(C, X, y, eps, lam, alpha, datafit, penalty, np.ones(2), 20000, tol=1e-15,
+                     beta=BETA, mm_steps=mm_steps)
+    w_bf, P_bf = _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty, BETA)
+    P = oracle.primal_objective(r["Q"], r["w"], C, y, eps, lam, alpha, datafit, penalty, BETA)
     assert P == pytest.approx(P_bf, rel=1e-9, abs=1e-12)
     np.testing.assert_allclose(r["w"], w_bf, rtol=2e-5)
 
@@ -256,14 +309,15 @@ def test_linear_and_log_domain_agree(datafit, penalty):
     C = spectra.squared_cost(d["x"])
     y = d["y"][0]
     w0 = spectra.initial_weights(y, d["D"])
-    a = oracle.solve(C, d["D"], y, 0.03, 1.0, 0.01, datafit, penalty, w0, 60)
-    b = oracle.solve_log(C, d["D"], y, 0.03, 1.0, 0.01, datafit, penalty, w0, 60)
+    a = oracle.solve(C, d["D"], y, 0.03, 1.0, 0.01, datafit, penalty, w0, 60, beta=BETA, mm_steps=2)
+    b = oracle.solve_log(C, d["D"], y, 0.03, 1.0, 0.01, datafit, penalty, w0, 60, beta=BETA, mm_steps=2)
     np.testing.assert_allclose(b["w"], a["w"], rtol=1e-11, atol=1e-300)
     np.testing.assert_allclose(b["t"], a["t"], rtol=1e-10, atol=1e-300)
     assert b["iters"] == a["iters"] == 60
 
 
-@pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("kl", "l1"), ("tv", "l1"), ("l2", "l2sq"), ("l2", "none")])
+@pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("kl", "l1"), ("tv", "l1"), ("l2", "l2sq"), ("l2", "none"),
+                                             ("kl", "elastic")])
 def test_invariants_along_the_trajectory(datafit, penalty):
     """w >= 0, Q >= 0, Q 1 = X w after the source step; primal objective non-increasing (observed,
     not proved in the paper: slack 1e-12 relative); weak duality P >= D at every iterate;
@@ -275,16 +329,16 @@ def test_invariants_along_the_trajectory(datafit, penalty):
     w, g = spectra.initial_weights(y, X), np.zeros(40)
     prev = np.inf
     for _ in range(150):
-        r = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 1, g0=g)
+        r = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 1, g0=g, beta=BETA)
         w, g = r["w"], r["g"]
         assert np.all(w >= 0) and np.all(r["Q"] >= 0)
-        P, Dv, Q = oracle.objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty)
+        P, Dv, Q = oracle.objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty, BETA)
         np.testing.assert_allclose(Q.sum(axis=1), X @ w, rtol=1e-12)
         assert P <= prev + 1e-12 * abs(prev) if np.isfinite(prev) else True
         assert P - Dv >= -1e-12 * abs(P)
         prev = P
-    r = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 20000, tol=1e-15, g0=g)
-    P, Dv, _ = oracle.objective_and_dual(r["w"], r["g"], C, X, y, eps, lam, alpha, datafit, penalty)
+    r = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 20000, tol=1e-15, g0=g, beta=BETA)
+    P, Dv, _ = oracle.objective_and_dual(r["w"], r["g"], C, X, y, eps, lam, alpha, datafit, penalty, BETA)
     assert P - Dv <= 1e-9 * abs(P)
 
 
