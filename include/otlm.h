@@ -64,7 +64,10 @@ typedef enum {            /* marginal datafit L(. | y), Table 1 */
 typedef enum {            /* weight penalty R(w), Table 2 */
   OTLM_PENALTY_NONE = 0,
   OTLM_PENALTY_L1   = 1,      /* alpha sum w                                                 */
-  OTLM_PENALTY_L2SQ = 2       /* (alpha/2) ||w||^2                                           */
+  OTLM_PENALTY_L2SQ = 2,      /* (alpha/2) ||w||^2                                           */
+  OTLM_PENALTY_ELASTIC = 3    /* alpha sum w + (beta/2) ||w||^2, beta from otlm_config; update
+                                 w_j = W0(g_j e^{nu_j - alpha/(eps x_j)})/g_j, g_j = beta/(eps x_j)
+                                 (App. A's stationarity condition; Table 2 prints alpha/beta)   */
 } otlm_penalty;
 
 typedef enum {
@@ -89,6 +92,11 @@ typedef struct otlm_config {
   double tol;          /* stop a problem once e <= tol; tol <= 0 runs exactly max_iter        */
   int    poll_every;   /* host polls the number of unfinished problems every this many
                           iterations (>= 1); larger = fewer host syncs, more idle launches   */
+  double beta;         /* squared-l2 weight of OTLM_PENALTY_ELASTIC (> 0 there; ignored by the
+                          other penalties)                                                     */
+  int    mm_steps;     /* MM steps of the weight update per iteration, all with the same
+                          a = K u1 (Sec. 4.2: Algorithm 1 takes one; more approach
+                          prox_{alpha P}(K u1 | X)); 0 or 1 = one step, at most 64             */
 } otlm_config;
 
 typedef struct otlm_ctx* otlm_handle;
@@ -96,7 +104,8 @@ typedef struct otlm_ctx* otlm_handle;
 /* Create a handle and its device workspace (about (8 n_max + 2 k_max + 16) * batch_max
  * elements).  `cuda_stream` is a cudaStream_t (NULL = default stream).  The workspace is
  * owned by the handle and released by otlm_destroy.
- * Errors: OTLM_EINVAL (null pointers, sizes out of range, unknown enum), OTLM_ENOMEM,
+ * Errors: OTLM_EINVAL (null pointers, sizes out of range, unknown enum, ELASTIC without a
+ * finite beta > 0, mm_steps outside 0..64), OTLM_ENOMEM,
  * OTLM_ECUDA.  On error *h is set to NULL. */
 int otlm_create(otlm_handle* h, const otlm_config* cfg, void* cuda_stream);
 
@@ -104,7 +113,7 @@ int otlm_create(otlm_handle* h, const otlm_config* cfg, void* cuda_stream);
 void otlm_destroy(otlm_handle h);
 
 /* Solve `batch` independent OTLM problems sharing one grid and one dictionary
- * (Algorithm 1, one MM step per iteration as in Sec. 4.2).
+ * (Algorithm 1; cfg.mm_steps MM steps per iteration, one by default as in Sec. 4.2).
  *   x      [n]          grid; cost C_ij = (x_i - x_j)^2
  *   D      [n][k]       dictionary X of the paper; entries >= 0, every column sum > 0
  *   y      [batch][n]   targets, >= 0
@@ -160,8 +169,8 @@ int otlm_solve_host(otlm_handle h, int batch, int n, int k,
  *   w               [sum k]     problem p at offset off_k[p]; in: initial weights (> 0), out: result
  *   n, k, eps, off_* , iters_out, err_out, status_out: [batch], device memory
  * g: in/out potentials (NULL = cold start, no output); t_out may be NULL.  lam and alpha as in
- * otlm_solve; datafit, penalty, max_iter and tol come from the handle, which must be
- * OTLM_PREC_FP32_LOG.  One CTA solves one problem at a time with its state in shared memory; CTAs
+ * otlm_solve; datafit, penalty, beta, mm_steps, max_iter and tol come from the handle, which
+ * must be OTLM_PREC_FP32_LOG.  One CTA solves one problem at a time with its state in shared memory; CTAs
  * take problems largest-first from a device queue; the launch is captured in a CUDA graph (on an
  * internal stream ordered after the handle's stream) and replayed while the arguments repeat.
  * The host copies n, k, eps once to validate and order the batch (a synchronous copy).
@@ -221,7 +230,7 @@ int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const floa
 /* Objective of a solver state (w, g), in FP64 (Eq. OTLM with the reading above).
  * From (w, g): a = K u1, s = D w, f = eps log(s/a); the plan Q = diag(e^{f/eps}) K diag(e^{g/eps})
  * satisfies Q 1 = D w, so primal_out = eps KL(Q||K) + lam L(Q^T 1|y) + alpha R(w) is the value
- * of a feasible point.  dual_out is the Fenchel dual
+ * of a feasible point (ELASTIC: alpha sum w + (beta/2)||w||^2 in place of alpha R(w)).  dual_out is the Fenchel dual
  *   -F1*(-f') - F2*(-g') - eps sum_ij K_ij (e^{(f'_i+g'_j)/eps} - 1)
  * at g' = the datafit step from K^T e^{f/eps} and f' = f shifted by the smallest constant that
  * makes it dual-feasible (l1 / no penalty), so dual_out <= optimum <= primal_out and
@@ -266,7 +275,9 @@ int otlm_get_timing(otlm_handle h, double* ms, long long* launches);
  * shares the one array and it keeps the previous call's contents (each solve re-initialises
  * what it reads), so calls whose GPU work overlaps -- two streams, two host threads -- race.
  * The host waits at the convergence polls (every 8 iterations) like otlm_solve.
- * Errors: OTLM_EINVAL (as otlm_solve, plus unknown datafit/penalty, max_iter < 1),
+ * One MM step per iteration; the penalty is NONE, L1 or L2SQ (ELASTIC needs a beta this call
+ * does not take).
+ * Errors: OTLM_EINVAL (as otlm_solve, plus unknown datafit/penalty, ELASTIC, max_iter < 1),
  * OTLM_ESCRATCH, OTLM_ECUDA. */
 int otlm_solve_noalloc(int batch, int n, int k, const float* x, const float* D, const float* y,
                        double eps, double lam, double alpha, int datafit, int penalty, int max_iter,

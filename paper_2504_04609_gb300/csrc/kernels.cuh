@@ -12,7 +12,7 @@ namespace otlm {
 
 enum { EPI_SOURCE = 0, EPI_TARGET = 1 };
 enum { DF_BALANCED = 0, DF_KL = 1, DF_TV = 2, DF_L2 = 3 };
-enum { PEN_NONE = 0, PEN_L1 = 1, PEN_L2SQ = 2 };
+enum { PEN_NONE = 0, PEN_L1 = 1, PEN_L2SQ = 2, PEN_ELASTIC = 3 };
 enum { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_NONFINITE = 2, ST_INVALID = 3 };
 
 template <typename T>
@@ -400,7 +400,8 @@ struct MMArgs {
   int it, max_iter;
   T tol;
   int penalty;
-  T eps, alpha;
+  int mm_steps = 1;  // MM steps with the same LA2 (a = K u1)
+  T eps, alpha, beta;
 };
 
 // S = D w for problem p (rows strided over the block), F2 = log2 S - LA2 when LA2 != nullptr,
@@ -426,7 +427,8 @@ __device__ __forceinline__ T source_marginal(const T* __restrict__ Dt, const T* 
 
 // Per active problem (one CTA of 256 threads): convergence decision for the previous iteration,
 // then Table 2's MM step  nu_j = log w_j + (ln2 / x_j) sum_i D_ij (LA2_i - log2 S_i)  (rows with
-// S_i = 0 dropped), the penalty update, and the source step S = D w, F2 = log2 S - LA2.
+// S_i = 0 dropped), the penalty update and S = D w, mm_steps times with the same LA2; the last
+// source step also writes F2 = log2 S - LA2.
 template <typename T, int KQ>
 __global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
   using P = Prec<T>;
@@ -463,54 +465,60 @@ __global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
     if (stop) return;
   }
 
-  // phase A: Dt r, r_i = LA2_i - log2 S_i (log2 units), 32 rows per warp step
-  T acc[KQ];
+  for (int m = 0; m < A.mm_steps; ++m) {
+    // phase A: Dt r, r_i = LA2_i - log2 S_i (log2 units), 32 rows per warp step
+    T acc[KQ];
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) acc[q] = T(0);
-  for (int base = warp * 32; base < n; base += 8 * 32) {
-    const int i = base + lane;
-    T r = T(0);
-    if (i < n) {
-      const T s = S[i];
-      r = s > T(0) ? LA2[i] - P::log2(s) : T(0);
-    }
-    const int cnt = min(32, n - base);
-    for (int t = 0; t < cnt; ++t) {
-      const T rt = __shfl_sync(0xffffffffu, r, t);
-      const T* Drow = A.D + (size_t)(base + t) * k;
+    for (int q = 0; q < KQ; ++q) acc[q] = T(0);
+    for (int base = warp * 32; base < n; base += 8 * 32) {
+      const int i = base + lane;
+      T r = T(0);
+      if (i < n) {
+        const T s = S[i];
+        r = s > T(0) ? LA2[i] - P::log2(s) : T(0);
+      }
+      const int cnt = min(32, n - base);
+      for (int t = 0; t < cnt; ++t) {
+        const T rt = __shfl_sync(0xffffffffu, r, t);
+        const T* Drow = A.D + (size_t)(base + t) * k;
 #pragma unroll
-      for (int q = 0; q < KQ; ++q) {
-        const int j = lane + 32 * q;
-        if (j < k) acc[q] = fma(Drow[j], rt, acc[q]);
+        for (int q = 0; q < KQ; ++q) {
+          const int j = lane + 32 * q;
+          if (j < k) acc[q] = fma(Drow[j], rt, acc[q]);
+        }
       }
     }
-  }
 #pragma unroll
-  for (int q = 0; q < KQ; ++q) red_s[warp][lane + 32 * q] = acc[q];
-  __syncthreads();
+    for (int q = 0; q < KQ; ++q) red_s[warp][lane + 32 * q] = acc[q];
+    __syncthreads();
 
-  // phase B: penalty update (Table 2)
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    T sum = T(0);
+    // phase B: penalty update (Table 2)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      T sum = T(0);
 #pragma unroll
-    for (int w8 = 0; w8 < 8; ++w8) sum += red_s[w8][j];
-    const T xj = A.xcol[j];
-    const T wold = A.W[(size_t)p * k + j];
-    const T nu = P::log(wold) + sum * T(kLn2) / xj;
-    T wn;
-    if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
-    else if (A.penalty == PEN_L2SQ) {
-      const T c = A.alpha / (A.eps * xj);
-      wn = wright_omega<T>(P::log(c) + nu) / c;
-    } else wn = P::exp(nu);
-    A.W[(size_t)p * k + j] = wn;
-    w_s[j] = wn;
-  }
-  __syncthreads();
+      for (int w8 = 0; w8 < 8; ++w8) sum += red_s[w8][j];
+      const T xj = A.xcol[j];
+      const T wold = A.W[(size_t)p * k + j];
+      const T nu = P::log(wold) + sum * T(kLn2) / xj;
+      // l1 and elastic net: nu shifted by alpha/(eps x_j); squared l2 and elastic net:
+      // W0(c e^nu)/c = omega(log c + nu)/c with c = alpha resp. beta over eps x_j (App. A)
+      const T shift = (A.penalty == PEN_L1 || A.penalty == PEN_ELASTIC) ? A.alpha / (A.eps * xj) : T(0);
+      T wn;
+      if (A.penalty == PEN_L2SQ || A.penalty == PEN_ELASTIC) {
+        const T c = (A.penalty == PEN_ELASTIC ? A.beta : A.alpha) / (A.eps * xj);
+        wn = wright_omega<T>(P::log(c) + nu - shift) / c;
+      } else wn = P::exp(nu - shift);
+      A.W[(size_t)p * k + j] = wn;
+      w_s[j] = wn;
+    }
+    __syncthreads();
 
-  // phase C: source step
-  const T mass = source_marginal<T>(A.Dt, w_s, n, k, S, A.F2 + (size_t)p * n, LA2, red);
-  if (threadIdx.x == 0) A.mass[p] = mass;
+    // phase C: source step
+    const bool last = m + 1 == A.mm_steps;
+    const T mass = source_marginal<T>(A.Dt, w_s, n, k, S, last ? A.F2 + (size_t)p * n : nullptr, LA2, red);
+    if (last && threadIdx.x == 0) A.mass[p] = mass;
+    __syncthreads();
+  }
 }
 
 // S = D w0 and its mass for every problem of the batch (one CTA per problem).

@@ -53,7 +53,7 @@ struct ObjArgs {
   const double* kmass;
   double* primal; double* dual;
   int n, k, datafit, penalty;
-  double eps, lam, alpha, balanced_rtol;
+  double eps, lam, alpha, beta, balanced_rtol;
 };
 
 __device__ __forceinline__ double block_min(double v, double* red) {
@@ -154,18 +154,23 @@ __global__ void __launch_bounds__(256) objective_reduce_kernel(ObjArgs<T> A) {
   }
   __syncthreads();
 
-  // penalty value, F1* and the feasibility shift c
+  // weighted penalty, F1* and the feasibility shift c
   double R = 0.0, f1c = 0.0, c = 0.0;
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const double wj = A.W[(size_t)p * k + j];
     const double xtf = xtf_s[j];
     if (A.penalty == PEN_L1) {
-      R += wj;
+      R += A.alpha * wj;
       c = fmax(c, (-A.alpha - xtf) / (double)A.xcol[j]);
     } else if (A.penalty == PEN_L2SQ) {
-      R += 0.5 * wj * wj;
+      R += 0.5 * A.alpha * wj * wj;
       const double v = fmax(-xtf, 0.0);
       f1c += v * v / (2.0 * A.alpha);
+    } else if (A.penalty == PEN_ELASTIC) {
+      // sup_{w >= 0} (v w - alpha w - beta w^2 / 2) = (v - alpha)+^2 / (2 beta), v = -(X^T f)_j
+      R += A.alpha * wj + 0.5 * A.beta * wj * wj;
+      const double v = fmax(-xtf - A.alpha, 0.0);
+      f1c += v * v / (2.0 * A.beta);
     } else {
       c = fmax(c, -xtf / (double)A.xcol[j]);
     }
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(256) objective_reduce_kernel(ObjArgs<T> A) {
     double datafit_term;
     if (A.datafit == DF_BALANCED) datafit_term = (bal_dev <= A.balanced_rtol * ymax) ? 0.0 : CUDART_INF;
     else datafit_term = A.lam * L;
-    A.primal[p] = sf + tg - A.eps * ssum + A.eps * kmass + datafit_term + A.alpha * R;
+    A.primal[p] = sf + tg - A.eps * ssum + A.eps * kmass + datafit_term + R;
     A.dual[p] = -f1c - f2c - A.eps * (::exp(c / A.eps) * vsum - kmass);
   }
 }
@@ -233,7 +238,7 @@ cudaError_t objective_device(const Launch& L, const Workspace<T>& ws, const Solv
   ObjArgs<T> oa;
   oa.D = D; oa.xcol = ws.xcol; oa.W = ws.W; oa.y = y; oa.S = ws.S; oa.F2 = ws.F2; oa.G2 = ws.G2; oa.LB2 = ws.LB2;
   oa.G2n = ws.LA2; oa.kmass = kmass; oa.primal = primal; oa.dual = dual; oa.n = n; oa.k = k;
-  oa.datafit = sp.datafit; oa.penalty = sp.penalty; oa.eps = sp.eps; oa.lam = sp.lam; oa.alpha = sp.alpha;
+  oa.datafit = sp.datafit; oa.penalty = sp.penalty; oa.eps = sp.eps; oa.lam = sp.lam; oa.alpha = sp.alpha; oa.beta = sp.beta;
   oa.balanced_rtol = sizeof(T) == 4 ? 1e-4 : 1e-10;
   L.begin(KIND_OTHER);
   objective_reduce_kernel<T><<<batch, 256, 0, L.stream>>>(oa);

@@ -47,7 +47,9 @@ namespace {
 bool valid_enum(const otlm_config& c) {
   return (c.precision == OTLM_PREC_FP32_LOG || c.precision == OTLM_PREC_FP64 || c.precision == OTLM_PREC_BF16_TC) &&
          (c.datafit >= OTLM_DATAFIT_BALANCED && c.datafit <= OTLM_DATAFIT_L2) &&
-         (c.penalty >= OTLM_PENALTY_NONE && c.penalty <= OTLM_PENALTY_L2SQ);
+         (c.penalty >= OTLM_PENALTY_NONE && c.penalty <= OTLM_PENALTY_ELASTIC) &&
+         (c.penalty != OTLM_PENALTY_ELASTIC || (c.beta > 0 && std::isfinite(c.beta))) &&
+         c.mm_steps >= 0 && c.mm_steps <= 64;
 }
 
 size_t workspace_bytes(const otlm_config& c) {
@@ -75,6 +77,7 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
   sp.batch = batch; sp.n = n; sp.k = k; sp.eps = eps; sp.lam = lam; sp.alpha = alpha;
   sp.datafit = h->cfg.datafit; sp.penalty = h->cfg.penalty; sp.max_iter = h->cfg.max_iter;
   sp.poll_every = h->cfg.poll_every; sp.tol = h->cfg.tol;
+  sp.beta = h->cfg.beta; sp.mm_steps = h->cfg.mm_steps > 1 ? h->cfg.mm_steps : 1;
   return sp;
 }
 
@@ -217,6 +220,7 @@ otlm::RaggedArgs ragged_args(otlm_ctx* h, int batch, const int* n, const int* k,
   a.iters = iters_out; a.err = err_out; a.status = status_out;
   a.datafit = h->cfg.datafit; a.penalty = h->cfg.penalty; a.max_iter = h->cfg.max_iter;
   a.lam = (float)lam; a.alpha = (float)alpha; a.tol = (float)h->cfg.tol;
+  a.beta = (float)h->cfg.beta; a.mm_steps = h->cfg.mm_steps > 1 ? h->cfg.mm_steps : 1;
   a.n_max = h->cfg.n_max; a.k_max = h->cfg.k_max;
   a.tot_n = h->rg_tot[0]; a.tot_D = h->rg_tot[1]; a.tot_k = h->rg_tot[2];
   return a;

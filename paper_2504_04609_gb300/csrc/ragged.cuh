@@ -40,6 +40,8 @@ struct RaggedArgs {
   int* status;
   int datafit, penalty, max_iter;
   float lam, alpha, tol;
+  float beta;                     // squared-l2 weight of the elastic net
+  int mm_steps;                   // MM steps per iteration (>= 1)
   int n_max, k_max;
   long long tot_n, tot_D, tot_k;  // packed sizes of x/y, D and w (sum n, sum n k, sum k)
   int smem_floats;                // dynamic shared memory of the launch, in floats
@@ -264,33 +266,37 @@ __device__ void ragged_solve_one(const RaggedArgs& A, int p, float* sm) {
       if (A.tol > 0.f && e <= A.tol) { st = ST_CONVERGED; break; }
     }
     if (it >= A.max_iter) { st = ST_MAX_ITER; break; }
-    // MM step: nu_j = log w_j + (ln2 / x_j) sum_i D_ij (LA2_i - log2 S_i)
-    for (int j0 = 0; j0 < k; j0 += 32) {
-      const int j = j0 + lane;
-      float part = 0.f;
-      if (j < k)
-        for (int i = warp; i < n; i += NW) {
-          const float s = S[i];
-          if (s > 0.f) part = fmaf(D[(size_t)i * k + j], LA2[i] - P::log2(s), part);
-        }
-      if (j < k) red_k[warp * A.k_max + j] = part;
+    // MM step: nu_j = log w_j + (ln2 / x_j) sum_i D_ij (LA2_i - log2 S_i), then S = D w; mm_steps
+    // times with the same LA2, the last one also writing F2
+    for (int m = 0; m < A.mm_steps; ++m) {
+      for (int j0 = 0; j0 < k; j0 += 32) {
+        const int j = j0 + lane;
+        float part = 0.f;
+        if (j < k)
+          for (int i = warp; i < n; i += NW) {
+            const float s = S[i];
+            if (s > 0.f) part = fmaf(D[(size_t)i * k + j], LA2[i] - P::log2(s), part);
+          }
+        if (j < k) red_k[warp * A.k_max + j] = part;
+      }
+      __syncthreads();
+      for (int j = tid; j < k; j += NT) {
+        float sum = 0.f;
+        for (int w8 = 0; w8 < NW; ++w8) sum += red_k[w8 * A.k_max + j];
+        const float xj = xcol[j];
+        const float nu = P::log(W[j]) + sum * float(kLn2) / xj;
+        const float shift = (A.penalty == PEN_L1 || A.penalty == PEN_ELASTIC) ? A.alpha / (eps * xj) : 0.f;
+        float wn;
+        if (A.penalty == PEN_L2SQ || A.penalty == PEN_ELASTIC) {
+          const float c = (A.penalty == PEN_ELASTIC ? A.beta : A.alpha) / (eps * xj);
+          wn = wright_omega<float>(P::log(c) + nu - shift) / c;
+        } else wn = P::exp(nu - shift);
+        W[j] = wn;
+      }
+      __syncthreads();
+      const float m_mass = source_step(m + 1 == A.mm_steps);
+      if (m + 1 == A.mm_steps) mass = m_mass;
     }
-    __syncthreads();
-    for (int j = tid; j < k; j += NT) {
-      float sum = 0.f;
-      for (int w8 = 0; w8 < NW; ++w8) sum += red_k[w8 * A.k_max + j];
-      const float xj = xcol[j];
-      const float nu = P::log(W[j]) + sum * float(kLn2) / xj;
-      float wn;
-      if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (eps * xj));
-      else if (A.penalty == PEN_L2SQ) {
-        const float c = A.alpha / (eps * xj);
-        wn = wright_omega<float>(P::log(c) + nu) / c;
-      } else wn = P::exp(nu);
-      W[j] = wn;
-    }
-    __syncthreads();
-    mass = source_step(true);
     // target apply and the datafit step (Table 1) in log2 units
     ragged_apply<NT, R>(xt, F2, LB2, n, it > 0, nullptr);
     const float kl_coef = A.lam / (eps + A.lam), tv_bound = A.lam / eps_ln2, loe = A.lam / eps;

@@ -120,6 +120,8 @@ struct SolveParams {
   double eps, lam, alpha;
   int datafit, penalty, max_iter, poll_every;
   double tol;
+  double beta = 0.0;  // elastic net's squared-l2 weight
+  int mm_steps = 1;   // MM steps per iteration
 };
 
 template <typename T> struct TileFor;
@@ -231,7 +233,7 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const SolvePar
   mm.xcol = ws.xcol; mm.LA2 = ws.LA2; mm.S = ws.S; mm.F2 = ws.F2; mm.W = ws.W; mm.mass = ws.mass;
   mm.err_acc = ws.err_acc; mm.err = ws.err; mm.done = ws.done; mm.iters = ws.iters; mm.status = ws.status;
   mm.max_iter = sp.max_iter; mm.tol = T(sp.tol); mm.penalty = sp.penalty; mm.eps = T(sp.eps);
-  mm.alpha = T(sp.alpha);
+  mm.alpha = T(sp.alpha); mm.beta = T(sp.beta); mm.mm_steps = sp.mm_steps;
 
   for (int it = 0;; ++it) {
     src.check = it > 0;

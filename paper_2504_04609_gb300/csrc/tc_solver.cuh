@@ -270,7 +270,7 @@ struct TcIterArgs {
   const int* active;
   const int* n_active;
   int n, k, ld, it, max_iter, datafit, penalty;
-  float tol, eps, alpha, kl_coef, tv_bound, lam_over_eps, log_lam_over_eps;
+  float tol, eps, alpha, beta, kl_coef, tv_bound, lam_over_eps, log_lam_over_eps;
   const float* y;
   const float* D;
   const float* Dt;
@@ -407,8 +407,10 @@ __device__ __forceinline__ float tc_violation_term(float s, float an, float ao, 
   return s * fabsf(ratio - 1.f);
 }
 
-template <int NT, int EPT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) tc_violation_kernel(TcIterArgs A) {
+// RATIO_ONLY: the log ratios alone, without the convergence check (the MM steps after the first
+// of an iteration, which reuse a = K u1)
+template <int NT, int EPT, bool RATIO_ONLY>
+__device__ __forceinline__ void tc_violation_body(const TcIterArgs& A) {
   using P = Prec<float>;
   __shared__ float red[32];
   const int slot = blockIdx.x;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) tc_violation_kernel(TcI
   float* rlo = A.t.Rlo + (size_t)slot * A.t.ld;
   const float mc = A.t.Msrc[cur][p], mo = A.t.Msrc[cur ^ 1][p];
   const float f = P::exp2(mc - mo);
-  const bool check = A.it > 0;
+  const bool check = !RATIO_ONLY && A.it > 0;
   float part = 0.f;
   if constexpr (EPT > 0) {
     float s[EPT], an[EPT], ao[EPT];
@@ -461,6 +463,16 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) tc_violation_kernel(TcI
       A.done[p] = 1;
     }
   }
+}
+
+template <int NT, int EPT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) tc_violation_kernel(TcIterArgs A) {
+  tc_violation_body<NT, EPT, false>(A);
+}
+
+template <int NT, int EPT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) tc_ratio_kernel(TcIterArgs A) {
+  tc_violation_body<NT, EPT, true>(A);
 }
 
 // ---- the MM step and the source step around the two TF32 dictionary GEMMs ----------------------
@@ -509,11 +521,11 @@ __global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, i
     for (int z = 0; z < splits; ++z) sum += M.NU[z * M.plane + (size_t)slot * M.ldnu + j];
     const float xj = A.xcol[j];
     const float nu = P::log(wn) + sum * float(kLn2) / xj;
-    if (A.penalty == PEN_L1) wn = P::exp(nu - A.alpha / (A.eps * xj));
-    else if (A.penalty == PEN_L2SQ) {
-      const float c = A.alpha / (A.eps * xj);
-      wn = wright_omega_fast(P::log(c) + nu) / c;
-    } else wn = P::exp(nu);
+    const float shift = (A.penalty == PEN_L1 || A.penalty == PEN_ELASTIC) ? A.alpha / (A.eps * xj) : 0.f;
+    if (A.penalty == PEN_L2SQ || A.penalty == PEN_ELASTIC) {
+      const float c = (A.penalty == PEN_ELASTIC ? A.beta : A.alpha) / (A.eps * xj);
+      wn = wright_omega_fast(P::log(c) + nu - shift) / c;
+    } else wn = P::exp(nu - shift);
     A.W[(size_t)p * k + j] = wn;
   }
   tf32_split(wn, A.t.Whi + (size_t)slot * A.t.kp + j, A.t.Wlo + (size_t)slot * A.t.kp + j);
@@ -646,7 +658,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   TcIterArgs ta{};
   ta.active = ws.active; ta.n_active = ws.n_active; ta.n = n; ta.k = k; ta.ld = tw.ld;
   ta.max_iter = sp.max_iter; ta.datafit = sp.datafit; ta.penalty = sp.penalty;
-  ta.tol = float(sp.tol); ta.eps = float(sp.eps); ta.alpha = float(sp.alpha);
+  ta.tol = float(sp.tol); ta.eps = float(sp.eps); ta.alpha = float(sp.alpha); ta.beta = float(sp.beta);
   ta.kl_coef = float(sp.lam / (sp.eps + sp.lam)); ta.tv_bound = float(sp.lam / eps_ln2);
   ta.lam_over_eps = float(sp.lam / sp.eps); ta.log_lam_over_eps = float(log(sp.lam / sp.eps));
   ta.y = y; ta.D = D; ta.Dt = ws.Dt; ta.xcol = ws.xcol; ta.G2 = ws.G2; ta.S = ws.S; ta.F2 = ws.F2; ta.W = ws.W;
@@ -732,6 +744,23 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
     L.end();
     if (e != cudaSuccess) return e;
+    // further MM steps with the same a: log ratios from the new s, D^T r, update, s = D w
+    for (int m = 1; m < sp.mm_steps; ++m) {
+      L.begin(KIND_MM);
+      TC_ROW_LAUNCH(tc_ratio_kernel, row_cfg, batch, L.stream, ta);
+      L.end();
+      L.begin(KIND_MM);
+      e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dthi, tw.Dtlo, tw.ld, tw.Rhi, tw.Rlo, tw.ld, k, batch, n, gr, L.stream);
+      L.end();
+      if (e != cudaSuccess) return e;
+      L.begin(KIND_MM);
+      tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1);
+      L.end();
+      L.begin(KIND_MM);
+      e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
+      L.end();
+      if (e != cudaSuccess) return e;
+    }
     if (it > 0) {
       L.begin(KIND_COMPACT);
       compact_kernel<<<1, 1024, 0, L.stream>>>(ws.active, ws.n_active, ws.done);

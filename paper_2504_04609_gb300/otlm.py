@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libotlm.so")
 OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED, OTLM_ESCRATCH, OTLM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 CONVERGED, MAX_ITER, NONFINITE, INVALID = 0, 1, 2, 3
 DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3}
-PENALTY = {"none": 0, "l1": 1, "l2sq": 2}
+PENALTY = {"none": 0, "l1": 1, "l2sq": 2, "elastic": 3}
 PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 
 EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm_solve_host", "otlm_objective",
@@ -32,7 +32,8 @@ TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 class otlm_config(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int), ("k_max", ctypes.c_int), ("batch_max", ctypes.c_int),
                 ("precision", ctypes.c_int), ("datafit", ctypes.c_int), ("penalty", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("poll_every", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("poll_every", ctypes.c_int),
+                ("beta", ctypes.c_double), ("mm_steps", ctypes.c_int)]
 
 
 _LIB = None
@@ -127,12 +128,15 @@ class SolveResult:
 
 
 class Handle:
-    """Owns one otlm handle (workspace sized for n_max x k_max x batch_max)."""
+    """Owns one otlm handle (workspace sized for n_max x k_max x batch_max).
+
+    beta: squared-l2 weight of the "elastic" penalty (alpha sum w + (beta/2) ||w||^2);
+    mm_steps: MM steps of the weight update per iteration (1 in Algorithm 1)."""
 
     def __init__(self, n_max, k_max, batch_max, precision="fp32", datafit="kl", penalty="l2sq",
-                 max_iter=1000, tol=0.0, poll_every=8, stream=None):
+                 max_iter=1000, tol=0.0, poll_every=8, stream=None, beta=0.0, mm_steps=1):
         self.cfg = otlm_config(n_max, k_max, batch_max, PRECISION[precision], DATAFIT[datafit], PENALTY[penalty],
-                               max_iter, float(tol), poll_every)
+                               max_iter, float(tol), poll_every, float(beta), mm_steps)
         self.precision = precision
         self._h = ctypes.c_void_p()
         _check(lib().otlm_create(ctypes.byref(self._h), ctypes.byref(self.cfg), stream), "otlm_create")
@@ -226,7 +230,7 @@ def solve_noalloc(x, D, y, eps, lam, alpha, datafit, penalty, max_iter, tol, w, 
 
 
 def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000, tol=0.0,
-          precision="fp32", poll_every=8):
+          precision="fp32", poll_every=8, beta=0.0, mm_steps=1):
     """One-shot convenience: allocate a handle sized for this problem and solve on the GPU.
 
     Inputs are torch CUDA tensors of the handle's dtype.  Returns SolveResult of CUDA tensors.
@@ -235,7 +239,7 @@ def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000
     B, n = y.shape
     k = D.shape[1]
     h = Handle(n, k, B, precision, datafit, penalty, max_iter, tol, poll_every,
-               stream=torch.cuda.current_stream().cuda_stream)
+               stream=torch.cuda.current_stream().cuda_stream, beta=beta, mm_steps=mm_steps)
     dt = torch.float64 if precision == "fp64" else torch.float32
     w = w0.clone()
     g = torch.zeros_like(y) if g0 is None else g0.clone()
