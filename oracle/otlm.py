@@ -33,6 +33,7 @@ Poisson (Table 1, last row) is not implemented.
 from __future__ import annotations
 
 import numpy as np
+from scipy.sparse import issparse
 from scipy.special import lambertw, logsumexp, wrightomega
 
 DATAFITS = ("balanced", "kl", "tv", "l2")
@@ -163,12 +164,13 @@ def mm_step_log(penalty, log_a, w_prev, X, eps, alpha, beta=0.0):
     Since Z_ij a_i / X_ij = w'_j a_i / s_i with s = X w' (wherever X_ij > 0), Table 2's
     exponent becomes nu_j = log w'_j + (1/x_j) sum_{i: s_i > 0} X_ij (log a_i - log s_i).
     The squared-l2 update is evaluated as omega(log c_j + nu_j) / c_j, which equals
-    W0(c_j e^{nu_j}) / c_j but never overflows.
+    W0(c_j e^{nu_j}) / c_j but never overflows.  X may be a dense array or a scipy.sparse matrix
+    (the products X w and X^T r are the same either way).
     """
-    X = np.asarray(X, dtype=np.float64)
+    X = X if issparse(X) else np.asarray(X, dtype=np.float64)
     w_prev = np.asarray(w_prev, dtype=np.float64)
     s = X @ w_prev
-    x = X.sum(axis=0)
+    x = np.asarray(X.sum(axis=0), dtype=np.float64).ravel()
     with np.errstate(divide="ignore", invalid="ignore"):
         r = np.where(s > 0, log_a - np.log(np.where(s > 0, s, 1.0)), 0.0)
         nu = np.log(w_prev) + (X.T @ r) / x
@@ -335,6 +337,86 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
     Q = np.exp(logQ)
     return dict(w=w, f=f, g=g, Q=Q, iters=it, err=err, err_hist=np.array(hist),
                 t=Q.sum(axis=0), s=Q.sum(axis=1), log_a=log_a)
+
+
+def band_to_dense(Cd, h):
+    """Dense C [n, n] from the diagonal (DIA) storage Cd [2h+1, n] of a banded cost:
+    C_{i, i+d-h} = Cd[d, i]; every pair outside the band, or stored as +inf, is forbidden
+    (C = +inf, K = 0)."""
+    Cd = np.asarray(Cd, dtype=np.float64)
+    n = Cd.shape[1]
+    C = np.full((n, n), np.inf)
+    for d in range(2 * h + 1):
+        for i in range(n):
+            j = i + d - h
+            if 0 <= j < n:
+                C[i, j] = Cd[d, i]
+    return C
+
+
+def _band_lse_rows(v, Cd, h, eps):
+    """log sum_j exp((v_j - C_ij) / eps) over the band of row i: j = i + d - h."""
+    n = v.shape[0]
+    terms = np.full((n, 2 * h + 1), -np.inf)
+    for d in range(2 * h + 1):
+        lo, hi = max(0, h - d), min(n, n + h - d)  # rows whose j = i + d - h lies in [0, n)
+        i = np.arange(lo, hi)
+        with np.errstate(invalid="ignore"):
+            terms[i, d] = (v[i + d - h] - Cd[d, i]) / eps
+    return logsumexp(terms, axis=1)
+
+
+def _band_lse_cols(v, Cd, h, eps):
+    """log sum_i exp((v_i - C_ij) / eps) over the band of column j: i = j + e - h, whose cost
+    C_{i, j} sits in diagonal 2h - e of row i."""
+    n = v.shape[0]
+    terms = np.full((n, 2 * h + 1), -np.inf)
+    for e in range(2 * h + 1):
+        lo, hi = max(0, h - e), min(n, n + h - e)
+        j = np.arange(lo, hi)
+        i = j + e - h
+        with np.errstate(invalid="ignore"):
+            terms[j, e] = (v[i] - Cd[2 * h - e, i]) / eps
+    return logsumexp(terms, axis=1)
+
+
+def solve_log_banded(Cd, h, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g0=None, beta=0.0,
+                     mm_steps=1):
+    """`solve_log` for a banded cost given in diagonal storage (C = +inf off the band: K_ij = 0
+    there, so the sums of Algorithm 1 run over the band only) and a dictionary X that may be a
+    scipy.sparse matrix.  Same iteration, stopping rule, arguments and outputs as `solve_log`,
+    except Q, which is not formed."""
+    Cd = np.asarray(Cd, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    g = np.zeros(y.shape[0]) if g0 is None else np.asarray(g0, dtype=np.float64).copy()
+    f = None
+    w = np.asarray(w0, dtype=np.float64).copy()
+    s = None
+    err = np.nan
+    hist = []
+    it = 0
+    log_a = None
+    log_b = None
+    for it in range(n_iter + 1):
+        log_a = _band_lse_rows(g, Cd, h, eps)
+        if it > 0:
+            err = float(np.sum(np.abs(s * np.expm1(log_a - log_a_old))) / np.sum(s))
+            hist.append(err)
+            if tol > 0 and err <= tol:
+                break
+        if it == n_iter:
+            break
+        for _ in range(mm_steps):
+            w = mm_step_log(penalty, log_a, w, X, eps, alpha, beta)
+        s = X @ w
+        with np.errstate(divide="ignore"):
+            f = eps * (np.log(s) - log_a)
+        log_a_old = log_a
+        log_b = _band_lse_cols(f, Cd, h, eps)
+        g = _log_datafit_potential(datafit, log_b, y, eps, lam)
+    # t = Q^T 1 = u1 * K^T u2 of the returned state
+    t = np.exp(g / eps + log_b) if log_b is not None else None
+    return dict(w=w, f=f, g=g, iters=it, err=err, err_hist=np.array(hist), t=t, s=s, log_a=log_a)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -121,6 +121,89 @@ def ragged(workload: int, count: int, n_range=(256, 4096), k_range=(8, 128), eps
     return out
 
 
+def scaling_dictionary(n: int, k: int, sigma_b: float = 2.0, trunc: float = 5.0):
+    """Sparse dictionary of the paper's scalability test (App. "Performance Scalability Tests"):
+    k Gaussians of height 1 on the sample grid x_i = i, means m n / k (m = 0..k-1), width sigma_b,
+    truncated at +-trunc sigma_b.  Returns CSC arrays (col_ptr [k+1] int32, row_idx [nnz] int32,
+    val [nnz] float64), rows ascending within each column."""
+    half = int(np.floor(trunc * sigma_b))
+    col_ptr = [0]
+    rows, vals = [], []
+    for m in range(k):
+        mu = m * n / k
+        lo, hi = max(0, int(np.ceil(mu - trunc * sigma_b))), min(n - 1, int(np.floor(mu + trunc * sigma_b)))
+        i = np.arange(lo, hi + 1)
+        rows.append(i)
+        vals.append(np.exp(-0.5 * ((i - mu) / sigma_b) ** 2))
+        col_ptr.append(col_ptr[-1] + i.size)
+    assert half >= 0
+    return (np.asarray(col_ptr, dtype=np.int32), np.concatenate(rows).astype(np.int32),
+            np.concatenate(vals))
+
+
+def truncated_cost_band(n: int, rho: float = 0.01, delta: float = 10.0):
+    """Cost of the scalability test, C_ij = rho |x_i - x_j| when |x_i - x_j| < delta, +inf
+    otherwise, on x_i = i, in diagonal storage: Cd[d, i] = C(i, i + d - h) with half-width
+    h = ceil(delta) - 1, +inf where i + d - h falls outside [0, n).  Returns (Cd [2h+1, n], h)."""
+    h = int(np.ceil(delta)) - 1
+    Cd = np.full((2 * h + 1, n), np.inf)
+    i = np.arange(n)
+    for d in range(2 * h + 1):
+        j = i + d - h
+        ok = (j >= 0) & (j < n) & (np.abs(d - h) < delta)
+        Cd[d, ok] = rho * np.abs(d - h)
+    return Cd, h
+
+
+def _skew_normal(x, mu, sigma, gamma):
+    from scipy.special import ndtr
+    z = (x - mu) / sigma
+    return 2.0 / sigma * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi) * ndtr(gamma * z)
+
+
+def scaling_target(n: int, k: int, rng: np.random.Generator) -> np.ndarray:
+    """Target of the scalability test: y_i = sum_m a_m f(x_i; mu_m, sigma_m, gamma_m) + |n_i| with
+    k skew-normal components, mu ~ U[0, n], sigma ~ |N(2, 0.2)|, a ~ |N(1, 0.2)| + 0.01,
+    gamma ~ N(0, 2), noise n_i ~ N(0, 0.002).  Each component is evaluated within +-12 sigma_m of
+    its mean (beyond that the density is below 1e-31 of its peak)."""
+    mu = rng.uniform(0.0, n, size=k)
+    sigma = np.abs(rng.normal(2.0, 0.2, size=k))
+    amp = np.abs(rng.normal(1.0, 0.2, size=k)) + 0.01
+    gamma = rng.normal(0.0, 2.0, size=k)
+    noise = np.abs(rng.normal(0.0, 0.002, size=n))
+    y = noise.copy()
+    for m in range(k):
+        lo, hi = max(0, int(mu[m] - 12 * sigma[m])), min(n, int(mu[m] + 12 * sigma[m]) + 2)
+        x = np.arange(lo, hi, dtype=np.float64)
+        y[lo:hi] += amp[m] * _skew_normal(x, mu[m], sigma[m], gamma[m])
+    return y
+
+
+def scaling_batch(workload: int, B: int, n: int, k: int = None, dtype=np.float32, first: int = 0):
+    """B targets of the scalability test sharing its cost band and dictionary (k = n / 10 by
+    default).  Returns dict(Cd [2h+1, n], h, col_ptr, row_idx, val, y [B, n], x_col [k]) with Cd,
+    val and y rounded to `dtype`; x_col are the column masses of the rounded dictionary (float64).
+    Target p comes from child stream (workload, 3, first + p)."""
+    k = n // 10 if k is None else k
+    Cd, h = truncated_cost_band(n)
+    col_ptr, row_idx, val = scaling_dictionary(n, k)
+    Y = np.stack([scaling_target(n, k, _rng(workload, 3, first + p)) for p in range(B)])
+    val = to_dtype(val, dtype)
+    x_col = np.add.reduceat(val.astype(np.float64), col_ptr[:-1])
+    return dict(Cd=to_dtype(Cd, dtype), h=h, col_ptr=col_ptr, row_idx=row_idx, val=val,
+                y=to_dtype(Y, dtype), x_col=x_col, n=n, k=k)
+
+
+def csc_to_dense(n: int, col_ptr, row_idx, val) -> np.ndarray:
+    """Dense [n, k] copy of a CSC dictionary (for small cases)."""
+    k = len(col_ptr) - 1
+    D = np.zeros((n, k))
+    for m in range(k):
+        for q in range(col_ptr[m], col_ptr[m + 1]):
+            D[row_idx[q], m] = val[q]
+    return D
+
+
 def initial_weights(y: np.ndarray, D: np.ndarray) -> np.ndarray:
     """Cold-start weights w0_j = sum(y) / (k * x_j), x_j the column mass of D.
 
@@ -154,4 +237,8 @@ WORKLOADS = {
     # per iteration; the same datafit and penalty as the n=4096 batch
     "hbm_single_n16384_l2_l2sq": dict(id=6, B=1, n=16384, k=128, nnz=5, eps=1e-2, datafit="l2", lam=1.0,
                                       penalty="l2sq", alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
+    # the paper's scalability test at its largest size: truncated cost rho |x_i - x_j| (< 10 samples),
+    # k = n / 10 truncated Gaussians, OT ridge (L2 datafit, squared-l2 penalty), 32 targets
+    "banded32_n100000_ridge": dict(id=7, B=32, n=100000, eps=1e-3, datafit="l2", lam=1.0, penalty="l2sq",
+                                   alpha=1e-3, iters=2000, tol=1e-5, dtype=np.float32),
 }

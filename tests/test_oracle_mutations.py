@@ -134,3 +134,19 @@ def test_wrong_elastic_conjugate_is_caught(monkeypatch):
         return good(penalty, f, X, alpha, beta)
     monkeypatch.setattr(ot, "_F1_conj_neg", bad)
     assert _fails(pins.test_invariants_along_the_trajectory, "kl", "elastic")
+
+
+def test_transposed_target_band_is_caught(monkeypatch):
+    """The target apply reading column j's costs from diagonal e instead of 2h - e (the source
+    apply's band transposed wrongly)."""
+    def bad(v, Cd, h, eps):
+        n = v.shape[0]
+        terms = np.full((n, 2 * h + 1), -np.inf)
+        for e in range(2 * h + 1):
+            lo, hi = max(0, h - e), min(n, n + h - e)
+            j = np.arange(lo, hi)
+            with np.errstate(invalid="ignore"):
+                terms[j, e] = (v[j + e - h] - Cd[e, j + e - h]) / eps
+        return ot.logsumexp(terms, axis=1)
+    monkeypatch.setattr(ot, "_band_lse_cols", bad)
+    assert _fails(pins.test_banded_solve_equals_the_dense_solve, "l2", "l2sq")

@@ -348,3 +348,50 @@ def test_balanced_target_marginal_met():
     y = d["y"][0]
     r = oracle.solve(C, d["D"], y, 0.05, 1.0, 0.0, "balanced", "none", spectra.initial_weights(y, d["D"]), 10)
     np.testing.assert_allclose(r["t"], y, rtol=1e-12)
+
+
+# --- banded cost in diagonal storage, sparse dictionary (the scalability test's form) ----------
+
+def _banded_case(n=60, h=5, k=6, seed=21):
+    """A non-symmetric truncated cost (a drift term for i > j, holes inside the band) written as a
+    dense matrix, and its diagonal storage Cd[d, i] = C[i, i + d - h] built here from it."""
+    rng = np.random.default_rng(seed)
+    C = np.full((n, n), np.inf)
+    for i in range(n):
+        for j in range(max(0, i - h), min(n, i + h + 1)):
+            C[i, j] = 0.01 * abs(i - j) + 0.004 * max(i - j, 0)
+    holes = rng.choice(n, size=6, replace=False)
+    for i in holes:
+        j = min(n - 1, i + 2)
+        if j != i:
+            C[i, j] = np.inf
+    Cd = np.full((2 * h + 1, n), np.inf)
+    for d in range(2 * h + 1):
+        for i in range(n):
+            if 0 <= i + d - h < n:
+                Cd[d, i] = C[i, i + d - h]
+    col_ptr, row_idx, val = spectra.scaling_dictionary(n, k)
+    X = spectra.csc_to_dense(n, col_ptr, row_idx, val)
+    y = spectra.scaling_target(n, k, rng)
+    return C, Cd, X, y
+
+
+def test_band_to_dense_inverts_the_diagonal_storage():
+    C, Cd, _, _ = _banded_case()
+    np.testing.assert_array_equal(oracle.band_to_dense(Cd, 5), C)
+
+
+@pytest.mark.parametrize("datafit,penalty", [("l2", "l2sq"), ("tv", "l1"), ("kl", "elastic")])
+def test_banded_solve_equals_the_dense_solve(datafit, penalty):
+    """Forbidden pairs have K = 0, so summing Algorithm 1's applies over the band must reproduce
+    the dense solve on the same cost; the cost is not symmetric, so reading the target apply's band
+    from the wrong diagonal changes the result."""
+    from scipy.sparse import csc_matrix
+    C, Cd, X, y = _banded_case()
+    eps, lam, alpha = 5e-3, 1.0, 1e-3
+    w0 = np.full(X.shape[1], y.sum() / X.sum())
+    a = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, 40, beta=BETA)
+    b = oracle.solve_log_banded(Cd, 5, csc_matrix(X), y, eps, lam, alpha, datafit, penalty, w0, 40, beta=BETA)
+    np.testing.assert_allclose(b["w"], a["w"], rtol=1e-11)
+    np.testing.assert_allclose(b["t"], a["t"], rtol=1e-10, atol=1e-300)
+    np.testing.assert_allclose(b["err_hist"], a["err_hist"], rtol=1e-8)
