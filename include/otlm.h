@@ -161,6 +161,33 @@ int otlm_solve_host(otlm_handle h, int batch, int n, int k,
                     void* w, void* g, void* t_out,
                     int* iters_out, void* err_out, int* status_out);
 
+/* Solve `batch` problems sharing a BANDED cost and a SPARSE dictionary (Algorithm 1, FP32 log
+ * domain; the form of the paper's scalability test, App. "Performance Scalability Tests": a cost
+ * truncated to +inf beyond a distance, so K_ij = 0 off a band, and k = n/10 truncated basis
+ * functions).  K is never formed; both applies are log-sum-exps over the band.
+ *   Cd       [2hw+1][n]  cost in diagonal storage: Cd[d][i] = C(i, i + d - hw); +inf marks a
+ *                        forbidden pair (K = 0) and pads the diagonals where i + d - hw falls
+ *                        outside [0, n) (entries there are ignored).  No NaN or -inf.
+ *   hw                   half-width of the band, 0..64 and < n
+ *   col_ptr [k+1], row_idx [nnz], val [nnz]   the dictionary X [n][k] in CSC form (int32 and
+ *                        float, device memory): column m holds rows row_idx[col_ptr[m] ..
+ *                        col_ptr[m+1]) with values >= 0; col_ptr[0] = 0, col_ptr[k] = nnz; every
+ *                        column sum > 0.  Not modified; a CSR copy is built in the workspace.
+ *   y [batch][n], w [batch][k] (in/out), g [batch][n] (in/out or NULL), t_out, iters_out,
+ *   err_out, status_out: as otlm_solve (float, device memory).
+ * The handle must be OTLM_PREC_FP32_LOG with mm_steps <= 1 (else OTLM_EUNSUPPORTED); datafit,
+ * penalty, beta, max_iter, tol and poll_every come from it; batch <= batch_max, while n and k are
+ * not bounded by n_max and k_max: the banded workspace (about 4 (6 batch n + batch k + (2hw+1) n
+ * + 2 nnz + 3 n) bytes) is allocated on the first call and grown when a later call needs more.
+ * The band and dictionary are validated on the device before use (one host synchronisation).
+ * Errors: OTLM_EINVAL (sizes, eps, lam, alpha as otlm_solve, hw out of range, NULL pointers, a
+ * malformed band or dictionary), OTLM_EUNSUPPORTED, OTLM_ENOMEM, OTLM_ECUDA. */
+int otlm_solve_banded(otlm_handle h, int batch, int n, int hw, const float* Cd,
+                      int k, int nnz, const int* col_ptr, const int* row_idx, const float* val,
+                      const float* y, double eps, double lam, double alpha,
+                      float* w, float* g, float* t_out, int* iters_out, float* err_out,
+                      int* status_out);
+
 /* Solve an UNEVEN batch in one persistent launch (Algorithm 1 per problem, FP32 log domain):
  * problem p has its own grid size n[p] (2..n_max, n_max <= 4096), dictionary size k[p]
  * (1..k_max), eps[p] > 0, grid, dictionary and target.  Arrays are concatenated over problems:

@@ -1,0 +1,515 @@
+// Algorithm 1 for a banded cost and a sparse dictionary (the paper's scalability test: a cost
+// truncated to C = +inf beyond a distance, so K_ij = 0 off a band of half-width h, and k = n/10
+// truncated basis functions), FP32 in the log domain.
+//
+// The cost comes in diagonal storage Cd[d][i] = C(i, i + d - h), d = 0..2h (+inf: no pair).  K is
+// never formed: both applies are log-sum-exps over the 2h + 1 entries of a row (source) or a
+// column (target) of the band,
+//   LA2_i = log2 sum_d 2^(G2_{i+d-h} - C2[d][i]),   LB2_j = log2 sum_e 2^(F2_{j+e-h} - C2[2h-e][j+e-h]),
+// with C2 = C / (eps ln2) (the target apply finds C(i, j), i = j + e - h, in diagonal 2h - e of
+// row i).  The dictionary is used in two sparse forms: the caller's CSC for D^T r (one thread
+// per atom) and a CSR copy built here for s = D w (one thread per row).
+//
+// One iteration is three launches over (tiles of TN bins or atoms) x problems:
+//   band_source_kernel : LA2 (source apply), the violation numerator per tile and the log ratios
+//                        r_i = LA2_i - log2 S_i for the MM step
+//   band_mm_kernel     : per problem, the stop decision from the tile partials (fixed order), then
+//                        Table 2's MM step per atom
+//   band_target_kernel : s = D w on the tile and its halo, F2 = log2 s - LA2, the target apply and
+//                        the datafit prox (Table 1); the tile's mass partial
+// A problem that stops keeps the state of its last completed iteration; later launches skip it.
+#pragma once
+
+#include "solver.cuh"
+
+namespace otlm {
+
+constexpr int BAND_TN = 1024;      // bins per tile
+constexpr int BAND_NT = 256;       // threads per CTA
+constexpr int BAND_HMAX = 64;      // largest half-width
+
+struct BandArgs {
+  int batch, n, k, h, tiles, it, max_iter, datafit, penalty;
+  float tol, eps, alpha, beta, kl_coef, tv_bound, lam_over_eps, log_lam_over_eps;
+  const float* C2;        // [2h+1][n] C / (eps ln2)
+  const int* col_ptr;     // [k+1]  CSC of D
+  const int* row_idx;     // [nnz]
+  const float* val;       // [nnz]
+  const int* row_ptr;     // [n+1]  CSR copy of D
+  const int* col_idx;     // [nnz]
+  const float* rval;      // [nnz]
+  const float* xcol;      // [k] column masses
+  const float* y;         // [B][n]
+  float* G2;              // [B][n] target potential / (eps ln2)
+  float* LA2;             // [B][n] log2 K u1 (previous iteration's on entry to the source kernel)
+  float* LB2;             // [B][n] log2 K^T u2
+  float* S;               // [B][n] D w
+  float* R;               // [B][n] log ratios
+  float* W;               // [B][k]
+  float* vpart;           // [B][tiles] violation numerators
+  float* mpart;           // [B][tiles] masses sum_i S_i
+  float* err;             // [B]
+  int* done;
+  int* iters;
+  int* status;
+  int* remaining;         // problems not yet stopped
+};
+
+__device__ __forceinline__ float band_lse_tail(float m, float sum) {
+  return m > -CUDART_INF_F ? m + Prec<float>::log2(sum) : -CUDART_INF_F;
+}
+
+__global__ void __launch_bounds__(BAND_NT) band_source_kernel(BandArgs A) {
+  using P = Prec<float>;
+  __shared__ float gs[BAND_TN + 2 * BAND_HMAX];
+  __shared__ float red[32];
+  const int tile = blockIdx.x, p = blockIdx.y;
+  if (A.done[p]) return;
+  const int n = A.n, h = A.h, W = 2 * h + 1;
+  const int t0 = tile * BAND_TN;
+  const size_t off = (size_t)p * n;
+  for (int q = threadIdx.x; q < BAND_TN + 2 * h; q += BAND_NT) {
+    const int j = t0 - h + q;
+    gs[q] = (j >= 0 && j < n) ? A.G2[off + j] : -CUDART_INF_F;
+  }
+  __syncthreads();
+  const bool check = A.it > 0;
+  float part = 0.f;
+  for (int q = threadIdx.x; q < BAND_TN; q += BAND_NT) {
+    const int i = t0 + q;
+    if (i >= n) break;
+    float m = -CUDART_INF_F;
+    for (int d = 0; d < W; ++d) m = fmaxf(m, gs[q + d] - A.C2[(size_t)d * n + i]);
+    float sum = 0.f;
+    if (m > -CUDART_INF_F)
+      for (int d = 0; d < W; ++d) sum += P::exp2(gs[q + d] - A.C2[(size_t)d * n + i] - m);
+    const float la = band_lse_tail(m, sum);
+    const float s = A.S[off + i];
+    if (check && s > 0.f) part += s * fabsf(P::exp2(la - A.LA2[off + i]) - 1.f);
+    A.LA2[off + i] = la;
+    A.R[off + i] = s > 0.f ? la - P::log2(s) : 0.f;
+  }
+  if (!check) return;
+  part = block_sum(part, red);
+  if (threadIdx.x == 0) A.vpart[(size_t)p * A.tiles + tile] = part;
+}
+
+// Sum of a problem's tile partials in a fixed order (lane-strided, then a fixed shuffle tree).
+__device__ __forceinline__ float band_tile_sum(const float* part, int tiles) {
+  const int lane = threadIdx.x & 31;
+  float v = 0.f;
+  for (int t = lane; t < tiles; t += 32) v += part[t];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(BAND_NT) band_mm_kernel(BandArgs A) {
+  using P = Prec<float>;
+  __shared__ int stop;
+  const int p = blockIdx.y;
+  if (A.done[p]) return;
+  if (A.it > 0) {
+    if (threadIdx.x < 32) {
+      const float num = band_tile_sum(A.vpart + (size_t)p * A.tiles, A.tiles);
+      const float mass = band_tile_sum(A.mpart + (size_t)p * A.tiles, A.tiles);
+      if (threadIdx.x == 0) {
+        const float e = num / mass;
+        int st = -1;
+        if (e != e) st = ST_NONFINITE;
+        else if (A.tol > 0.f && e <= A.tol) st = ST_CONVERGED;
+        else if (A.it >= A.max_iter) st = ST_MAX_ITER;
+        if (blockIdx.x == 0) {
+          A.err[p] = e;
+          if (st >= 0) {
+            A.status[p] = st;
+            A.iters[p] = A.it;
+            A.done[p] = 1;
+            atomicSub(A.remaining, 1);
+          }
+        }
+        stop = st >= 0;
+      }
+    }
+    __syncthreads();
+    if (stop) return;
+  }
+  const int m = blockIdx.x * BAND_NT + threadIdx.x;
+  if (m >= A.k) return;
+  const float* R = A.R + (size_t)p * A.n;
+  float acc = 0.f;
+  for (int q = A.col_ptr[m]; q < A.col_ptr[m + 1]; ++q) acc = fmaf(A.val[q], R[A.row_idx[q]], acc);
+  const float xj = A.xcol[m];
+  float* Wp = A.W + (size_t)p * A.k;
+  const float nu = P::log(Wp[m]) + acc * float(kLn2) / xj;
+  const float shift = (A.penalty == PEN_L1 || A.penalty == PEN_ELASTIC) ? A.alpha / (A.eps * xj) : 0.f;
+  float wn;
+  if (A.penalty == PEN_L2SQ || A.penalty == PEN_ELASTIC) {
+    const float c = (A.penalty == PEN_ELASTIC ? A.beta : A.alpha) / (A.eps * xj);
+    wn = wright_omega<float>(P::log(c) + nu - shift) / c;
+  } else wn = P::exp(nu - shift);
+  Wp[m] = wn;
+}
+
+__device__ __forceinline__ float band_datafit(const BandArgs& A, float v, float yv) {
+  using P = Prec<float>;
+  switch (A.datafit) {
+    case DF_BALANCED: return P::log2(yv) - v;
+    case DF_KL: return A.kl_coef * (P::log2(yv) - v);
+    case DF_TV: return fminf(fmaxf(P::log2(yv) - v, -A.tv_bound), A.tv_bound);
+    default: {
+      const float z = A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
+      return (A.lam_over_eps * yv - wright_omega_fast(z)) * float(kLog2e);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BAND_NT) band_target_kernel(BandArgs A) {
+  using P = Prec<float>;
+  __shared__ float fs[BAND_TN + 2 * BAND_HMAX];
+  __shared__ float red[32];
+  const int tile = blockIdx.x, p = blockIdx.y;
+  if (A.done[p]) return;
+  const int n = A.n, h = A.h, W = 2 * h + 1;
+  const int t0 = tile * BAND_TN;
+  const size_t off = (size_t)p * n;
+  const float* Wp = A.W + (size_t)p * A.k;
+  float mass = 0.f;
+  // source step on the tile and its halo: s = D w (rows in CSR), F2 = log2 s - LA2
+  for (int q = threadIdx.x; q < BAND_TN + 2 * h; q += BAND_NT) {
+    const int i = t0 - h + q;
+    float f2 = -CUDART_INF_F;
+    if (i >= 0 && i < n) {
+      float s = 0.f;
+      for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) s = fmaf(A.rval[e], Wp[A.col_idx[e]], s);
+      // a subnormal mass counts as 0, as in the other FP32 paths (log2 flushes it to -inf)
+      if (s < P::tiny()) s = 0.f;
+      if (s > 0.f) f2 = P::log2(s) - A.LA2[off + i];
+      if (q >= h && q < h + BAND_TN) {
+        A.S[off + i] = s;
+        mass += s;
+      }
+    }
+    fs[q] = f2;
+  }
+  __syncthreads();
+  // target apply and the datafit prox
+  for (int q = threadIdx.x; q < BAND_TN; q += BAND_NT) {
+    const int j = t0 + q;
+    if (j >= n) break;
+    float m = -CUDART_INF_F;
+    for (int e = 0; e < W; ++e) {
+      const int i = j + e - h;
+      if (i >= 0 && i < n) m = fmaxf(m, fs[q + e] - A.C2[(size_t)(2 * h - e) * n + i]);
+    }
+    float sum = 0.f;
+    if (m > -CUDART_INF_F)
+      for (int e = 0; e < W; ++e) {
+        const int i = j + e - h;
+        if (i >= 0 && i < n) sum += P::exp2(fs[q + e] - A.C2[(size_t)(2 * h - e) * n + i] - m);
+      }
+    const float lb = band_lse_tail(m, sum);
+    A.LB2[off + j] = lb;
+    A.G2[off + j] = band_datafit(A, lb, A.y[off + j]);
+  }
+  mass = block_sum(mass, red);
+  if (threadIdx.x == 0) A.mpart[(size_t)p * A.tiles + tile] = mass;
+}
+
+// ---- set-up: scaled cost band, CSR copy of the dictionary, column masses, initial state -------
+
+// C2[d][i] = Cd[d][i] / (eps ln2); any NaN or -inf entry flags the input as invalid.
+__global__ void band_cost_kernel(const float* Cd, float* C2, size_t count, float inv, int* bad) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x) {
+    const float c = Cd[q];
+    if (c != c || c == -CUDART_INF_F) atomicOr(bad, 1);
+    C2[q] = c * inv;
+  }
+}
+
+// Per atom: the column's entries must lie in [0, n) with non-negative values, its pointers must
+// be ordered and its mass positive; counts entries per row.
+__global__ void band_csc_check_kernel(const int* col_ptr, const int* row_idx, const float* val, int n, int k,
+                                      int nnz, float* xcol, int* cnt, int* bad) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > k) return;
+  if (m == k) {
+    if (col_ptr[0] != 0 || col_ptr[k] != nnz) atomicOr(bad, 1);
+    return;
+  }
+  const int a = col_ptr[m], b = col_ptr[m + 1];
+  if (a < 0 || b < a || b > nnz) {
+    atomicOr(bad, 1);
+    return;
+  }
+  float s = 0.f;
+  for (int q = a; q < b; ++q) {
+    const int r = row_idx[q];
+    const float v = val[q];
+    if (r < 0 || r >= n || !(v >= 0.f)) {
+      atomicOr(bad, 1);
+      continue;
+    }
+    atomicAdd(cnt + r, 1);
+    s += v;
+  }
+  xcol[m] = s;
+  if (!(s > 0.f)) atomicOr(bad, 1);
+}
+
+// Exclusive scan of the row counts into row_ptr [n+1] (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) band_scan_kernel(const int* cnt, int* row_ptr, int n) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int wv = warp_tot[lane];
+      int wi = wv;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      warp_tot[lane] = wi - wv;
+    }
+    __syncthreads();
+    const int carry = carry_s;
+    if (i < n) row_ptr[i] = carry + warp_tot[warp] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = carry + warp_tot[31] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) row_ptr[n] = carry_s;
+}
+
+// Scatter the CSC entries into their rows (positions by atomics), then sort every row by atom
+// index so that the row sums of s = D w run in a fixed order.
+__global__ void band_fill_kernel(const int* col_ptr, const int* row_idx, const float* val, int k, const int* row_ptr,
+                                 int* fill, int* col_idx, float* rval) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= k) return;
+  for (int q = col_ptr[m]; q < col_ptr[m + 1]; ++q) {
+    const int r = row_idx[q];
+    const int pos = row_ptr[r] + atomicAdd(fill + r, 1);
+    col_idx[pos] = m;
+    rval[pos] = val[q];
+  }
+}
+
+__global__ void band_sort_rows_kernel(const int* row_ptr, int* col_idx, float* rval, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int a = row_ptr[i], b = row_ptr[i + 1];
+  for (int q = a + 1; q < b; ++q) {  // insertion sort by (atom, value): rows hold a few entries
+    const int c = col_idx[q];
+    const float v = rval[q];
+    int t = q - 1;
+    while (t >= a && (col_idx[t] > c || (col_idx[t] == c && rval[t] > v))) {
+      col_idx[t + 1] = col_idx[t];
+      rval[t + 1] = rval[t];
+      --t;
+    }
+    col_idx[t + 1] = c;
+    rval[t + 1] = v;
+  }
+}
+
+// Initial state per problem: W = w0, G2 = g0 / (eps ln2) (0 for a cold start), S = D w0 (CSR rows),
+// status MAX_ITER, not done.  One thread per (problem, row) for G2 and S, per (problem, atom) for W.
+__global__ void band_init_kernel(BandArgs A, const float* w0, const float* g0, float gscale) {
+  const size_t rows = (size_t)A.batch * A.n, atoms = (size_t)A.batch * A.k;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < atoms; q += (size_t)gridDim.x * blockDim.x)
+    A.W[q] = w0[q];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < rows; q += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(q / A.n), i = (int)(q - (size_t)p * A.n);
+    A.G2[q] = g0 ? g0[q] * gscale : 0.f;
+    float s = 0.f;
+    for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) s = fmaf(A.rval[e], w0[(size_t)p * A.k + A.col_idx[e]], s);
+    A.S[q] = s < Prec<float>::tiny() ? 0.f : s;
+    A.LB2[q] = -CUDART_INF_F;
+  }
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)A.batch;
+       q += (size_t)gridDim.x * blockDim.x) {
+    A.done[q] = 0;
+    A.iters[q] = 0;
+    A.status[q] = ST_MAX_ITER;
+    A.err[q] = CUDART_NAN_F;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.remaining = A.batch;
+}
+
+// Outputs: w, g = G2 eps ln2, t = Q^T 1 = 2^(G2 + LB2) (0 before the first target step), iters,
+// err, status.
+__global__ void band_finalize_kernel(BandArgs A, float* w_out, float* g_out, float* t_out, int* iters_out,
+                                     float* err_out, int* status_out, float gscale_inv) {
+  const size_t rows = (size_t)A.batch * A.n, atoms = (size_t)A.batch * A.k;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < atoms; q += (size_t)gridDim.x * blockDim.x)
+    w_out[q] = A.W[q];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < rows; q += (size_t)gridDim.x * blockDim.x) {
+    if (g_out) g_out[q] = A.G2[q] * gscale_inv;
+    if (t_out) {
+      const float lb = A.LB2[q];
+      t_out[q] = lb > -CUDART_INF_F ? Prec<float>::exp2(A.G2[q] + lb) : 0.f;
+    }
+  }
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)A.batch;
+       q += (size_t)gridDim.x * blockDim.x) {
+    if (iters_out) iters_out[q] = A.iters[q];
+    if (err_out) err_out[q] = A.err[q];
+    if (status_out) status_out[q] = A.status[q];
+  }
+}
+
+// Device workspace of the banded path (allocated by the handle on first use and grown on demand).
+struct BandWorkspace {
+  float* C2;
+  int *row_ptr, *cnt, *fill, *col_idx;
+  float *rval, *xcol;
+  float *G2, *LA2, *LB2, *S, *R, *W, *vpart, *mpart, *err;
+  int *done, *iters, *status, *remaining, *bad;
+};
+
+inline size_t carve_band_workspace(void* base, int batch, int n, int k, int h, int nnz, BandWorkspace* ws) {
+  size_t off = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? b + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  const size_t W = 2 * (size_t)h + 1, rows = (size_t)batch * n;
+  const size_t tiles = (size_t)(n + BAND_TN - 1) / BAND_TN;
+  BandWorkspace w;
+  w.C2 = (float*)take(4 * W * n);
+  w.row_ptr = (int*)take(4 * ((size_t)n + 1));
+  w.cnt = (int*)take(4 * (size_t)n);
+  w.fill = (int*)take(4 * (size_t)n);
+  w.col_idx = (int*)take(4 * (size_t)nnz);
+  w.rval = (float*)take(4 * (size_t)nnz);
+  w.xcol = (float*)take(4 * (size_t)k);
+  w.G2 = (float*)take(4 * rows);
+  w.LA2 = (float*)take(4 * rows);
+  w.LB2 = (float*)take(4 * rows);
+  w.S = (float*)take(4 * rows);
+  w.R = (float*)take(4 * rows);
+  w.W = (float*)take(4 * (size_t)batch * k);
+  w.vpart = (float*)take(4 * (size_t)batch * tiles);
+  w.mpart = (float*)take(4 * (size_t)batch * tiles);
+  w.err = (float*)take(4 * (size_t)batch);
+  w.done = (int*)take(4 * (size_t)batch);
+  w.iters = (int*)take(4 * (size_t)batch);
+  w.status = (int*)take(4 * (size_t)batch);
+  w.remaining = (int*)take(4);
+  w.bad = (int*)take(4);
+  if (ws) *ws = w;
+  return off;
+}
+
+// One banded solve: inputs as otlm_solve_banded (device pointers).
+struct BandCall {
+  int batch, n, k, h, nnz;
+  const float* Cd;
+  const int* col_ptr;
+  const int* row_idx;
+  const float* val;
+  const float* y;
+  float* w;
+  float* g;
+  float* t_out;
+  int* iters_out;
+  float* err_out;
+  int* status_out;
+};
+
+// Returns the first CUDA error; *invalid is set when the band or the dictionary is malformed
+// (checked on the device before any index from them is used).
+inline cudaError_t solve_device_band(const Launch& L, const BandWorkspace& ws, const SolveParams& sp,
+                                     const BandCall& c, bool* invalid) {
+  *invalid = false;
+  const int n = c.n, k = c.k, h = c.h, W = 2 * h + 1;
+  const double eps_ln2 = sp.eps * kLn2;
+  BandArgs A{};
+  A.batch = c.batch; A.n = n; A.k = k; A.h = h; A.tiles = (n + BAND_TN - 1) / BAND_TN;
+  A.max_iter = sp.max_iter; A.datafit = sp.datafit; A.penalty = sp.penalty;
+  A.tol = float(sp.tol); A.eps = float(sp.eps); A.alpha = float(sp.alpha); A.beta = float(sp.beta);
+  A.kl_coef = float(sp.lam / (sp.eps + sp.lam)); A.tv_bound = float(sp.lam / eps_ln2);
+  A.lam_over_eps = float(sp.lam / sp.eps); A.log_lam_over_eps = float(log(sp.lam / sp.eps));
+  A.C2 = ws.C2; A.col_ptr = c.col_ptr; A.row_idx = c.row_idx; A.val = c.val;
+  A.row_ptr = ws.row_ptr; A.col_idx = ws.col_idx; A.rval = ws.rval; A.xcol = ws.xcol; A.y = c.y;
+  A.G2 = ws.G2; A.LA2 = ws.LA2; A.LB2 = ws.LB2; A.S = ws.S; A.R = ws.R; A.W = ws.W;
+  A.vpart = ws.vpart; A.mpart = ws.mpart; A.err = ws.err; A.done = ws.done; A.iters = ws.iters;
+  A.status = ws.status; A.remaining = ws.remaining;
+
+  cudaError_t e = cudaMemsetAsync(ws.cnt, 0, sizeof(int) * n, L.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.fill, 0, sizeof(int) * n, L.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.bad, 0, sizeof(int), L.stream);
+  if (e != cudaSuccess) return e;
+  L.begin(KIND_OTHER);
+  band_cost_kernel<<<592, 256, 0, L.stream>>>(c.Cd, ws.C2, (size_t)W * n, float(1.0 / eps_ln2), ws.bad);
+  L.end();
+  L.begin(KIND_OTHER);
+  band_csc_check_kernel<<<(k + 1 + 255) / 256, 256, 0, L.stream>>>(c.col_ptr, c.row_idx, c.val, n, k, c.nnz,
+                                                                   ws.xcol, ws.cnt, ws.bad);
+  L.end();
+  e = cudaMemcpyAsync(L.host_flag, ws.bad, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+  if (e != cudaSuccess) return e;
+  if (*L.host_flag) {
+    *invalid = true;
+    return cudaSuccess;
+  }
+  L.begin(KIND_OTHER);
+  band_scan_kernel<<<1, 1024, 0, L.stream>>>(ws.cnt, ws.row_ptr, n);
+  L.end();
+  L.begin(KIND_OTHER);
+  band_fill_kernel<<<(k + 255) / 256, 256, 0, L.stream>>>(c.col_ptr, c.row_idx, c.val, k, ws.row_ptr, ws.fill,
+                                                          ws.col_idx, ws.rval);
+  L.end();
+  L.begin(KIND_OTHER);
+  band_sort_rows_kernel<<<(n + 255) / 256, 256, 0, L.stream>>>(ws.row_ptr, ws.col_idx, ws.rval, n);
+  L.end();
+  L.begin(KIND_OTHER);
+  band_init_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, float(1.0 / eps_ln2));
+  L.end();
+
+  const dim3 grid_rows(A.tiles, c.batch), grid_atoms((k + BAND_NT - 1) / BAND_NT, c.batch);
+  for (int it = 0;; ++it) {
+    A.it = it;
+    L.begin(KIND_APPLY);
+    band_source_kernel<<<grid_rows, BAND_NT, 0, L.stream>>>(A);
+    L.end();
+    L.begin(KIND_MM);
+    band_mm_kernel<<<grid_atoms, BAND_NT, 0, L.stream>>>(A);
+    L.end();
+    if (it >= sp.max_iter) break;
+    L.begin(KIND_APPLY);
+    band_target_kernel<<<grid_rows, BAND_NT, 0, L.stream>>>(A);
+    L.end();
+    if ((it + 1) % sp.poll_every == 0) {
+      e = cudaMemcpyAsync(L.host_flag, ws.remaining, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+      if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();
+      if (e != cudaSuccess) return e;
+      if (*L.host_flag == 0) break;
+    }
+  }
+  L.begin(KIND_OTHER);
+  band_finalize_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, c.t_out, c.iters_out, c.err_out, c.status_out,
+                                                   float(eps_ln2));
+  L.end();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();
+  return e;
+}
+
+}  // namespace otlm

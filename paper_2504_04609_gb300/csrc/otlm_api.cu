@@ -13,6 +13,7 @@
 #include "solver.cuh"
 #include "tc_solver.cuh"
 #include "ragged.cuh"
+#include "banded.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -40,6 +41,9 @@ struct otlm_ctx {
   unsigned char rg_key[sizeof(otlm::RaggedArgs) + 2 * sizeof(int)] = {};
   int rg_variant = 1;              // CTA size chosen by otlm_tune_ragged (default 256 threads)
   long long rg_tot[3] = {0, 0, 0}; // packed sizes sum n, sum n k, sum k of the last batch
+  // banded path (allocated on first use, grown when a call needs more)
+  void* bd = nullptr;
+  size_t bd_bytes = 0;
 };
 
 namespace {
@@ -267,6 +271,7 @@ void otlm_destroy(otlm_handle h) {
   if (h->rg_exec) cudaGraphExecDestroy(h->rg_exec);
   if (h->rg_order) cudaFree(h->rg_order);
   if (h->rg_stream) cudaStreamDestroy(h->rg_stream);
+  if (h->bd) cudaFree(h->bd);
   for (cudaEvent_t e : h->rg_ev)
     if (e) cudaEventDestroy(e);
   delete h;
@@ -354,6 +359,41 @@ int otlm_objective(otlm_handle h, int batch, int n, int k, const void* x, const 
   const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
   if (h->cfg.precision == OTLM_PREC_FP64) return run_objective<double>(h, sp, x, D, y, w, g, primal_out, dual_out);
   return run_objective<float>(h, sp, x, D, y, w, g, primal_out, dual_out);
+}
+
+int otlm_solve_banded(otlm_handle h, int batch, int n, int hw, const float* Cd, int k, int nnz, const int* col_ptr,
+                      const int* row_idx, const float* val, const float* y, double eps, double lam, double alpha,
+                      float* w, float* g, float* t_out, int* iters_out, float* err_out, int* status_out) {
+  if (!h || !Cd || !col_ptr || !row_idx || !val || !y || !w) return OTLM_EINVAL;
+  if (h->cfg.precision != OTLM_PREC_FP32_LOG || h->cfg.mm_steps > 1) return OTLM_EUNSUPPORTED;
+  if (batch < 1 || batch > h->cfg.batch_max || n < 2 || k < 1 || nnz < 1 || hw < 0 || hw > otlm::BAND_HMAX ||
+      hw >= n || (long long)batch * n > (1LL << 40))
+    return OTLM_EINVAL;
+  if (!(eps > 0) || !std::isfinite(eps)) return OTLM_EINVAL;
+  if (h->cfg.datafit != OTLM_DATAFIT_BALANCED && (!(lam > 0) || !std::isfinite(lam))) return OTLM_EINVAL;
+  if (!(alpha >= 0) || !std::isfinite(alpha) || (h->cfg.penalty == OTLM_PENALTY_L2SQ && !(alpha > 0)))
+    return OTLM_EINVAL;
+  const size_t need = otlm::carve_band_workspace(nullptr, batch, n, k, hw, nnz, nullptr);
+  if (need > h->bd_bytes) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return OTLM_ECUDA;
+    if (h->bd) cudaFree(h->bd);
+    h->bd = nullptr;
+    h->bd_bytes = 0;
+    if (cudaMalloc(&h->bd, need) != cudaSuccess) {
+      h->bd = nullptr;
+      return OTLM_ENOMEM;
+    }
+    h->bd_bytes = need;
+  }
+  otlm::BandWorkspace bw;
+  otlm::carve_band_workspace(h->bd, batch, n, k, hw, nnz, &bw);
+  const otlm::SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
+  otlm::BandCall c{batch, n, k, hw, nnz, Cd, col_ptr, row_idx, val, y, w, g, t_out, iters_out, err_out, status_out};
+  Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
+  bool invalid = false;
+  const cudaError_t e = otlm::solve_device_band(L, bw, sp, c, &invalid);
+  if (e != cudaSuccess) return OTLM_ECUDA;
+  return invalid ? OTLM_EINVAL : OTLM_OK;
 }
 
 int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,

@@ -22,7 +22,7 @@ PENALTY = {"none": 0, "l1": 1, "l2sq": 2, "elastic": 3}
 PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 
 EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm_solve_host", "otlm_objective",
-           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged",
+           "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged", "otlm_solve_banded",
            "otlm_tune_ragged", "otlm_ws_create", "otlm_ws_destroy", "otlm_ws_num_params", "otlm_ws_set_normalization",
            "otlm_ws_get_params", "otlm_ws_set_params", "otlm_ws_gradients", "otlm_ws_train_step", "otlm_ws_predict",
            "otlm_strerror")
@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
         L.otlm_solve_noalloc.restype = i
         L.otlm_solve_ragged.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp]
         L.otlm_solve_ragged.restype = i
+        L.otlm_solve_banded.argtypes = [vp, i, i, i, vp, i, i, vp, vp, vp, vp, d, d, d, vp, vp, vp, vp, vp, vp]
+        L.otlm_solve_banded.restype = i
         L.otlm_tune_ragged.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp, i, i,
                                        ctypes.POINTER(ctypes.c_int)]
         L.otlm_tune_ragged.restype = i
@@ -193,6 +195,17 @@ class Handle:
                                    _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
         _check(rc, "otlm_solve_host")
         return SolveResult(w, g, t_out, iters, err, status)
+
+    def solve_banded(self, Cd, hw, col_ptr, row_idx, val, y, eps, lam, alpha, w, g=None, t_out=None, iters=None,
+                     err=None, status=None):
+        """otlm_solve_banded: Cd [2hw+1, n] float32, col_ptr / row_idx int32 and val float32 (CSC
+        dictionary), y [B, n], w [B, k] (in/out); all CUDA tensors."""
+        B, n = y.shape
+        k = col_ptr.shape[0] - 1
+        rc = lib().otlm_solve_banded(self._h, B, n, hw, _ptr(Cd), k, val.shape[0], _ptr(col_ptr), _ptr(row_idx),
+                                     _ptr(val), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g), _ptr(t_out), _ptr(iters),
+                                     _ptr(err), _ptr(status))
+        _check(rc, "otlm_solve_banded")
 
     def solve_ragged(self, rb, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):
         """otlm_solve_ragged on a RaggedBatch of device tensors (see ragged_batch)."""
