@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libotlm.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["otlm_api.cu", "otlm_noalloc.cu", "otlm_warmstart.cu"]
+SOURCES = ["otlm_api.cu", "otlm_banded.cu", "otlm_noalloc.cu", "otlm_warmstart.cu"]
 
 
 def _nvcc() -> str:

@@ -1,32 +1,35 @@
 // Algorithm 1 for a banded cost and a sparse dictionary (the paper's scalability test: a cost
 // truncated to C = +inf beyond a distance, so K_ij = 0 off a band of half-width h, and k = n/10
-// truncated basis functions), FP32 in the log domain.
+// truncated basis functions), FP32.
 //
-// The cost comes in diagonal storage Cd[d][i] = C(i, i + d - h), d = 0..2h (+inf: no pair).  K is
-// never formed: both applies are log-sum-exps over the 2h + 1 entries of a row (source) or a
-// column (target) of the band,
-//   LA2_i = log2 sum_d 2^(G2_{i+d-h} - C2[d][i]),   LB2_j = log2 sum_e 2^(F2_{j+e-h} - C2[2h-e][j+e-h]),
-// with C2 = C / (eps ln2) (the target apply finds C(i, j), i = j + e - h, in diagonal 2h - e of
-// row i).  The dictionary is used in two sparse forms: the caller's CSC for D^T r (one thread
-// per atom) and a CSR copy built here for s = D w (one thread per row).
+// The cost comes in diagonal storage Cd[d][i] = C(i, i + d - h), d = 0..2h (+inf: no pair).  With
+// C2 = C / (eps ln2) the applies are
+//   LA2_i = log2 sum_d 2^(G2_{i+d-h} - C2[d][i]),   LB2_j = log2 sum_e 2^(F2_{j+e-h} - C2[2h-e][j+e-h])
+// (the target apply finds C(i, j), i = j + e - h, in diagonal 2h - e of row i).  K itself is never
+// stored in HBM.  The dictionary is used in two sparse forms: the caller's CSC for D^T r (one
+// thread per atom and problem) and a CSR copy built here for s = D w (one thread per row).
 //
-// One iteration is three launches over (tiles of TN bins or atoms) x problems:
-//   band_source_kernel : LA2 (source apply), the violation numerator per tile and the log ratios
-//                        r_i = LA2_i - log2 S_i for the MM step
-//   band_mm_kernel     : per problem, the stop decision from the tile partials (fixed order), then
-//                        Table 2's MM step per atom
-//   band_target_kernel : s = D w on the tile and its halo, F2 = log2 s - LA2, the target apply and
-//                        the datafit prox (Table 1); the tile's mass partial
+// One iteration is three launches: source apply (LA2, the violation numerator per tile, the log
+// ratios r = LA2 - log2 S), MM step (stop decision from the tile partials in a fixed order, then
+// Table 2 per atom and problem), and target kernel (s = D w on the tile and its halo, F2 =
+// log2 s - LA2, the target apply and the datafit prox of Table 1, the tile's mass).  The apply
+// kernels take tiles of 256 bins x PB problems per CTA: a thread owns one row (or column) of the
+// band, loads its 2h + 1 costs once into registers (template buckets of 9, 19 and 33 diagonals,
+// padded with +inf; wider bands read them from global memory) and uses them for the PB problems,
+// whose potentials (tile plus halo) are staged in shared memory.  Each log-sum-exp is one pass of
+// exp2 around the previous iteration's value of the same sum, which is also the ratio new / old
+// the convergence test needs; a sum outside [2^-60, 2^60] is redone exactly (max, then sum).  A
+// shared shift per window of rows would not do: at eps = 1e-3 the potentials move by ~14 log2
+// units per bin, so a window's largest term underflows most of its rows' terms.
 // A problem that stops keeps the state of its last completed iteration; later launches skip it.
 #pragma once
 
-#include "solver.cuh"
+#include "banded_api.h"
 
 namespace otlm {
 
-constexpr int BAND_TN = 1024;      // bins per tile
+constexpr int BAND_TN = 256;       // bins per tile (one per thread)
 constexpr int BAND_NT = 256;       // threads per CTA
-constexpr int BAND_HMAX = 64;      // largest half-width
 
 struct BandArgs {
   int batch, n, k, h, tiles, it, max_iter, datafit, penalty;
@@ -42,7 +45,7 @@ struct BandArgs {
   const float* y;         // [B][n]
   float* G2;              // [B][n] target potential / (eps ln2)
   float* LA2;             // [B][n] log2 K u1 (previous iteration's on entry to the source kernel)
-  float* LB2;             // [B][n] log2 K^T u2
+  float* LB2;             // [B][n] log2 K^T u2 (previous iteration's on entry to the target kernel)
   float* S;               // [B][n] D w
   float* R;               // [B][n] log ratios
   float* W;               // [B][k]
@@ -55,44 +58,101 @@ struct BandArgs {
   int* remaining;         // problems not yet stopped
 };
 
-__device__ __forceinline__ float band_lse_tail(float m, float sum) {
-  return m > -CUDART_INF_F ? m + Prec<float>::log2(sum) : -CUDART_INF_F;
+constexpr int BAND_WARPS = BAND_NT / 32;
+
+// Shared memory of the apply kernels (bytes): PB potential rows [TN + 2h] and the block-sum
+// scratch [PB][warps].
+inline size_t band_smem_bytes(int h, int pb) {
+  return 4 * ((size_t)pb * (BAND_TN + 2 * (size_t)h) + (size_t)pb * BAND_WARPS);
 }
 
-__global__ void __launch_bounds__(BAND_NT) band_source_kernel(BandArgs A) {
+// Stage PB potential rows: dst[pp][c] = src[p0 + pp][t0 - h + c] (-inf outside [0, n) or past the batch).
+template <int PB>
+__device__ __forceinline__ void band_stage_rows(const BandArgs& A, const float* src, float* dst, int p0, int t0,
+                                                int L) {
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp)
+    for (int c = threadIdx.x; c < L; c += BAND_NT) {
+      const int j = t0 - A.h + c;
+      dst[pp * L + c] = (p0 + pp < A.batch && j >= 0 && j < A.n) ? src[(size_t)(p0 + pp) * A.n + j] : -CUDART_INF_F;
+    }
+}
+
+// One row's band costs: WR > 0 keeps them in registers (cr, padded with +inf), otherwise they are
+// read from global memory at cg[t * cgstride].
+template <int WR>
+struct BandRow {
+  float cr[WR > 0 ? WR : 1];
+  const float* cg;
+  long cgstride;
+  __device__ __forceinline__ float c(int t) const {
+    if constexpr (WR > 0) return cr[t];
+    else return cg[t * cgstride];
+  }
+};
+
+// log2 sum_t 2^(v_t - c_t) over the row's band (v: potentials in shared memory at stride 1).  One
+// pass around `shift`, the previous iteration's log-sum, so the sum is the ratio new / old; when
+// that sum leaves [2^-60, 2^60], or the shift is not finite, the exact two passes (max, then the
+// sum around it).  Returns the log-sum and writes the ratio 2^(new - shift).
+template <int WR>
+__device__ __forceinline__ float band_lse(const float* v, const BandRow<WR>& row, int W, float shift, float* ratio) {
   using P = Prec<float>;
-  __shared__ float gs[BAND_TN + 2 * BAND_HMAX];
-  __shared__ float red[32];
-  const int tile = blockIdx.x, p = blockIdx.y;
-  if (A.done[p]) return;
-  const int n = A.n, h = A.h, W = 2 * h + 1;
-  const int t0 = tile * BAND_TN;
-  const size_t off = (size_t)p * n;
-  for (int q = threadIdx.x; q < BAND_TN + 2 * h; q += BAND_NT) {
-    const int j = t0 - h + q;
-    gs[q] = (j >= 0 && j < n) ? A.G2[off + j] : -CUDART_INF_F;
+  constexpr bool REG = WR > 0;
+  const int T = REG ? WR : W;
+  if (shift > -CUDART_INF_F && shift < CUDART_INF_F) {
+    float sum = 0.f;
+#pragma unroll
+    for (int t = 0; t < T; ++t) sum += P::exp2(v[t] - row.c(t) - shift);
+    if (sum >= 0x1p-60f && sum <= 0x1p60f) {
+      *ratio = sum;
+      return shift + P::log2(sum);
+    }
+  }
+  float m = -CUDART_INF_F;
+#pragma unroll
+  for (int t = 0; t < T; ++t) m = fmaxf(m, v[t] - row.c(t));
+  if (!(m > -CUDART_INF_F)) {
+    *ratio = P::exp2(-CUDART_INF_F - shift);
+    return -CUDART_INF_F;
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int t = 0; t < T; ++t) sum += P::exp2(v[t] - row.c(t) - m);
+  const float la = m + P::log2(sum);
+  *ratio = P::exp2(la - shift);
+  return la;
+}
+
+// Fixed-order block sum of PB per-thread values; thread pp < PB gets the total of value pp.
+template <int PB>
+__device__ __forceinline__ float band_block_sums(const float (&v)[PB], float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) {
+    float x = v[pp];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[pp * BAND_WARPS + warp] = x;
   }
   __syncthreads();
-  const bool check = A.it > 0;
-  float part = 0.f;
-  for (int q = threadIdx.x; q < BAND_TN; q += BAND_NT) {
-    const int i = t0 + q;
-    if (i >= n) break;
-    float m = -CUDART_INF_F;
-    for (int d = 0; d < W; ++d) m = fmaxf(m, gs[q + d] - A.C2[(size_t)d * n + i]);
-    float sum = 0.f;
-    if (m > -CUDART_INF_F)
-      for (int d = 0; d < W; ++d) sum += P::exp2(gs[q + d] - A.C2[(size_t)d * n + i] - m);
-    const float la = band_lse_tail(m, sum);
-    const float s = A.S[off + i];
-    if (check && s > 0.f) part += s * fabsf(P::exp2(la - A.LA2[off + i]) - 1.f);
-    A.LA2[off + i] = la;
-    A.R[off + i] = s > 0.f ? la - P::log2(s) : 0.f;
-  }
-  if (!check) return;
-  part = block_sum(part, red);
-  if (threadIdx.x == 0) A.vpart[(size_t)p * A.tiles + tile] = part;
+  float t = 0.f;
+  if (threadIdx.x < PB)
+    for (int w8 = 0; w8 < BAND_WARPS; ++w8) t += red[threadIdx.x * BAND_WARPS + w8];
+  return t;
 }
+
+template <int PB>
+__device__ __forceinline__ bool band_live(const BandArgs& A, int p0, bool (&live)[PB]) {
+  bool any = false;
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) {
+    live[pp] = p0 + pp < A.batch && !A.done[p0 + pp];
+    any |= live[pp];
+  }
+  return any;
+}
+
+__device__ __forceinline__ bool band_live_one(const BandArgs& A, int p) { return p < A.batch && !A.done[p]; }
 
 // Sum of a problem's tile partials in a fixed order (lane-strided, then a fixed shuffle tree).
 __device__ __forceinline__ float band_tile_sum(const float* part, int tiles) {
@@ -103,9 +163,56 @@ __device__ __forceinline__ float band_tile_sum(const float* part, int tiles) {
   return v;
 }
 
+// Source apply for PB problems on one tile of rows: LA2, the violation numerator
+// sum_i S_i |a_new,i / a_old,i - 1| and the log ratios R_i = LA2_i - log2 S_i.  Row i's costs
+// C2[d][i] are loaded once (coalesced across the tile) for the PB problems.
+template <int PB, int WR>
+__global__ void __launch_bounds__(BAND_NT) band_source_kernel(BandArgs A) {
+  using P = Prec<float>;
+  extern __shared__ float smem[];
+  const int tile = blockIdx.x, p0 = blockIdx.y * PB;
+  const int n = A.n, h = A.h, W = 2 * h + 1, L = BAND_TN + 2 * h, t0 = tile * BAND_TN;
+  bool live[PB];
+  if (!band_live<PB>(A, p0, live)) return;
+  float* gs = smem;
+  float* red = gs + (size_t)PB * L;
+  band_stage_rows<PB>(A, A.G2, gs, p0, t0, L);
+  const int i = t0 + threadIdx.x;
+  const bool valid = i < n;
+  BandRow<WR> row;
+  row.cg = A.C2 + (valid ? i : 0);
+  row.cgstride = n;
+  if constexpr (WR > 0) {
+#pragma unroll
+    for (int t = 0; t < WR; ++t) row.cr[t] = (valid && t < W) ? A.C2[(size_t)t * n + i] : CUDART_INF_F;
+  }
+  __syncthreads();
+  const bool check = A.it > 0;
+  float part[PB];
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) {
+    part[pp] = 0.f;
+    if (!live[pp] || !valid) continue;
+    const size_t o = (size_t)(p0 + pp) * n + i;
+    float ratio;
+    const float la = band_lse<WR>(gs + pp * L + threadIdx.x, row, W, A.LA2[o], &ratio);
+    const float s = A.S[o];
+    if (check && s > 0.f) part[pp] = s * fabsf(ratio - 1.f);
+    A.LA2[o] = la;
+    A.R[o] = s > 0.f ? la - P::log2(s) : 0.f;
+  }
+  if (!check) return;
+  const float tot = band_block_sums<PB>(part, red);
+  if (threadIdx.x < PB && band_live_one(A, p0 + threadIdx.x))
+    A.vpart[(size_t)(p0 + threadIdx.x) * A.tiles + tile] = tot;
+}
+
+// One problem (blockIdx.y) x 256 atoms per CTA: warp 0 takes the problem's stop decision from the
+// tile partials (every CTA of the problem reaches the same one; the first records it), then each
+// thread runs Table 2's MM step for its atom.
 __global__ void __launch_bounds__(BAND_NT) band_mm_kernel(BandArgs A) {
   using P = Prec<float>;
-  __shared__ int stop;
+  __shared__ int stop_s;
   const int p = blockIdx.y;
   if (A.done[p]) return;
   if (A.it > 0) {
@@ -127,27 +234,38 @@ __global__ void __launch_bounds__(BAND_NT) band_mm_kernel(BandArgs A) {
             atomicSub(A.remaining, 1);
           }
         }
-        stop = st >= 0;
+        stop_s = st >= 0;
       }
     }
     __syncthreads();
-    if (stop) return;
+    if (stop_s) return;
   }
   const int m = blockIdx.x * BAND_NT + threadIdx.x;
   if (m >= A.k) return;
   const float* R = A.R + (size_t)p * A.n;
+  const int q0 = A.col_ptr[m], q1 = A.col_ptr[m + 1];
   float acc = 0.f;
-  for (int q = A.col_ptr[m]; q < A.col_ptr[m + 1]; ++q) acc = fmaf(A.val[q], R[A.row_idx[q]], acc);
+  int q = q0;
+  for (; q + 4 <= q1; q += 4) {  // four independent gathers in flight
+    const int r0 = A.row_idx[q], r1 = A.row_idx[q + 1], r2 = A.row_idx[q + 2], r3 = A.row_idx[q + 3];
+    const float v0 = A.val[q], v1 = A.val[q + 1], v2 = A.val[q + 2], v3 = A.val[q + 3];
+    const float x0 = R[r0], x1 = R[r1], x2 = R[r2], x3 = R[r3];
+    acc = fmaf(v0, x0, acc);
+    acc = fmaf(v1, x1, acc);
+    acc = fmaf(v2, x2, acc);
+    acc = fmaf(v3, x3, acc);
+  }
+  for (; q < q1; ++q) acc = fmaf(A.val[q], R[A.row_idx[q]], acc);
   const float xj = A.xcol[m];
-  float* Wp = A.W + (size_t)p * A.k;
-  const float nu = P::log(Wp[m]) + acc * float(kLn2) / xj;
+  float* wp = A.W + (size_t)p * A.k + m;
+  const float nu = P::log(*wp) + acc * float(kLn2) / xj;
   const float shift = (A.penalty == PEN_L1 || A.penalty == PEN_ELASTIC) ? A.alpha / (A.eps * xj) : 0.f;
   float wn;
   if (A.penalty == PEN_L2SQ || A.penalty == PEN_ELASTIC) {
     const float c = (A.penalty == PEN_ELASTIC ? A.beta : A.alpha) / (A.eps * xj);
     wn = wright_omega<float>(P::log(c) + nu - shift) / c;
   } else wn = P::exp(nu - shift);
-  Wp[m] = wn;
+  *wp = wn;
 }
 
 __device__ __forceinline__ float band_datafit(const BandArgs& A, float v, float yv) {
@@ -163,56 +281,88 @@ __device__ __forceinline__ float band_datafit(const BandArgs& A, float v, float 
   }
 }
 
+// Source step, target apply and datafit prox for PB problems on one tile: s = D w over the tile and
+// its halo (CSR rows, shared by the PB problems), F2 = log2 s - LA2, then LB2 and G2 (Table 1).
+// Column j's costs C(j + e - h, j) = C2[2h - e][j + e - h] are loaded once for the PB problems.
+template <int PB, int WR>
 __global__ void __launch_bounds__(BAND_NT) band_target_kernel(BandArgs A) {
   using P = Prec<float>;
-  __shared__ float fs[BAND_TN + 2 * BAND_HMAX];
-  __shared__ float red[32];
-  const int tile = blockIdx.x, p = blockIdx.y;
-  if (A.done[p]) return;
-  const int n = A.n, h = A.h, W = 2 * h + 1;
-  const int t0 = tile * BAND_TN;
-  const size_t off = (size_t)p * n;
-  const float* Wp = A.W + (size_t)p * A.k;
-  float mass = 0.f;
-  // source step on the tile and its halo: s = D w (rows in CSR), F2 = log2 s - LA2
-  for (int q = threadIdx.x; q < BAND_TN + 2 * h; q += BAND_NT) {
-    const int i = t0 - h + q;
-    float f2 = -CUDART_INF_F;
+  extern __shared__ float smem[];
+  const int tile = blockIdx.x, p0 = blockIdx.y * PB;
+  const int n = A.n, h = A.h, W = 2 * h + 1, L = BAND_TN + 2 * h, t0 = tile * BAND_TN;
+  bool live[PB];
+  if (!band_live<PB>(A, p0, live)) return;
+  float* fs = smem;
+  float* red = fs + (size_t)PB * L;
+  float mass[PB];
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) mass[pp] = 0.f;
+  for (int c = threadIdx.x; c < L; c += BAND_NT) {
+    const int i = t0 - h + c;
+    float s[PB];
+#pragma unroll
+    for (int pp = 0; pp < PB; ++pp) s[pp] = 0.f;
     if (i >= 0 && i < n) {
-      float s = 0.f;
-      for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) s = fmaf(A.rval[e], Wp[A.col_idx[e]], s);
-      // a subnormal mass counts as 0, as in the other FP32 paths (log2 flushes it to -inf)
-      if (s < P::tiny()) s = 0.f;
-      if (s > 0.f) f2 = P::log2(s) - A.LA2[off + i];
-      if (q >= h && q < h + BAND_TN) {
-        A.S[off + i] = s;
-        mass += s;
+      const int e0 = A.row_ptr[i], e1 = A.row_ptr[i + 1];
+      for (int e = e0; e < e1; ++e) {
+        const size_t col = (size_t)A.col_idx[e];
+        const float v = A.rval[e];
+#pragma unroll
+        for (int pp = 0; pp < PB; ++pp)
+          if (live[pp]) s[pp] = fmaf(v, A.W[(size_t)(p0 + pp) * A.k + col], s[pp]);
       }
     }
-    fs[q] = f2;
+    const bool own = c >= h && c < h + BAND_TN && i < n;
+#pragma unroll
+    for (int pp = 0; pp < PB; ++pp) {
+      float f2 = -CUDART_INF_F;
+      if (live[pp] && i >= 0 && i < n) {
+        // a subnormal mass counts as 0, as in the other FP32 paths (log2 flushes it to -inf)
+        const float sv = s[pp] < P::tiny() ? 0.f : s[pp];
+        const size_t o = (size_t)(p0 + pp) * n + i;
+        if (sv > 0.f) f2 = P::log2(sv) - A.LA2[o];
+        if (own) {
+          A.S[o] = sv;
+          mass[pp] += sv;
+        }
+      }
+      fs[pp * L + c] = f2;
+    }
+  }
+  const int j = t0 + threadIdx.x;
+  const bool valid = j < n;
+  // term e of column j: row j + e - h, diagonal 2h - e, i.e. C2 + (2h - e) n + j + e - h
+  BandRow<WR> col;
+  col.cg = A.C2 + (valid ? (long)(2 * h) * n + j - h : 0);
+  col.cgstride = 1 - (long)n;
+  if constexpr (WR > 0) {
+#pragma unroll
+    for (int t = 0; t < WR; ++t) {
+      const int i = j + t - h;
+      col.cr[t] = (valid && t < W && i >= 0 && i < n) ? A.C2[(size_t)(2 * h - t) * n + i] : CUDART_INF_F;
+    }
+  }
+  // the PB problems' previous sums and targets of column j, loaded before any is used
+  float old[PB], yv[PB];
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) {
+    const size_t o = (size_t)(p0 + pp) * n + j;
+    old[pp] = (live[pp] && valid) ? A.LB2[o] : 0.f;
+    yv[pp] = (live[pp] && valid) ? A.y[o] : 0.f;
   }
   __syncthreads();
-  // target apply and the datafit prox
-  for (int q = threadIdx.x; q < BAND_TN; q += BAND_NT) {
-    const int j = t0 + q;
-    if (j >= n) break;
-    float m = -CUDART_INF_F;
-    for (int e = 0; e < W; ++e) {
-      const int i = j + e - h;
-      if (i >= 0 && i < n) m = fmaxf(m, fs[q + e] - A.C2[(size_t)(2 * h - e) * n + i]);
-    }
-    float sum = 0.f;
-    if (m > -CUDART_INF_F)
-      for (int e = 0; e < W; ++e) {
-        const int i = j + e - h;
-        if (i >= 0 && i < n) sum += P::exp2(fs[q + e] - A.C2[(size_t)(2 * h - e) * n + i] - m);
-      }
-    const float lb = band_lse_tail(m, sum);
-    A.LB2[off + j] = lb;
-    A.G2[off + j] = band_datafit(A, lb, A.y[off + j]);
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) {
+    if (!live[pp] || !valid) continue;
+    const size_t o = (size_t)(p0 + pp) * n + j;
+    float ratio;
+    const float lb = band_lse<WR>(fs + pp * L + threadIdx.x, col, W, old[pp], &ratio);
+    A.LB2[o] = lb;
+    A.G2[o] = band_datafit(A, lb, yv[pp]);
   }
-  mass = block_sum(mass, red);
-  if (threadIdx.x == 0) A.mpart[(size_t)p * A.tiles + tile] = mass;
+  const float tot = band_block_sums<PB>(mass, red);
+  if (threadIdx.x < PB && band_live_one(A, p0 + threadIdx.x))
+    A.mpart[(size_t)(p0 + threadIdx.x) * A.tiles + tile] = tot;
 }
 
 // ---- set-up: scaled cost band, CSR copy of the dictionary, column masses, initial state -------
@@ -336,6 +486,7 @@ __global__ void band_init_kernel(BandArgs A, const float* w0, const float* g0, f
     float s = 0.f;
     for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) s = fmaf(A.rval[e], w0[(size_t)p * A.k + A.col_idx[e]], s);
     A.S[q] = s < Prec<float>::tiny() ? 0.f : s;
+    A.LA2[q] = -CUDART_INF_F;  // no previous sums: the first applies take the exact two-pass path
     A.LB2[q] = -CUDART_INF_F;
   }
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)A.batch;
@@ -415,21 +566,45 @@ inline size_t carve_band_workspace(void* base, int batch, int n, int k, int h, i
   return off;
 }
 
-// One banded solve: inputs as otlm_solve_banded (device pointers).
-struct BandCall {
-  int batch, n, k, h, nnz;
-  const float* Cd;
-  const int* col_ptr;
-  const int* row_idx;
-  const float* val;
-  const float* y;
-  float* w;
-  float* g;
-  float* t_out;
-  int* iters_out;
-  float* err_out;
-  int* status_out;
-};
+// The iteration loop with PB problems per apply CTA and register-held bands of WR diagonals (0:
+// read from global memory); polls the number of unfinished problems every poll_every iterations.
+template <int PB, int WR>
+cudaError_t band_iterate(const Launch& L, BandArgs& A, const BandWorkspace& ws, const SolveParams& sp) {
+  const size_t smem = band_smem_bytes(A.h, PB);
+  const dim3 grid_rows(A.tiles, (A.batch + PB - 1) / PB), grid_atoms((A.k + BAND_NT - 1) / BAND_NT, A.batch);
+  for (int it = 0;; ++it) {
+    A.it = it;
+    L.begin(KIND_APPLY);
+    band_source_kernel<PB, WR><<<grid_rows, BAND_NT, smem, L.stream>>>(A);
+    L.end();
+    L.begin(KIND_MM);
+    band_mm_kernel<<<grid_atoms, BAND_NT, 0, L.stream>>>(A);
+    L.end();
+    if (it >= sp.max_iter) break;
+    L.begin(KIND_APPLY);
+    band_target_kernel<PB, WR><<<grid_rows, BAND_NT, smem, L.stream>>>(A);
+    L.end();
+    if ((it + 1) % sp.poll_every == 0) {
+      cudaError_t e = cudaMemcpyAsync(L.host_flag, ws.remaining, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+      if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();
+      if (e != cudaSuccess) return e;
+      if (*L.host_flag == 0) break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+// Dispatch on problems per CTA (8 for batches of 8 or more, else 1) and the band-width bucket (9,
+// 19 or 33 diagonals in registers, padded with +inf; wider bands from global memory).
+template <int PB>
+cudaError_t band_iterate_pb(const Launch& L, BandArgs& A, const BandWorkspace& ws, const SolveParams& sp) {
+  const int W = 2 * A.h + 1;
+  if (W <= 9) return band_iterate<PB, 9>(L, A, ws, sp);
+  if (W <= 19) return band_iterate<PB, 19>(L, A, ws, sp);
+  if (W <= 33) return band_iterate<PB, 33>(L, A, ws, sp);
+  return band_iterate<PB, 0>(L, A, ws, sp);
+}
 
 // Returns the first CUDA error; *invalid is set when the band or the dictionary is malformed
 // (checked on the device before any index from them is used).
@@ -482,27 +657,8 @@ inline cudaError_t solve_device_band(const Launch& L, const BandWorkspace& ws, c
   band_init_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, float(1.0 / eps_ln2));
   L.end();
 
-  const dim3 grid_rows(A.tiles, c.batch), grid_atoms((k + BAND_NT - 1) / BAND_NT, c.batch);
-  for (int it = 0;; ++it) {
-    A.it = it;
-    L.begin(KIND_APPLY);
-    band_source_kernel<<<grid_rows, BAND_NT, 0, L.stream>>>(A);
-    L.end();
-    L.begin(KIND_MM);
-    band_mm_kernel<<<grid_atoms, BAND_NT, 0, L.stream>>>(A);
-    L.end();
-    if (it >= sp.max_iter) break;
-    L.begin(KIND_APPLY);
-    band_target_kernel<<<grid_rows, BAND_NT, 0, L.stream>>>(A);
-    L.end();
-    if ((it + 1) % sp.poll_every == 0) {
-      e = cudaMemcpyAsync(L.host_flag, ws.remaining, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
-      if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();
-      if (e != cudaSuccess) return e;
-      if (*L.host_flag == 0) break;
-    }
-  }
+  e = c.batch >= 8 ? band_iterate_pb<8>(L, A, ws, sp) : band_iterate_pb<1>(L, A, ws, sp);
+  if (e != cudaSuccess) return e;
   L.begin(KIND_OTHER);
   band_finalize_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, c.t_out, c.iters_out, c.err_out, c.status_out,
                                                    float(eps_ln2));

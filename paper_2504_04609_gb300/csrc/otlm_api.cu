@@ -13,7 +13,7 @@
 #include "solver.cuh"
 #include "tc_solver.cuh"
 #include "ragged.cuh"
-#include "banded.cuh"
+#include "banded_api.h"
 
 #include <algorithm>
 #include <vector>
@@ -373,7 +373,7 @@ int otlm_solve_banded(otlm_handle h, int batch, int n, int hw, const float* Cd, 
   if (h->cfg.datafit != OTLM_DATAFIT_BALANCED && (!(lam > 0) || !std::isfinite(lam))) return OTLM_EINVAL;
   if (!(alpha >= 0) || !std::isfinite(alpha) || (h->cfg.penalty == OTLM_PENALTY_L2SQ && !(alpha > 0)))
     return OTLM_EINVAL;
-  const size_t need = otlm::carve_band_workspace(nullptr, batch, n, k, hw, nnz, nullptr);
+  const size_t need = otlm::band_workspace_bytes(batch, n, k, hw, nnz);
   if (need > h->bd_bytes) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return OTLM_ECUDA;
     if (h->bd) cudaFree(h->bd);
@@ -385,13 +385,11 @@ int otlm_solve_banded(otlm_handle h, int batch, int n, int hw, const float* Cd, 
     }
     h->bd_bytes = need;
   }
-  otlm::BandWorkspace bw;
-  otlm::carve_band_workspace(h->bd, batch, n, k, hw, nnz, &bw);
   const otlm::SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
   otlm::BandCall c{batch, n, k, hw, nnz, Cd, col_ptr, row_idx, val, y, w, g, t_out, iters_out, err_out, status_out};
   Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
   bool invalid = false;
-  const cudaError_t e = otlm::solve_device_band(L, bw, sp, c, &invalid);
+  const cudaError_t e = otlm::band_solve(L, h->bd, sp, c, &invalid);
   if (e != cudaSuccess) return OTLM_ECUDA;
   return invalid ? OTLM_EINVAL : OTLM_OK;
 }

@@ -75,8 +75,8 @@ def _oracle(d, p, datafit, penalty, eps, lam, alpha, iters, tol=0.0, beta=0.0):
     ("kl", "elastic", TOL32),
 ])
 def test_scalability_inputs_trajectory_parity(datafit, penalty, bar):
-    """3 targets, n = 2300 (two full 1024-bin tiles and a ragged one), k = 230, hw = 9,
-    eps = alpha = 1e-3, 40 iterations."""
+    """3 targets (two groups of 2 per CTA, the second one short), n = 2300 (nine 256-bin tiles, the
+    last ragged), k = 230, hw = 9, eps = alpha = 1e-3, 40 iterations."""
     d = spectra.scaling_batch(61, 3, 2300)
     r = _gpu(d, datafit, penalty, 1e-3, 1.0, 1e-3, 40, beta=2e-3)
     assert np.all(r["iters"] == 40) and np.all(r["status"] == api.MAX_ITER)
@@ -168,3 +168,22 @@ def test_invalid_inputs_are_refused():
     with pytest.raises(api.OTLMError):
         h64.solve_banded(Cd, d["h"], cp, ri, val, y, 1e-2, 1.0, 1e-3, w)
     h64.close()
+
+
+@pytest.mark.parametrize("delta,B", [(41.0, 5), (41.0, 9), (4.0, 9), (15.0, 9), (10.0, 1)])
+def test_band_buckets_and_problem_groups(delta, B):
+    """Every band-width bucket (half-width 3: 9 diagonals in registers; 9: 19; 14: 33; 40: read
+    from global memory) with one problem per CTA (B < 8) and eight (B = 9: the second group one
+    problem), n = 700 (a ragged third tile), eps = 5e-2 so that the far diagonals carry weight."""
+    n, k = 700, 70
+    Cd, h = spectra.truncated_cost_band(n, rho=0.01, delta=delta)
+    cp, ri, vv = spectra.scaling_dictionary(n, k)
+    Y = np.stack([spectra.scaling_target(n, k, np.random.default_rng(640 + p)) for p in range(B)])
+    vv32 = spectra.to_dtype(vv, np.float32)
+    d = dict(Cd=spectra.to_dtype(Cd, np.float32), h=h, col_ptr=cp, row_idx=ri, val=vv32,
+             y=spectra.to_dtype(Y, np.float32), n=n, k=k, x_col=np.add.reduceat(vv32.astype(np.float64), cp[:-1]))
+    r = _gpu(d, "kl", "l1", 5e-2, 1.0, 1e-3, 25)
+    for p in range(B):
+        o = _oracle(d, p, "kl", "l1", 5e-2, 1.0, 1e-3, 25)
+        ew, et = rel_l1(r["w"][p], o["w"]), rel_l1(r["t"][p], o["t"])
+        assert ew <= TOL32 and et <= TOL32, (p, h, ew, et)
