@@ -43,7 +43,8 @@ def test_strerror_names_every_code():
 
 @pytest.mark.parametrize("field,value", [("n_max", 1), ("k_max", 0), ("k_max", 257), ("batch_max", 0),
                                          ("max_iter", 0), ("poll_every", 0), ("precision", 7),
-                                         ("datafit", 9), ("penalty", -1)])
+                                         ("datafit", 9), ("penalty", -1), ("penalty", 4), ("mm_steps", -1),
+                                         ("mm_steps", 65)])
 def test_create_rejects_bad_config_without_gpu(field, value):
     _ensure_built()
     cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)
@@ -59,3 +60,19 @@ def test_null_handle_is_rejected():
     rc = api.lib().otlm_solve(None, 1, 8, 2, 1, 1, 1, 0.1, 1.0, 0.1, 1, None, None, None, None, None)
     assert rc == api.OTLM_EINVAL
     assert api.lib().otlm_launch_count(None) == -1
+
+
+@pytest.mark.parametrize("beta", [0.0, -1.0, float("inf"), float("nan")])
+def test_elastic_net_needs_a_finite_positive_beta(beta):
+    _ensure_built()
+    cfg = api.otlm_config(64, 8, 4, 0, 1, api.PENALTY["elastic"], 10, 0.0, 4, beta, 1)
+    h = ctypes.c_void_p(123)
+    assert api.lib().otlm_create(ctypes.byref(h), ctypes.byref(cfg), None) == api.OTLM_EINVAL
+    assert h.value is None
+
+
+def test_banded_entry_point_rejects_a_null_handle():
+    _ensure_built()
+    rc = api.lib().otlm_solve_banded(None, 1, 64, 3, 1, 4, 8, 1, 1, 1, 1, 1e-2, 1.0, 1e-3, 1, None, None, None, None,
+                                     None)
+    assert rc == api.OTLM_EINVAL
