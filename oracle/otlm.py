@@ -17,6 +17,11 @@ Readings of passages the paper leaves garbled or open:
       columns have unit mass).
   A5  Table 2, squared l2: w_j = W0(c_j e^{nu_j}) / c_j, c_j = alpha/(eps x_j), from App. A
       (ln w_j + c_j w_j = nu_j); R(w) = (alpha/2)||w||^2.
+  A7  Table 1, Poisson: with L(s | y) = sum (s - y log s) (App. B's definition), stationarity of
+      lam L(v | y) + eps KL(v || b) is eps log(v / b) + lam - lam y / v = 0 (App. B prints the
+      sign of the lam term flipped; its next line follows the correct one), so u = lam y / (eps v)
+      solves u e^u = (lam y / (eps b)) e^{lam / eps} and v = (lam y / eps) / W0(...): Table 1's
+      "W0^{-1}" is read as the reciprocal 1 / W0.  For y = 0 the prox is b e^{-lam / eps}.
   A8  "not converged" (Algorithm 1): source-marginal violation
       e = ||u2 * (K u1) - X w||_1 / ||X w||_1, measured with the u1 of the next iteration.
   A6  Table 2, elastic net alpha l1 + (beta/2) l2^2: Table 2 prints the prefactor alpha/beta and a
@@ -28,7 +33,6 @@ Readings of passages the paper leaves garbled or open:
   A18 more than one MM step per outer iteration (Sec. 4.2 allows running the MM iteration for
       prox_{alpha P}(K u1 | X) longer than one step): every inner step uses the same a = K u1 and
       its own previous w; the source step u2 = X w / a follows the last inner step.
-Poisson (Table 1, last row) is not implemented.
 """
 from __future__ import annotations
 
@@ -36,7 +40,7 @@ import numpy as np
 from scipy.sparse import issparse
 from scipy.special import lambertw, logsumexp, wrightomega
 
-DATAFITS = ("balanced", "kl", "tv", "l2")
+DATAFITS = ("balanced", "kl", "tv", "l2", "poisson")
 PENALTIES = ("none", "l1", "l2sq", "elastic")
 
 
@@ -80,6 +84,11 @@ def datafit_loss(datafit, t, y):
         return float(np.sum(np.abs(t - y)))
     if datafit == "l2":
         return 0.5 * float(np.sum((t - y) ** 2))
+    if datafit == "poisson":
+        # negative Poisson log-likelihood without its constant (reading A7); y log t = 0 where y = 0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ylogt = np.where(y > 0, y * np.log(t), 0.0)
+        return float(np.sum(t - ylogt))
     raise ValueError(datafit)
 
 
@@ -115,6 +124,11 @@ def prox_datafit(datafit, s, y, eps, lam):
         return np.minimum(s * np.exp(lam / eps), np.maximum(s * np.exp(-lam / eps), y))
     if datafit == "l2":
         return (eps / lam) * lambert_w0((lam / eps) * s * np.exp((lam / eps) * y))
+    if datafit == "poisson":
+        c = lam * y / eps
+        with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+            v = c / lambert_w0(c / s * np.exp(lam / eps))
+        return np.where(y > 0, v, s * np.exp(-lam / eps))
     raise ValueError(datafit)
 
 
@@ -278,6 +292,8 @@ def _log_datafit_potential(datafit, log_b, y, eps, lam):
     tv      : g = clip(eps (log y - log b), -lam, lam)
     l2      : log v2 = log(eps/lam) + log omega(log(lam/eps) + log b + (lam/eps) y)
               (W0(e^z) = omega(z)), g = eps (log v2 - log b)
+    poisson : log v2 = log(lam y/eps) - log omega(log(lam y/eps) - log b + lam/eps) for y > 0,
+              g = -lam for y = 0 (reading A7)
     """
     with np.errstate(divide="ignore"):
         log_y = np.log(y)
@@ -291,6 +307,11 @@ def _log_datafit_potential(datafit, log_b, y, eps, lam):
         z = np.log(lam / eps) + log_b + (lam / eps) * y
         log_v = np.log(eps / lam) + np.log(wright_omega(z))
         return eps * (log_v - log_b)
+    if datafit == "poisson":
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lc = np.log(lam * y / eps)
+            g = eps * (lc - np.log(wright_omega(lc - log_b + lam / eps)) - log_b)
+        return np.where(y > 0, g, -lam)
     raise ValueError(datafit)
 
 
@@ -454,6 +475,14 @@ def _F2_conj_neg(datafit, g, y, lam):
     if datafit == "l2":
         inside = y - g / lam >= 0
         return float(np.sum(np.where(inside, -g * y + g * g / (2 * lam), -lam * y * y / 2)))
+    if datafit == "poisson":
+        # sup_t (-g t - lam t + lam y log t): finite only for g > -lam (y > 0) or g >= -lam (y = 0);
+        # at t = lam y / (lam + g) it is lam y (log(lam y / (lam + g)) - 1)
+        if np.any((y > 0) & (g <= -lam)) or np.any((y == 0) & (g < -lam * (1 + 1e-12))):
+            return np.inf
+        with np.errstate(divide="ignore", invalid="ignore"):
+            v = np.where(y > 0, lam * y * (np.log(lam * y / (lam + g)) - 1.0), 0.0)
+        return float(np.sum(v))
     raise ValueError(datafit)
 
 
@@ -499,6 +528,12 @@ def dual_objective(f, g, C, X, y, eps, lam, alpha, datafit, penalty, beta=0.0):
     bad = np.isneginf(f) & (X.sum(axis=1) > 0)
     if np.any(bad):
         f = np.where(bad, np.min(f[np.isfinite(f)]), f)
+    if datafit == "poisson":
+        # any g > -lam is dual-feasible at a bin with y > 0; a prox step at a bin with tiny y leaves
+        # g within rounding of -lam (g + lam = lam y / v), so such g are moved to -lam (1 - 2^-50),
+        # which keeps D a lower bound and changes the entropic term by ~lam 2^-50 / eps
+        gmin = -lam * (1.0 - 2.0 ** -50)
+        g = np.where((np.asarray(y) > 0) & (g < gmin), gmin, g)
     if penalty in ("l1", "none"):
         bound = alpha if penalty == "l1" else 0.0
         with np.errstate(invalid="ignore"):

@@ -150,3 +150,17 @@ def test_transposed_target_band_is_caught(monkeypatch):
         return ot.logsumexp(terms, axis=1)
     monkeypatch.setattr(ot, "_band_lse_cols", bad)
     assert _fails(pins.test_banded_solve_equals_the_dense_solve, "l2", "l2sq")
+
+
+def test_poisson_prox_with_the_printed_stationarity_sign_is_caught(monkeypatch):
+    """App. B's stationarity line as printed (eps log(q/k) - lam y/q - lam = 0) leads to
+    u e^u = (lam y / (eps s)) e^{-lam/eps}: the 1-D minimisation must reject it."""
+    good = ot.prox_datafit
+
+    def bad(datafit, s, y, eps, lam):
+        if datafit == "poisson":
+            c = lam * np.asarray(y) / eps
+            return c / ot.lambert_w0(c / np.asarray(s) * np.exp(-lam / eps))
+        return good(datafit, s, y, eps, lam)
+    monkeypatch.setattr(pins.oracle, "prox_datafit", bad)
+    assert _fails(pins.test_prox_matches_1d_minimisation, "poisson", 0.05, 1.0)

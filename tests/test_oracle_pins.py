@@ -74,6 +74,8 @@ def _prox_by_minimisation(datafit, b, y, eps, lam):
             L = v * np.log(v / y) - v + y
         elif datafit == "tv":
             L = abs(v - y)
+        elif datafit == "poisson":
+            L = v - y * np.log(v)
         else:
             L = 0.5 * (v - y) ** 2
         return lam * L + eps * (v * np.log(v / b) - v + b)
@@ -82,7 +84,7 @@ def _prox_by_minimisation(datafit, b, y, eps, lam):
     return np.exp(res.x)
 
 
-@pytest.mark.parametrize("datafit", ["kl", "tv", "l2"])
+@pytest.mark.parametrize("datafit", ["kl", "tv", "l2", "poisson"])
 @pytest.mark.parametrize("eps,lam", [(0.05, 1.0), (0.5, 0.3), (1.0, 2.0)])
 def test_prox_matches_1d_minimisation(datafit, eps, lam):
     rng = np.random.default_rng(7)
@@ -93,12 +95,24 @@ def test_prox_matches_1d_minimisation(datafit, eps, lam):
         assert got == pytest.approx(ref, rel=2e-6), (datafit, b, y)
 
 
+def test_poisson_prox_at_zero_target_bins():
+    """y = 0 leaves lam v + eps KL(v || b), minimised at v = b e^{-lam/eps}; the prox must reach
+    that limit continuously as y -> 0."""
+    b = np.array([0.3, 1.7])
+    for eps, lam in ((0.05, 1.0), (0.5, 0.3)):
+        v0 = oracle.prox_datafit("poisson", b, np.zeros(2), eps, lam)
+        np.testing.assert_allclose(v0, b * np.exp(-lam / eps), rtol=1e-14)
+        # v = v0 (1 + lam y / (eps v0) + ...): y = 1e-9 v0 moves it by ~1e-9 lam / eps
+        v_small = oracle.prox_datafit("poisson", b, 1e-9 * v0, eps, lam)
+        np.testing.assert_allclose(v_small, v0, rtol=1e-6)
+
+
 def test_prox_balanced_is_target():
     y = np.array([0.2, 0.0, 1.5])
     np.testing.assert_array_equal(oracle.prox_datafit("balanced", np.array([3.0, 1.0, 2.0]), y, 0.1, 1.0), y)
 
 
-@pytest.mark.parametrize("datafit", ["balanced", "kl", "tv", "l2"])
+@pytest.mark.parametrize("datafit", ["balanced", "kl", "tv", "l2", "poisson"])
 def test_log_potential_equals_linear_prox(datafit):
     """The log-domain potential update equals eps log(prox(b)/b); the second setting makes
     the TV clamp bind (|eps log(y/b)| > lam for part of the bins)."""
@@ -266,6 +280,8 @@ def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty, beta=0.0):
         t = Q.sum(0)
         if datafit == "kl":
             L = torch.sum(t * torch.log(t / yt) - t + yt)
+        elif datafit == "poisson":
+            L = torch.sum(t - yt * torch.log(t))
         else:
             L = 0.5 * torch.sum((t - yt) ** 2)
         if penalty == "elastic":
@@ -287,7 +303,7 @@ def _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty, beta=0.0):
 
 @pytest.mark.parametrize("datafit,penalty,mm_steps", [("kl", "l2sq", 1), ("l2", "l1", 1), ("kl", "l1", 1),
                                                       ("l2", "l2sq", 1), ("kl", "elastic", 1), ("l2", "elastic", 3),
-                                                      ("kl", "l1", 4)])
+                                                      ("kl", "l1", 4), ("poisson", "l1", 1), ("poisson", "l2sq", 2)])
 def test_brute_force_tiny_instance(datafit, penalty, mm_steps):
     """Same convex problem solved by a generic optimiser; C is not symmetric, so a transposed
     K or a swapped marginal in Algorithm 1 lands on a different w.  Several inner MM steps per
@@ -317,7 +333,7 @@ def test_linear_and_log_domain_agree(datafit, penalty):
 
 
 @pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("kl", "l1"), ("tv", "l1"), ("l2", "l2sq"), ("l2", "none"),
-                                             ("kl", "elastic")])
+                                             ("kl", "elastic"), ("poisson", "l2sq")])
 def test_invariants_along_the_trajectory(datafit, penalty):
     """w >= 0, Q >= 0, Q 1 = X w after the source step; primal objective non-increasing (observed,
     not proved in the paper: slack 1e-12 relative); weak duality P >= D at every iterate;
