@@ -58,7 +58,11 @@ typedef enum {            /* marginal datafit L(. | y), Table 1 */
   OTLM_DATAFIT_BALANCED = 0,  /* indicator {Q^T 1 = y}: prox = y                               */
   OTLM_DATAFIT_KL       = 1,  /* lam KL(s|y): prox = s^{eps/(eps+lam)} y^{lam/(eps+lam)}        */
   OTLM_DATAFIT_TV       = 2,  /* lam ||s-y||_1: prox = min(s e^{lam/eps}, max(s e^{-lam/eps},y)) */
-  OTLM_DATAFIT_L2       = 3   /* (lam/2)||s-y||^2: prox = (eps/lam) W0((lam/eps) s e^{lam y/eps}) */
+  OTLM_DATAFIT_L2       = 3,  /* (lam/2)||s-y||^2: prox = (eps/lam) W0((lam/eps) s e^{lam y/eps}) */
+  OTLM_DATAFIT_POISSON  = 4   /* lam sum (s - y log s): prox = (lam y/eps) / W0((lam y/(eps s))
+                                 e^{lam/eps}), s e^{-lam/eps} where y = 0 (Table 1's last row; its
+                                 "W0^{-1}" read as 1/W0, re-derived from the stationarity
+                                 condition of App. B); not accepted by otlm_objective */
 } otlm_datafit;
 
 typedef enum {            /* weight penalty R(w), Table 2 */
@@ -264,7 +268,7 @@ int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const floa
  * primal_out - dual_out is a duality gap.  BALANCED datafit: primal_out is +inf unless Q^T 1 = y.
  * The two kernel applies run in the handle's arithmetic; all sums are FP64.
  *   w [batch][k], g [batch][n] as returned by otlm_solve; primal_out, dual_out [batch] device
- *   doubles.  Errors as otlm_solve. */
+ *   doubles.  Errors as otlm_solve, plus OTLM_EUNSUPPORTED for the Poisson datafit. */
 int otlm_objective(otlm_handle h, int batch, int n, int k,
                    const void* x, const void* D, const void* y,
                    double eps, double lam, double alpha,

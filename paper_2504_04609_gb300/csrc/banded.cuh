@@ -274,9 +274,14 @@ __device__ __forceinline__ float band_datafit(const BandArgs& A, float v, float 
     case DF_BALANCED: return P::log2(yv) - v;
     case DF_KL: return A.kl_coef * (P::log2(yv) - v);
     case DF_TV: return fminf(fmaxf(P::log2(yv) - v, -A.tv_bound), A.tv_bound);
-    default: {
-      const float z = A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
-      return (A.lam_over_eps * yv - wright_omega_fast(z)) * float(kLog2e);
+    default: {  // L2 or Poisson (reading A7; -lam where y = 0), one Wright omega
+      const bool pois = A.datafit == DF_POISSON;
+      if (pois && !(yv > 0.f)) return -A.tv_bound;
+      const float l2c = pois ? A.log_lam_over_eps * float(kLog2e) + P::log2(yv) : 0.f;
+      const float z = pois ? (l2c - v) * float(kLn2) + A.lam_over_eps
+                           : A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
+      const float om = wright_omega_fast(z);
+      return pois ? l2c - P::log2(om) - v : (A.lam_over_eps * yv - om) * float(kLog2e);
     }
   }
 }

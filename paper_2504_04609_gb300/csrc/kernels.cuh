@@ -11,9 +11,20 @@
 namespace otlm {
 
 enum { EPI_SOURCE = 0, EPI_TARGET = 1 };
-enum { DF_BALANCED = 0, DF_KL = 1, DF_TV = 2, DF_L2 = 3 };
+enum { DF_BALANCED = 0, DF_KL = 1, DF_TV = 2, DF_L2 = 3, DF_POISSON = 4 };
 enum { PEN_NONE = 0, PEN_L1 = 1, PEN_L2SQ = 2, PEN_ELASTIC = 3 };
 enum { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_NONFINITE = 2, ST_INVALID = 3 };
+
+// Poisson datafit step (reading A7) in log2 units, from v = log2 b and the target bin y:
+// G2 = log2(lam y/eps) - log2 omega(ln(lam y/eps) - ln b + lam/eps) - v, and -lam/(eps ln2) where
+// y = 0 (`neg_bound`).  Kept out of line so that the apply kernel's epilogue keeps its registers.
+template <typename T>
+__device__ __noinline__ T poisson_g2(T log_lam_over_eps, T lam_over_eps, T neg_bound, T v, T yv) {
+  using P = Prec<T>;
+  if (!(yv > T(0))) return -neg_bound;
+  const T l2c = log_lam_over_eps * T(kLog2e) + P::log2(yv);
+  return l2c - P::log2(wright_omega<T>((l2c - v) * T(kLn2) + lam_over_eps)) - v;
+}
 
 template <typename T>
 struct ApplyArgs {
@@ -362,6 +373,7 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
             case DF_BALANCED: gn = P::log2(yv) - v; break;
             case DF_KL: gn = A.kl_coef * (P::log2(yv) - v); break;
             case DF_TV: gn = fmin(fmax(P::log2(yv) - v, -A.tv_bound), A.tv_bound); break;
+            case DF_POISSON: gn = poisson_g2<T>(A.log_lam_over_eps, A.lam_over_eps, A.tv_bound, v, yv); break;
             default: {  // L2: g = lam y - eps omega(ln(lam/eps) + ln b + (lam/eps) y)
               const T z = A.log_lam_over_eps + v * T(kLn2) + A.lam_over_eps * yv;
               gn = (A.lam_over_eps * yv - wright_omega<T>(z)) * T(kLog2e);

@@ -50,7 +50,7 @@ namespace {
 
 bool valid_enum(const otlm_config& c) {
   return (c.precision == OTLM_PREC_FP32_LOG || c.precision == OTLM_PREC_FP64 || c.precision == OTLM_PREC_BF16_TC) &&
-         (c.datafit >= OTLM_DATAFIT_BALANCED && c.datafit <= OTLM_DATAFIT_L2) &&
+         (c.datafit >= OTLM_DATAFIT_BALANCED && c.datafit <= OTLM_DATAFIT_POISSON) &&
          (c.penalty >= OTLM_PENALTY_NONE && c.penalty <= OTLM_PENALTY_ELASTIC) &&
          (c.penalty != OTLM_PENALTY_ELASTIC || (c.beta > 0 && std::isfinite(c.beta))) &&
          c.mm_steps >= 0 && c.mm_steps <= 64;
@@ -356,6 +356,7 @@ int otlm_objective(otlm_handle h, int batch, int n, int k, const void* x, const 
   if (!h || !x || !D || !y || !w || !g || !primal_out || !dual_out) return OTLM_EINVAL;
   int rc = check_problem(h, batch, n, k, eps, lam, alpha);
   if (rc != OTLM_OK) return rc;
+  if (h->cfg.datafit == OTLM_DATAFIT_POISSON) return OTLM_EUNSUPPORTED;
   const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
   if (h->cfg.precision == OTLM_PREC_FP64) return run_objective<double>(h, sp, x, D, y, w, g, primal_out, dual_out);
   return run_objective<float>(h, sp, x, D, y, w, g, primal_out, dual_out);

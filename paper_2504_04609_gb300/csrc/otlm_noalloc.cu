@@ -56,7 +56,7 @@ extern "C" int otlm_solve_noalloc(int batch, int n, int k, const float* x, const
                                   int* status_out, void* cuda_stream) {
   if (!x || !D || !y || !w) return OTLM_EINVAL;
   if (batch < 1 || n < 2 || k < 1 || k > 256 || max_iter < 1) return OTLM_EINVAL;
-  if (datafit < OTLM_DATAFIT_BALANCED || datafit > OTLM_DATAFIT_L2) return OTLM_EINVAL;
+  if (datafit < OTLM_DATAFIT_BALANCED || datafit > OTLM_DATAFIT_POISSON) return OTLM_EINVAL;
   if (penalty < OTLM_PENALTY_NONE || penalty > OTLM_PENALTY_L2SQ) return OTLM_EINVAL;
   if (!(eps > 0) || !(alpha >= 0) || !(tol == tol)) return OTLM_EINVAL;
   if (datafit != OTLM_DATAFIT_BALANCED && !(lam > 0)) return OTLM_EINVAL;

@@ -308,9 +308,16 @@ __device__ void ragged_solve_one(const RaggedArgs& A, int p, float* sm) {
         case DF_BALANCED: gn = P::log2(yv) - v; break;
         case DF_KL: gn = kl_coef * (P::log2(yv) - v); break;
         case DF_TV: gn = fminf(fmaxf(P::log2(yv) - v, -tv_bound), tv_bound); break;
-        default: {
-          const float z = lloe + v * float(kLn2) + loe * yv;
-          gn = (loe * yv - wright_omega<float>(z)) * float(kLog2e);
+        default: {  // L2 or Poisson (reading A7; -lam where y = 0), one Wright omega
+          const bool pois = A.datafit == DF_POISSON;
+          if (pois && !(yv > 0.f)) {
+            gn = -tv_bound;
+            break;
+          }
+          const float l2c = pois ? lloe * float(kLog2e) + P::log2(yv) : 0.f;
+          const float z = pois ? (l2c - v) * float(kLn2) + loe : lloe + v * float(kLn2) + loe * yv;
+          const float om = wright_omega<float>(z);
+          gn = pois ? l2c - P::log2(om) - v : (loe * yv - om) * float(kLog2e);
         }
       }
       G2[j] = gn;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libotlm.so")
 
 OTLM_OK, OTLM_EINVAL, OTLM_ECUDA, OTLM_ENOMEM, OTLM_EUNSUPPORTED, OTLM_ESCRATCH, OTLM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 CONVERGED, MAX_ITER, NONFINITE, INVALID = 0, 1, 2, 3
-DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3}
+DATAFIT = {"balanced": 0, "kl": 1, "tv": 2, "l2": 3, "poisson": 4}
 PENALTY = {"none": 0, "l1": 1, "l2sq": 2, "elastic": 3}
 PRECISION = {"fp32": 0, "fp64": 1, "bf16tc": 2}
 

@@ -73,6 +73,7 @@ def _oracle(d, p, datafit, penalty, eps, lam, alpha, iters, tol=0.0, beta=0.0):
     ("l2", "l2sq", TOL_EPS1E3),   # OT ridge of the scalability test (potentials near 1e3 log2 units)
     ("tv", "l1", TOL_EPS1E3),     # OT-TV of the scalability test (TV clamp at 1443 log2 units)
     ("kl", "elastic", TOL32),
+    ("poisson", "l1", TOL_EPS1E3),  # Poisson at eps = 1e-3: potentials up to lam / (eps ln2) as for TV
 ])
 def test_scalability_inputs_trajectory_parity(datafit, penalty, bar):
     """3 targets (two groups of 2 per CTA, the second one short), n = 2300 (nine 256-bin tiles, the

@@ -58,6 +58,8 @@ CASES = [  # (datafit, penalty, eps, lam, alpha)
     ("balanced", "none", 2e-2, 1.0, 0.0),
     ("l2", "none", 3e-2, 1.0, 0.0),
     ("kl", "none", 2e-2, 0.5, 0.0),
+    ("poisson", "l2sq", 1e-2, 1.0, 1e-3),
+    ("poisson", "l1", 2e-2, 1.0, 1e-2),
 ]
 
 
@@ -87,7 +89,7 @@ def test_fp64_single_target_n200():
     np.testing.assert_allclose(r["g"][0], o["g"], rtol=1e-9, atol=1e-12)
 
 
-@pytest.mark.parametrize("datafit,penalty,eps,lam,alpha", [CASES[0], CASES[2], CASES[3]])
+@pytest.mark.parametrize("datafit,penalty,eps,lam,alpha", [CASES[0], CASES[2], CASES[3], CASES[7]])
 def test_fp64_parity_matches_oracle_tightly(datafit, penalty, eps, lam, alpha):
     d = spectra.batch(12, 3, 257, 33, 4, dtype=np.float64)
     r = _gpu_solve(d, eps, lam, alpha, datafit, penalty, 60, precision="fp64")
@@ -204,3 +206,22 @@ def test_objective_and_gap_match_oracle(datafit, penalty, eps, lam, alpha):
             assert P[p].item() == pytest.approx(Po, rel=2e-6)
         assert Dv[p].item() == pytest.approx(Do, rel=2e-6)
         assert P[p].item() - Dv[p].item() >= -1e-6 * abs(Po)
+
+
+def test_poisson_zero_target_bins_and_objective_refusal():
+    """Poisson datafit with exact zeros in y (g = -lam there, t = b e^{-lam/eps}); the FP32 path
+    follows the oracle, and otlm_objective refuses the Poisson datafit."""
+    d = spectra.batch(19, 3, 160, 6, 2)
+    d["y"][:, :25] = 0.0
+    r = _gpu_solve(d, 2e-2, 1.0, 1e-2, "poisson", "l1", 25)
+    for p in range(3):
+        o = _oracle(d, p, 2e-2, 1.0, 1e-2, "poisson", "l1", 25)
+        np.testing.assert_allclose(r["g"][p][:25], -1.0, rtol=1e-6)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL32 and rel_l1(r["t"][p], o["t"]) <= TOL32
+    h = api.Handle(160, 6, 3, "fp32", "poisson", "l1", 25, 0.0, 4)
+    P = torch.empty(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.OTLMError):
+        h.objective(torch.tensor(d["x"], device="cuda"), torch.tensor(d["D"], device="cuda"),
+                    torch.tensor(d["y"], device="cuda"), 2e-2, 1.0, 1e-2, torch.tensor(r["w"], device="cuda"),
+                    torch.tensor(r["g"], device="cuda"), P, P)
+    h.close()

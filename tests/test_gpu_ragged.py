@@ -55,7 +55,7 @@ def _oracle(p, datafit, penalty, lam, alpha, iters, tol=0.0):
 
 
 @pytest.mark.parametrize("datafit,penalty,lam,alpha", [("tv", "l1", 1.0, 1e-2), ("l2", "l2sq", 1.0, 1e-3),
-                                                       ("kl", "l1", 1.0, 1e-2)])
+                                                       ("kl", "l1", 1.0, 1e-2), ("poisson", "l2sq", 1.0, 1e-3)])
 def test_ragged_trajectory_parity(datafit, penalty, lam, alpha):
     """Ten problems, n in [256, 700] (one and two rows per thread), k in [8, 60], own eps."""
     probs = spectra.ragged(41, 10, n_range=(256, 700), k_range=(8, 60))

@@ -41,6 +41,7 @@ def _oracle(d, p, eps, lam, alpha, datafit, penalty, iters, tol=0.0):
     ("l2", "l1", 2e-2, 1.0, 1e-2),
     ("kl", "l2sq", 5e-2, 1.0, 1e-3),
     ("tv", "l1", 5e-2, 1.0, 1e-2),
+    ("poisson", "l2sq", 2e-2, 1.0, 1e-3),
 ])
 def test_tensorcore_trajectory_parity_small(datafit, penalty, eps, lam, alpha):
     """9 problems (one partial 128-column tile; a batch this small splits each apply's reduction),
