@@ -1,4 +1,4 @@
-"""FP64 CPU reference of the learned warm-start network (the benchmark spec's extension; the paper has
+"""FP64 CPU reference of the learned warm-start network (an extension of the solver; the paper has
 no learned component).  TEST INFRASTRUCTURE ONLY, like the rest of oracle/.
 
 Network: features x0 = [n y / sum(y), log sum(y)]; h_l = GELU(h_{l-1} W_l^T + b_l) for l = 1..3
