@@ -360,6 +360,30 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
                 t=Q.sum(axis=0), s=Q.sum(axis=1), log_a=log_a)
 
 
+def solve_converged(C, X, y, eps, lam, alpha, datafit, penalty, w0, rtol_w=1e-14, max_iter=10 ** 6, g0=None,
+                    beta=0.0, mm_steps=1):
+    """The long-run solution: Algorithm 1 (log domain) continued from (w0, g0) one iteration at a
+    time until ||w_new - w||_1 / ||w_new||_1 < rtol_w or max_iter iterations.  The marginal
+    violation of reading A8 reaches small tolerances long before w settles, so this is the
+    reference for the solution quality of a solve stopped at tol.
+
+    Returns dict(w, g, t, iters, dw) with dw the last relative change of w.
+    """
+    w = np.asarray(w0, dtype=np.float64).copy()
+    g = None if g0 is None else np.asarray(g0, dtype=np.float64).copy()
+    dw = np.inf
+    r = None
+    it = 0
+    while it < max_iter:
+        r = solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w, 1, g0=g, beta=beta, mm_steps=mm_steps)
+        it += 1
+        dw = float(np.sum(np.abs(r["w"] - w)) / np.sum(np.abs(r["w"])))
+        w, g = r["w"], r["g"]
+        if dw < rtol_w:
+            break
+    return dict(w=w, g=g, t=r["t"], iters=it, dw=dw)
+
+
 def band_to_dense(Cd, h):
     """Dense C [n, n] from the diagonal (DIA) storage Cd [2h+1, n] of a banded cost:
     C_{i, i+d-h} = Cd[d, i]; every pair outside the band, or stored as +inf, is forbidden

@@ -411,3 +411,17 @@ def test_banded_solve_equals_the_dense_solve(datafit, penalty):
     np.testing.assert_allclose(b["w"], a["w"], rtol=1e-11)
     np.testing.assert_allclose(b["t"], a["t"], rtol=1e-10, atol=1e-300)
     np.testing.assert_allclose(b["err_hist"], a["err_hist"], rtol=1e-8)
+
+
+@pytest.mark.parametrize("datafit,penalty", [("kl", "l1"), ("l2", "l2sq")])
+def test_converged_solution_is_the_optimum(datafit, penalty):
+    """The long-run solution (||dw||/||w|| < 1e-14) closes the duality gap and equals the brute-force
+    optimum of the tiny instance."""
+    X, y, C = _tiny(n=5, k=2, seed=13)
+    eps, lam, alpha = 0.05, 1.0, 0.02
+    r = oracle.solve_converged(C, X, y, eps, lam, alpha, datafit, penalty, np.ones(2), max_iter=200000)
+    assert r["dw"] < 1e-14
+    P, Dv, _ = oracle.objective_and_dual(r["w"], r["g"], C, X, y, eps, lam, alpha, datafit, penalty)
+    assert P - Dv <= 1e-10 * abs(P)
+    w_bf, _ = _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty)
+    np.testing.assert_allclose(r["w"], w_bf, rtol=2e-5)
