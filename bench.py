@@ -33,6 +33,23 @@ import numpy as np  # noqa: E402
 import spectra  # noqa: E402
 
 METRIC = "OTLM problems solved/s to 1e-5 marginal tol (n=4096) vs plain FP32 on 1 GB300; % roofline"
+# the metric of each secondary workload, by name prefix (the same for the GPU arm and the reference arm)
+WORKLOAD_METRICS = {
+    "batch1024_n1024": "OTLM problems solved/s to 1e-5 marginal tol (n=1024 batch) vs plain FP32 on 1 GB300",
+    "ragged": "OTLM problems solved/s to 1e-5 marginal tol, uneven batch (n ~ U{256..4096}) in one persistent launch",
+    "warmstart": "OTLM problems solved/s to 1e-5 marginal tol, learned warm start vs cold start (n=2048)",
+    "single": "OTLM single-target FP64 solve time (n=m=200, k=10, 500 iterations)",
+    "hbm": "single-target OTLM solves/s to 1e-5 marginal tol at n=16384 (stored kernel streamed from HBM)",
+    "banded": "OTLM problems/s to 1e-5 marginal tol, banded cost + sparse dictionary at n=100000 "
+              "(the paper's scalability test)",
+}
+
+
+def workload_metric(workload: str) -> str:
+    for prefix, metric in WORKLOAD_METRICS.items():
+        if workload.startswith(prefix):
+            return metric
+    return METRIC
 SMS = 152
 MAX_SM_MHZ = 2070.0
 # exponent-unit (MUFU.EX2) results per SM per clock on GB300; a throughput probe measured 30.3
@@ -85,12 +102,31 @@ d = spectra.batch(c["id"], {count}, c["n"], c["k"], c["nnz"], first={first})
 C = spectra.squared_cost(d["x"].astype(np.float64))
 D = d["D"].astype(np.float64)
 out = []
-iters, tol = ({max_iters}, 0.0) if {max_iters} else (c["iters"], c["tol"])
+iters, tol = ({max_iters}, 0.0) if {max_iters} else (c["iters"], c.get("tol", 0.0))
 for p in range({count}):
     y = d["y"][p].astype(np.float64)
     t0 = time.perf_counter()
     r = oracle.solve_log(C, D, y, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"],
                          spectra.initial_weights(y, D), iters, tol=tol)
+    out.append((time.perf_counter() - t0, int(r["iters"])))
+print(json.dumps(out))
+"""
+
+
+_ORACLE_CHILD_RAGGED = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle, spectra
+c = spectra.WORKLOADS[{wl!r}]
+out = []
+iters, tol = ({max_iters}, 0.0) if {max_iters} else (c["iters"], c.get("tol", 0.0))
+for q in spectra.ragged(c["id"], {count}, first={first}):
+    D = q["D"].astype(np.float64)
+    y = q["y"].astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.solve_log(spectra.squared_cost(q["x"].astype(np.float64)), D, y, q["eps"], c["lam"], c["alpha"],
+                         c["datafit"], c["penalty"], spectra.initial_weights(y, D), iters, tol=tol)
     out.append((time.perf_counter() - t0, int(r["iters"])))
 print(json.dumps(out))
 """
@@ -122,7 +158,8 @@ def oracle_sample(workload: str, count: int, first: int, max_iters: int = 0):
     """FP64 oracle on `count` problems of the workload: to its tolerance, or exactly `max_iters`
     iterations when given (the bounded sample of a workload whose full solve takes minutes)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    child = _ORACLE_CHILD_BANDED if workload.startswith("banded") else _ORACLE_CHILD
+    child = (_ORACLE_CHILD_BANDED if workload.startswith("banded") else
+             _ORACLE_CHILD_RAGGED if workload.startswith("ragged") else _ORACLE_CHILD)
     src = child.format(root=ROOT, wl=workload, count=count, first=first, max_iters=int(max_iters))
     r = subprocess.run([sys.executable, "-c", src], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -327,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
                                         "probe measured 30.3 ex2/clk/SM)"},
              "clocks": fp["clocks"]}
     out = {
-        "metric": METRIC,
+        "metric": workload_metric(args.workload),
         "value": value,
         "unit": "problems/s",
         "n_gpus": world,
@@ -456,7 +493,7 @@ def run_ragged(args, rank, world, local_rank):
     h2d = (hx.numel() + hD.numel() + hy.numel() + hw0.numel()) * 4
     d2h = (hw.numel() + ht.numel() + hit.numel()) * 4
     out = {
-        "metric": "OTLM problems solved/s to 1e-5 marginal tol, uneven batch (n ~ U{256..4096}) in one persistent launch",
+        "metric": workload_metric(args.workload),
         "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
@@ -525,7 +562,7 @@ def run_single_fp64(args, rank, local_rank):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     h.close()
-    return {"metric": "OTLM single-target FP64 solve time (n=m=200, k=10, 500 iterations)", "value": ms,
+    return {"metric": workload_metric(args.workload), "value": ms,
             "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
@@ -564,7 +601,7 @@ def run_warmstart(args, rank, local_rank):
     t0 = time.perf_counter()
     losses = ws.train(net, ytr, targets, epochs=args.ws_epochs, batch=512, lr=1e-3, weight_decay=1e-5, log_every=100)
     train_s = time.perf_counter() - t0
-    out = {"metric": "OTLM problems solved/s to 1e-5 marginal tol, learned warm start vs cold start (n=2048)",
+    out = {"metric": workload_metric(args.workload),
            "unit": "problems/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 solve, bf16-weight MLP", "data": "synthetic (seeded Gaussian-peak spectra)",
            "config": {"workload": args.workload, "n": n, "k": k, "eps": c["eps"], "datafit": c["datafit"],
@@ -691,7 +728,7 @@ def run_single_hbm(args, rank, world, local_rank):
     achieved = 4.0 * n * n / (launch_ms / 1e3) / 1e9
     peak = float(_peaks().get("hbm_gbs", 6800.0))
     out = {
-        "metric": "single-target OTLM solves/s to 1e-5 marginal tol at n=16384 (stored kernel streamed from HBM)",
+        "metric": workload_metric(args.workload),
         "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3 tensor (hi/lo split) + f32",
@@ -824,8 +861,7 @@ def run_banded(args, rank, world, local_rank):
     achieved = ex2_per_launch / (launch_ms / 1e3) / 1e9
     peak = 152 * 32 * 2.07
     out = {
-        "metric": "OTLM problems/s to 1e-5 marginal tol, banded cost + sparse dictionary at n=100000 "
-                  "(the paper's scalability test)",
+        "metric": workload_metric(args.workload),
         "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (log domain)",
@@ -864,8 +900,7 @@ def run_reference(args, rank):
         for s in range(args.steps):
             secs += oracle_sample(args.workload, 1, s, max_iters=BANDED_ORACLE_ITERS)[0][0]
         v = args.steps / (secs / BANDED_ORACLE_ITERS * BANDED_ITERS_TO_TOL)
-        return {"impl": "reference", "metric": "OTLM problems/s to 1e-5 marginal tol, banded cost + sparse "
-                                                "dictionary at n=100000 (the paper's scalability test)",
+        return {"impl": "reference", "metric": workload_metric(args.workload),
                 "value": v, "unit": "problems/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic (the scalability appendix's recipe)",
@@ -879,8 +914,7 @@ def run_reference(args, rank):
         for s in range(args.steps):
             secs += oracle_sample(args.workload, 1, s, max_iters=HBM_ORACLE_ITERS)[0][0]
         v = args.steps / (secs / HBM_ORACLE_ITERS * HBM_ITERS_TO_TOL)
-        return {"impl": "reference", "metric": "single-target OTLM solves/s to 1e-5 marginal tol at n=16384 "
-                                                "(stored kernel streamed from HBM)",
+        return {"impl": "reference", "metric": workload_metric(args.workload),
                 "value": v, "unit": "problems/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
@@ -896,16 +930,19 @@ def run_reference(args, rank):
     for s in range(args.steps):
         samp += oracle_sample(args.workload, 1, s)
     secs = time.perf_counter() - t0
-    v = len(samp) / secs
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "problems/s", "n_gpus": 1,
+    if args.workload.startswith("single"):  # this workload's metric is a solve time
+        v, unit, higher = secs * 1e3 / len(samp), "ms", False
+    else:
+        v, unit, higher = len(samp) / secs, "problems/s", True
+    return {"impl": "reference", "metric": workload_metric(args.workload), "value": v, "unit": unit, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
-            "config": {"workload": args.workload, "n": c["n"], "k": c["k"], "eps": c["eps"], "tol": c["tol"],
-                       "sample_per_step": "1 problem", "iters": [i for _, i in samp]},
-            "cpu_baseline": {"value": v, "unit": "problems/s", "cores": 1, "kind": "oracle",
+            "config": {"workload": args.workload, "n": c.get("n"), "k": c.get("k"), "eps": c.get("eps"),
+                       "tol": c.get("tol"), "sample_per_step": "1 problem", "iters": [i for _, i in samp]},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
                              "sample": f"{len(samp)} problems of {args.workload}, one per step, FP64 numpy oracle"},
-            "e2e": {"value": v, "unit": "problems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
