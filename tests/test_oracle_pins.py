@@ -397,8 +397,9 @@ def test_band_to_dense_inverts_the_diagonal_storage():
     np.testing.assert_array_equal(oracle.band_to_dense(Cd, 5), C)
 
 
-@pytest.mark.parametrize("datafit,penalty", [("l2", "l2sq"), ("tv", "l1"), ("kl", "elastic")])
-def test_banded_solve_equals_the_dense_solve(datafit, penalty):
+@pytest.mark.parametrize("datafit,penalty,mm_steps", [("l2", "l2sq", 1), ("tv", "l1", 1), ("kl", "elastic", 1),
+                                                      ("poisson", "l1", 1), ("kl", "l2sq", 3)])
+def test_banded_solve_equals_the_dense_solve(datafit, penalty, mm_steps):
     """Forbidden pairs have K = 0, so summing Algorithm 1's applies over the band must reproduce
     the dense solve on the same cost; the cost is not symmetric, so reading the target apply's band
     from the wrong diagonal changes the result."""
@@ -406,8 +407,9 @@ def test_banded_solve_equals_the_dense_solve(datafit, penalty):
     C, Cd, X, y = _banded_case()
     eps, lam, alpha = 5e-3, 1.0, 1e-3
     w0 = np.full(X.shape[1], y.sum() / X.sum())
-    a = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, 40, beta=BETA)
-    b = oracle.solve_log_banded(Cd, 5, csc_matrix(X), y, eps, lam, alpha, datafit, penalty, w0, 40, beta=BETA)
+    a = oracle.solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, 40, beta=BETA, mm_steps=mm_steps)
+    b = oracle.solve_log_banded(Cd, 5, csc_matrix(X), y, eps, lam, alpha, datafit, penalty, w0, 40, beta=BETA,
+                                mm_steps=mm_steps)
     np.testing.assert_allclose(b["w"], a["w"], rtol=1e-11)
     np.testing.assert_allclose(b["t"], a["t"], rtol=1e-10, atol=1e-300)
     np.testing.assert_allclose(b["err_hist"], a["err_hist"], rtol=1e-8)
