@@ -427,3 +427,18 @@ def test_converged_solution_is_the_optimum(datafit, penalty):
     assert P - Dv <= 1e-10 * abs(P)
     w_bf, _ = _brute_force_primal(X, y, C, eps, lam, alpha, datafit, penalty)
     np.testing.assert_allclose(r["w"], w_bf, rtol=2e-5)
+
+
+@pytest.mark.parametrize("datafit,penalty", [("kl", "l1"), ("tv", "l2sq"), ("poisson", "l1")])
+def test_violation_is_the_source_marginal_error_of_the_explicit_plan(datafit, penalty):
+    """Reading A8: after an iteration the solver measures e = ||Q 1 - X w||_1 / ||X w||_1 for the plan
+    Q = diag(u2) K diag(u1) with the u1 of the next iteration; formed here as a matrix from the
+    returned scalings."""
+    X, y, C = _tiny(n=7, k=3, seed=23)
+    eps, lam, alpha = 0.05, 1.0, 0.02
+    for T in (1, 2, 5):
+        r = oracle.solve(C, X, y, eps, lam, alpha, datafit, penalty, np.ones(3), T)
+        Q = r["u2"][:, None] * np.exp(-C / eps) * r["u1"][None, :]
+        s = X @ r["w"]
+        assert r["err"] == pytest.approx(np.abs(Q.sum(axis=1) - s).sum() / s.sum(), rel=1e-12)
+        assert len(r["err_hist"]) == T
