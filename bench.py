@@ -864,6 +864,7 @@ def run_banded(args, rank, world, local_rank):
         "metric": workload_metric(args.workload),
         "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "iters_per_s": float(its.sum()) * world * args.steps / (ms / 1e3),
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (log domain)",
         "data": "synthetic (the scalability appendix's recipe: skew-normal mixtures, truncated Gaussian basis)",
         "config": {"workload": args.workload, "B_per_gpu": B, "n": n, "k": k, "hw": hw, "nnz": int(d["val"].size),
