@@ -731,6 +731,7 @@ def run_single_hbm(args, rank, world, local_rank):
         "metric": workload_metric(args.workload),
         "value": whole_job_rate(B, world, args.steps, ms / 1e3), "unit": "problems/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "iters_per_s": whole_job_rate(B, world, args.steps, ms / 1e3) * it,
         "vs_baseline": None, "dtype": "bf16x3 tensor (hi/lo split) + f32",
         "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
         "config": {"workload": args.workload, "B_per_gpu": B, "n": n, "k": k, "eps": c["eps"], "datafit": c["datafit"],
