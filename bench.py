@@ -592,12 +592,11 @@ def run_warmstart(args, rank, local_rank):
     del dtr, dte
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    targets = ws.make_labels(x, D, ytr, c)
+    net = api.WarmStart(n, k, 512, 512, seed=2504_04609)
+    targets = ws.make_labels(net, x, D, ytr, c)
     torch.cuda.synchronize()
     label_s = time.perf_counter() - t0
-    mean, std = ws.normalization(targets)
-    net = api.WarmStart(n, k, 512, 512, seed=2504_04609)
-    net.set_normalization(mean, std)
+    ws.normalization(net, targets)
     t0 = time.perf_counter()
     losses = ws.train(net, ytr, targets, epochs=args.ws_epochs, batch=512, lr=1e-3, weight_decay=1e-5, log_every=100)
     train_s = time.perf_counter() - t0

@@ -204,9 +204,11 @@ int otlm_solve_banded(otlm_handle h, int batch, int n, int hw, const float* Cd,
  * must be OTLM_PREC_FP32_LOG.  One CTA solves one problem at a time with its state in shared memory; CTAs
  * take problems largest-first from a device queue; the launch is captured in a CUDA graph (on an
  * internal stream ordered after the handle's stream) and replayed while the arguments repeat.
- * The host copies n, k, eps once to validate and order the batch (a synchronous copy).
- * Errors: OTLM_EINVAL (sizes beyond the handle, eps <= 0, NULL pointers), OTLM_EUNSUPPORTED
- * (handle not FP32), OTLM_ENOMEM, OTLM_ECUDA. */
+ * The host copies n, k, eps and the three offset arrays once to validate and order the batch
+ * (synchronous copies): every problem's range must lie inside the packed lengths sum n, sum n k
+ * and sum k (offsets may come in any order).
+ * Errors: OTLM_EINVAL (sizes beyond the handle, eps <= 0, an offset range outside the packed
+ * arrays, NULL pointers), OTLM_EUNSUPPORTED (handle not FP32), OTLM_ENOMEM, OTLM_ECUDA. */
 int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
                       const long long* off_n, const long long* off_D, const long long* off_k,
                       const float* x, const float* D, const float* y, double lam, double alpha,
@@ -250,6 +252,18 @@ int otlm_ws_gradients(otlm_ws w, int batch, const float* y, const float* target,
 /* One AdamW step on that loss (learning rate lr, weight decay wd); loss_out may be NULL. */
 int otlm_ws_train_step(otlm_ws w, int batch, const float* y, const float* target, double lr,
                        double weight_decay, float* loss_out);
+/* Training targets from solved problems: targets [batch][n + k] = [g / eps, log w] for g [batch][n]
+ * and w [batch][k] as returned by otlm_solve; g / eps is clipped below at g_floor, and a
+ * non-finite g or a weight <= 0 gives -inf (masked by the loss).  batch is not bounded by
+ * batch_max.  Errors: OTLM_EINVAL (NULL pointers, batch < 1, eps not finite and > 0, g_floor NaN),
+ * OTLM_ECUDA. */
+int otlm_ws_make_targets(otlm_ws w, int batch, const float* g, const float* wts, double eps, double g_floor,
+                         float* targets);
+/* Output normalisation fitted to training targets [rows][n + k]: per output, the mean and the
+ * standard deviation (floored at 1e-3) over the finite entries, two passes with FP64 sums; stored
+ * on the network (as otlm_ws_set_normalization) and copied to mean_out / std_out [n + k] when not
+ * NULL.  rows is not bounded by batch_max.  Errors: OTLM_EINVAL, OTLM_ECUDA. */
+int otlm_ws_fit_normalization(otlm_ws w, int rows, const float* targets, float* mean_out, float* std_out);
 /* Warm start for otlm_solve: g0 [batch][n] = eps * predicted g/eps, w0 [batch][k] = exp(predicted
  * log w); a non-finite prediction falls back to the cold start (g0 = 0, w0 = cold_w).  The forward
  * pass runs on the tensor cores (BF16 weights times activations carried as BF16 hi/lo pairs, FP32
@@ -257,6 +271,14 @@ int otlm_ws_train_step(otlm_ws w, int batch, const float* y, const float* target
  * GEMMs gives up a bounded wait, every row falls back to the cold start. */
 int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const float* cold_w, float* g0,
                     float* w0);
+
+/* Cold start of Algorithm 1 on the device: w_out [batch][k] = sum_i y_pi / (k x_j), x_j = sum_i D_ij
+ * (Algorithm 1 leaves the initial w open; this reading spreads the target's mass evenly over the
+ * atoms; the matching initial potential is u1 = 1, i.e. g = NULL in otlm_solve).  D [n][k] and
+ * y [batch][n] as in otlm_solve, element type of the handle; sums in FP64.  Uses the handle's
+ * stream and workspace (column masses); asynchronous.
+ * Errors: OTLM_EINVAL (NULL pointers, batch/n/k beyond the handle), OTLM_ECUDA. */
+int otlm_initial_weights(otlm_handle h, int batch, int n, int k, const void* D, const void* y, void* w_out);
 
 /* Objective of a solver state (w, g), in FP64 (Eq. OTLM with the reading above).
  * From (w, g): a = K u1, s = D w, f = eps log(s/a); the plan Q = diag(e^{f/eps}) K diag(e^{g/eps})

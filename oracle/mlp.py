@@ -90,3 +90,27 @@ def loss_and_grad(params, dims, y, target, mean, std, round_weights=True):
     grads.reverse()
     flat = np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
     return loss, flat
+
+
+def grad_magnitudes(params, dims, y, target, mean, std, round_weights=True):
+    """Per gradient entry, the sum of the absolute values of the terms the chain rule adds up:
+    the same backward pass as `loss_and_grad` with every factor replaced by its absolute value
+    (|d| @ |W|, |gelu'|, |d|^T @ |h|).  Floating-point evaluation of an entry errs by at most a
+    multiple of this scale times the unit roundoff, so it is the natural per-entry tolerance scale
+    for comparing a lower-precision gradient with this reference."""
+    params = np.asarray(params, np.float64)
+    layers = unpack(params, dims)
+    z, hs, pres = forward(params, dims, y, round_weights)
+    t = np.asarray(target, np.float64)
+    mask = np.isfinite(t)
+    tn = np.where(mask, (np.where(mask, t, 0.0) - mean) / std, 0.0)
+    d = np.abs(np.where(mask, 2.0 * (z - tn), 0.0)) / mask.sum()
+    mags = []
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        Wf = bf16(W) if round_weights else W
+        mags.append(((d.T @ np.abs(hs[l])), d.sum(axis=0)))
+        if l > 0:
+            d = (d @ np.abs(Wf)) * np.abs(gelu_grad(pres[l - 1]))
+    mags.reverse()
+    return np.concatenate([np.concatenate([m.ravel(), mb]) for m, mb in mags])

@@ -635,6 +635,27 @@ struct FinArgs {
 };
 
 // Copy the solver state out: w, g = eps ln2 G2, t = Q^T 1 = 2^(G2 + LB2), per-problem stats.
+// Cold start of Algorithm 1 (reading A10: w0_j = sum(y) / (k x_j), x_j = sum_i D_ij; u1 = 1).
+// cold_colsum_kernel: thread j sums column j of D [n][k] (FP64 accumulation; consecutive threads
+// read consecutive atoms of a row); cold_weights_kernel: one CTA per problem.
+template <typename T>
+__global__ void cold_colsum_kernel(const T* D, int n, int k, T* xcol) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += (double)D[(size_t)i * k + j];
+  xcol[j] = (T)s;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) cold_weights_kernel(const T* y, const T* xcol, int n, int k, T* w0) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)y[(size_t)b * n + i];
+  s = block_sum(s, red);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) w0[(size_t)b * k + j] = (T)(s / ((double)k * (double)xcol[j]));
+}
+
 template <typename T>
 __global__ void finalize_kernel(FinArgs<T> A) {
   using P = Prec<T>;

@@ -280,5 +280,68 @@ __global__ void decode_kernel(const float* z, const float* mean, const float* st
   }
 }
 
+
+// ---- training data: targets of solved problems and their per-output normalisation ------------
+
+// Target row [g / eps (n), log w (k)] of a solved problem: g / eps is clipped below at g_floor
+// (far below any potential that matters: the prediction only seeds the iteration); a
+// non-finite g (u1 = 0 where y = 0 under the KL datafit) and w <= 0 give -inf, which the loss
+// masks out.
+__global__ void make_targets_kernel(const float* g, const float* wts, int rows, int n, int k, float inv_eps,
+                                    float g_floor, float* t) {
+  const int cols = n + k;
+  const size_t total = (size_t)rows * cols;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / cols), j = (int)(e % cols);
+    float v;
+    if (j < n) {
+      const float gv = g[(size_t)b * n + j];
+      v = isfinite(gv) ? fmaxf(gv * inv_eps, g_floor) : -CUDART_INF_F;
+    } else {
+      const float wv = wts[(size_t)b * k + (j - n)];
+      v = wv > 0.f ? logf(wv) : -CUDART_INF_F;
+    }
+    t[e] = v;
+  }
+}
+
+// Per-output mean and standard deviation over the finite entries of targets [rows][cols], in two
+// passes (sum and count, then squared deviations), FP64 partial sums per (row chunk, column) added
+// in a fixed order; std is floored at 1e-3.  Thread = column (coalesced across a row), blockIdx.y =
+// chunk of rows r = chunk, chunk + NORM_CHUNKS, ...
+constexpr int NORM_CHUNKS = 128;
+__global__ void norm_partial_kernel(const float* t, int rows, int cols, const float* mean, double* part,
+                                    int* cnt) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
+  if (c >= cols) return;
+  double s = 0.0;
+  int m = 0;
+  const float mu = mean ? mean[c] : 0.f;
+  for (int r = z; r < rows; r += NORM_CHUNKS) {
+    const float v = t[(size_t)r * cols + c];
+    if (isfinite(v)) {
+      const double d = mean ? (double)v - (double)mu : (double)v;
+      s += mean ? d * d : d;
+      ++m;
+    }
+  }
+  part[(size_t)z * cols + c] = s;
+  if (cnt) cnt[(size_t)z * cols + c] = m;
+}
+// pass 1 (std_out == null): mean = sum / count; pass 2: std = sqrt(sum of squares / count)
+__global__ void norm_finish_kernel(const double* part, const int* cnt, int cols, float* mean, float* std_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0.0;
+  long long m = 0;
+  for (int z = 0; z < NORM_CHUNKS; ++z) {
+    s += part[(size_t)z * cols + c];
+    m += cnt[(size_t)z * cols + c];
+  }
+  const double q = s / (double)(m > 0 ? m : 1);
+  if (!std_out) mean[c] = (float)q;
+  else std_out[c] = fmaxf((float)sqrt(q), 1e-3f);
+}
+
 }  // namespace mlp
 }  // namespace otlm

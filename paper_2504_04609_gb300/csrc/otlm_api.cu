@@ -123,16 +123,24 @@ int run_objective(otlm_ctx* h, const SolveParams& sp, const void* x, const void*
 }
 
 
-// Validate an uneven batch on host copies of n, k, eps and build the largest-work-first order.
-int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps, std::vector<int>* order) {
+// Validate an uneven batch on host copies of n, k, eps and the offsets, and build the
+// largest-work-first order.  The packed arrays hold sum n, sum n k and sum k elements (the
+// header's contract), so every problem's range must lie inside them; the kernel repeats the check
+// as a backstop.
+int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps, const long long* off_n,
+                 const long long* off_D, const long long* off_k, std::vector<int>* order) {
   const otlm_config& c = h->cfg;
   if (c.precision != OTLM_PREC_FP32_LOG) return OTLM_EUNSUPPORTED;
   if (batch < 1 || batch > c.batch_max || c.n_max > 4096) return OTLM_EINVAL;
   std::vector<int> hn(batch), hk(batch);
   std::vector<float> he(batch);
+  std::vector<long long> hon(batch), hoD(batch), hok(batch);
   if (cudaMemcpy(hn.data(), n, sizeof(int) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(hk.data(), k, sizeof(int) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(he.data(), eps, sizeof(float) * batch, cudaMemcpyDeviceToHost) != cudaSuccess)
+      cudaMemcpy(he.data(), eps, sizeof(float) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hon.data(), off_n, sizeof(long long) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hoD.data(), off_D, sizeof(long long) * batch, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hok.data(), off_k, sizeof(long long) * batch, cudaMemcpyDeviceToHost) != cudaSuccess)
     return OTLM_ECUDA;
   for (int p = 0; p < batch; ++p)
     if (hn[p] < 2 || hn[p] > c.n_max || hk[p] < 1 || hk[p] > c.k_max || !(he[p] > 0.f) || !std::isfinite(he[p]))
@@ -143,6 +151,10 @@ int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float
     tD += (long long)hn[p] * hk[p];
     tk += hk[p];
   }
+  for (int p = 0; p < batch; ++p)
+    if (hon[p] < 0 || hon[p] > tn - hn[p] || hoD[p] < 0 || hoD[p] > tD - (long long)hn[p] * hk[p] || hok[p] < 0 ||
+        hok[p] > tk - hk[p])
+      return OTLM_EINVAL;
   h->rg_tot[0] = tn; h->rg_tot[1] = tD; h->rg_tot[2] = tk;
   order->resize(batch);
   for (int p = 0; p < batch; ++p) (*order)[p] = p;
@@ -406,7 +418,7 @@ int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, cons
       (h->cfg.penalty == OTLM_PENALTY_L2SQ && !(alpha > 0)))
     return OTLM_EINVAL;
   std::vector<int> order;
-  int rc = ragged_setup(h, batch, n, k, eps, &order);
+  int rc = ragged_setup(h, batch, n, k, eps, off_n, off_D, off_k, &order);
   if (rc != OTLM_OK) return rc;
   if (cudaMemcpyAsync(h->rg_order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, h->stream) !=
       cudaSuccess)
@@ -425,17 +437,13 @@ int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const
   if (!h || !n || !k || !eps || !off_n || !off_D || !off_k || !x || !D || !y || !w || sample_every < 1 || iters < 1)
     return OTLM_EINVAL;
   std::vector<int> order;
-  int rc = ragged_setup(h, batch, n, k, eps, &order);
+  int rc = ragged_setup(h, batch, n, k, eps, off_n, off_D, off_k, &order);
   if (rc != OTLM_OK) return rc;
   // sample: every sample_every-th problem of the work order (so the sample spans the sizes)
   std::vector<int> sample;
   for (int i = 0; i < batch; i += sample_every) sample.push_back(order[i]);
-  long long last_k = 0;
-  int kk = 0;
-  if (cudaMemcpy(&last_k, off_k + (batch - 1), sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(&kk, k + (batch - 1), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return OTLM_ECUDA;
-  const size_t wn = (size_t)(last_k + kk);
+  // the weights' packed length sum k (the setup checked every problem's range against it)
+  const size_t wn = (size_t)h->rg_tot[2];
   float *wtmp = nullptr, *etmp = nullptr;
   int *itmp = nullptr, *stmp = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -479,6 +487,28 @@ int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const
   }
   if (cta_threads_out) *cta_threads_out = otlm::ragged_nt(best_v);
   return OTLM_OK;
+}
+
+int otlm_initial_weights(otlm_handle h, int batch, int n, int k, const void* D, const void* y, void* w_out) {
+  if (!h || !D || !y || !w_out) return OTLM_EINVAL;
+  const otlm_config& c = h->cfg;
+  if (batch < 1 || batch > c.batch_max || n < 2 || n > c.n_max || k < 1 || k > c.k_max) return OTLM_EINVAL;
+  Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
+  L.begin(otlm::KIND_OTHER);
+  if (c.precision == OTLM_PREC_FP64) {
+    Workspace<double> ws;
+    otlm::carve_workspace<double>(h->ws, c.n_max, c.k_max, c.batch_max, &ws);
+    otlm::cold_colsum_kernel<double><<<(k + 127) / 128, 128, 0, h->stream>>>((const double*)D, n, k, ws.xcol);
+    otlm::cold_weights_kernel<double><<<batch, 256, 0, h->stream>>>((const double*)y, ws.xcol, n, k, (double*)w_out);
+  } else {
+    Workspace<float> ws;
+    otlm::carve_workspace<float>(h->ws, c.n_max, c.k_max, c.batch_max, &ws);
+    otlm::cold_colsum_kernel<float><<<(k + 127) / 128, 128, 0, h->stream>>>((const float*)D, n, k, ws.xcol);
+    otlm::cold_weights_kernel<float><<<batch, 256, 0, h->stream>>>((const float*)y, ws.xcol, n, k, (float*)w_out);
+  }
+  L.end();
+  h->launches += 1;  // two kernels, one timed region
+  return cudaGetLastError() == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
 long long otlm_launch_count(otlm_handle h) { return h ? h->launches : -1; }

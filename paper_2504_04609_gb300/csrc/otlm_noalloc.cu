@@ -13,6 +13,7 @@
 // streams, two host threads) race on it.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -58,8 +59,9 @@ extern "C" int otlm_solve_noalloc(int batch, int n, int k, const float* x, const
   if (batch < 1 || n < 2 || k < 1 || k > 256 || max_iter < 1) return OTLM_EINVAL;
   if (datafit < OTLM_DATAFIT_BALANCED || datafit > OTLM_DATAFIT_POISSON) return OTLM_EINVAL;
   if (penalty < OTLM_PENALTY_NONE || penalty > OTLM_PENALTY_L2SQ) return OTLM_EINVAL;
-  if (!(eps > 0) || !(alpha >= 0) || !(tol == tol)) return OTLM_EINVAL;
-  if (datafit != OTLM_DATAFIT_BALANCED && !(lam > 0)) return OTLM_EINVAL;
+  if (!(eps > 0) || !std::isfinite(eps) || !(alpha >= 0) || !std::isfinite(alpha) || !std::isfinite(tol))
+    return OTLM_EINVAL;
+  if (datafit != OTLM_DATAFIT_BALANCED && (!(lam > 0) || !std::isfinite(lam))) return OTLM_EINVAL;
   if (penalty == OTLM_PENALTY_L2SQ && !(alpha > 0)) return OTLM_EINVAL;
   // the workspace this problem needs, laid out exactly as a handle's workspace
   if ((size_t)batch * (size_t)n > kScratchBytes) return OTLM_ESCRATCH;

@@ -36,7 +36,10 @@ struct otlm_ws_ctx {
   __nv_bfloat16 *Hhi[2] = {}, *Hlo[2] = {};
   float* Zs = nullptr;             // [TC_MAX_SPLITS][batch_max][dmax]
   int* tc_err = nullptr;
-  bool tc_dirty = true;            // W16p is stale (weights changed since the last refresh)
+  bool tc_dirty = true;
+  // per-output normalisation statistics: FP64 partial sums and counts per (row chunk, output)
+  double* norm_part = nullptr;
+  int* norm_cnt = nullptr;            // W16p is stale (weights changed since the last refresh)
 };
 
 namespace {
@@ -159,6 +162,7 @@ int otlm_ws_create(otlm_ws* out, int n, int k, int width, int batch_max, unsigne
   }
   bytes += w16b + align256(2 * zero_elems) + 4 * align256(2 * (size_t)batch_max * maxp) +
            align256(4 * (size_t)TC_MAX_SPLITS * batch_max * w->dmax) + 256;
+  bytes += align256(8 * (size_t)NORM_CHUNKS * (n + k)) + align256(4 * (size_t)NORM_CHUNKS * (n + k));
   if (cudaMalloc(&w->mem, bytes) != cudaSuccess) {
     delete w;
     return OTLM_ENOMEM;
@@ -186,6 +190,8 @@ int otlm_ws_create(otlm_ws* out, int n, int k, int width, int batch_max, unsigne
   }
   w->Zs = (float*)take(4 * (size_t)TC_MAX_SPLITS * batch_max * w->dmax);
   w->tc_err = (int*)take(256);
+  w->norm_part = (double*)take(8 * (size_t)NORM_CHUNKS * (n + k));
+  w->norm_cnt = (int*)take(4 * (size_t)NORM_CHUNKS * (n + k));
   cudaStream_t s = w->stream;
   // the zero lo part of the weights, and zero padding columns of the weights and activations
   // (never read past the tensor maps' extents, cleared all the same)
@@ -279,6 +285,31 @@ int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const floa
   decode_kernel<<<1184, 256, 0, w->stream>>>(w->act[LAYERS], w->mean, w->stdv, batch, w->n, w->k, (float)eps, cold_w,
                                              g0, w0, w->tc_err);
   return cudaGetLastError() == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
+}
+
+int otlm_ws_make_targets(otlm_ws w, int batch, const float* g, const float* wts, double eps, double g_floor,
+                         float* targets) {
+  if (!w || !g || !wts || !targets || batch < 1 || !(eps > 0) || !std::isfinite(eps) || !(g_floor == g_floor))
+    return OTLM_EINVAL;
+  make_targets_kernel<<<1184, 256, 0, w->stream>>>(g, wts, batch, w->n, w->k, (float)(1.0 / eps), (float)g_floor,
+                                                   targets);
+  return cudaGetLastError() == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
+}
+
+int otlm_ws_fit_normalization(otlm_ws w, int rows, const float* targets, float* mean_out, float* std_out) {
+  if (!w || !targets || rows < 1) return OTLM_EINVAL;
+  const int cols = w->n + w->k;
+  const dim3 grid((cols + 255) / 256, NORM_CHUNKS);
+  cudaStream_t s = w->stream;
+  norm_partial_kernel<<<grid, 256, 0, s>>>(targets, rows, cols, nullptr, w->norm_part, w->norm_cnt);
+  norm_finish_kernel<<<(cols + 255) / 256, 256, 0, s>>>(w->norm_part, w->norm_cnt, cols, w->mean, nullptr);
+  norm_partial_kernel<<<grid, 256, 0, s>>>(targets, rows, cols, w->mean, w->norm_part, nullptr);
+  norm_finish_kernel<<<(cols + 255) / 256, 256, 0, s>>>(w->norm_part, w->norm_cnt, cols, w->mean, w->stdv);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && mean_out)
+    e = cudaMemcpyAsync(mean_out, w->mean, 4 * (size_t)cols, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && std_out) e = cudaMemcpyAsync(std_out, w->stdv, 4 * (size_t)cols, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
 }  // extern "C"

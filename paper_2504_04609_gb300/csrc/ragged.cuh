@@ -357,7 +357,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ragged_kernel(RaggedArg
     else if (RMAX >= 4 && rows <= 4) ragged_solve_one<NT, (RMAX >= 4 ? 4 : 2)>(A, p, sm);
     else if (RMAX >= 8 && rows <= 8) ragged_solve_one<NT, (RMAX >= 8 ? 8 : 2)>(A, p, sm);
     else if (RMAX >= 16 && rows <= 16) ragged_solve_one<NT, (RMAX >= 16 ? 16 : 2)>(A, p, sm);
-    else if (RMAX >= 32) ragged_solve_one<NT, (RMAX >= 32 ? 32 : 2)>(A, p, sm);
+    else if (RMAX >= 32 && rows <= 32) ragged_solve_one<NT, (RMAX >= 32 ? 32 : 2)>(A, p, sm);
+    else if (threadIdx.x == 0) {  // more rows per thread than this CTA size supports
+      A.iters[p] = 0;
+      A.err[p] = CUDART_NAN_F;
+      A.status[p] = ST_INVALID;
+    }
   }
 }
 

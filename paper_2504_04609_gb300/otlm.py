@@ -25,7 +25,7 @@ EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm
            "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged", "otlm_solve_banded",
            "otlm_tune_ragged", "otlm_ws_create", "otlm_ws_destroy", "otlm_ws_num_params", "otlm_ws_set_normalization",
            "otlm_ws_get_params", "otlm_ws_set_params", "otlm_ws_gradients", "otlm_ws_train_step", "otlm_ws_predict",
-           "otlm_strerror")
+           "otlm_ws_make_targets", "otlm_ws_fit_normalization", "otlm_initial_weights", "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 
 
@@ -93,6 +93,12 @@ def lib() -> ctypes.CDLL:
         L.otlm_ws_train_step.restype = i
         L.otlm_ws_predict.argtypes = [vp, i, vp, d, vp, vp, vp]
         L.otlm_ws_predict.restype = i
+        L.otlm_ws_make_targets.argtypes = [vp, i, vp, vp, d, d, vp]
+        L.otlm_ws_make_targets.restype = i
+        L.otlm_ws_fit_normalization.argtypes = [vp, i, vp, vp, vp]
+        L.otlm_ws_fit_normalization.restype = i
+        L.otlm_initial_weights.argtypes = [vp, i, i, i, vp, vp, vp]
+        L.otlm_initial_weights.restype = i
         L.otlm_strerror.argtypes = [i]
         L.otlm_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -223,6 +229,12 @@ class Handle:
         _check(rc, "otlm_tune_ragged")
         return out.value
 
+    def initial_weights(self, D, y, w_out):
+        """otlm_initial_weights: the cold-start weights sum(y) / (k x_j) into w_out [B, k]."""
+        B, n = y.shape
+        k = D.shape[1]
+        _check(lib().otlm_initial_weights(self._h, B, n, k, _ptr(D), _ptr(y), _ptr(w_out)), "otlm_initial_weights")
+
     def objective(self, x, D, y, eps, lam, alpha, w, g, primal, dual):
         B, n = y.shape
         k = D.shape[1]
@@ -333,6 +345,14 @@ class WarmStart:
     def train_step(self, y, target, lr, weight_decay=0.0, loss_out=None):
         _check(lib().otlm_ws_train_step(self._w, y.shape[0], _ptr(y), _ptr(target), lr, weight_decay,
                                         _ptr(loss_out)), "otlm_ws_train_step")
+
+    def make_targets(self, g, w, eps, g_floor, targets):
+        _check(lib().otlm_ws_make_targets(self._w, g.shape[0], _ptr(g), _ptr(w), eps, g_floor, _ptr(targets)),
+               "otlm_ws_make_targets")
+
+    def fit_normalization(self, targets, mean_out=None, std_out=None):
+        _check(lib().otlm_ws_fit_normalization(self._w, targets.shape[0], _ptr(targets), _ptr(mean_out),
+                                               _ptr(std_out)), "otlm_ws_fit_normalization")
 
     def predict(self, y, eps, cold_w, g0, w0):
         _check(lib().otlm_ws_predict(self._w, y.shape[0], _ptr(y), eps, _ptr(cold_w), _ptr(g0), _ptr(w0)),

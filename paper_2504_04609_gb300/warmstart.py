@@ -14,18 +14,23 @@ import time
 
 import numpy as np
 
-import spectra
-
 from . import otlm as api
 
 # float32 tensors on the device; the caller owns torch
 G_FLOOR = -200.0  # g / eps labels below this are clipped (bins with y = 0 carry -inf; masked)
 
 
-def cold_weights(y, D):
-    """The cold-start weights w0_j = sum(y) / (k x_j) on the device (torch ops on device tensors)."""
+def cold_weights(y, D, chunk=4096, stream=None):
+    """The cold-start weights w0_j = sum(y) / (k x_j) on the device (otlm_initial_weights)."""
+    import torch
+    B, n = y.shape
     k = D.shape[1]
-    return (y.sum(dim=1, keepdim=True) / (k * D.sum(dim=0, keepdim=True))).contiguous()
+    w0 = torch.empty(B, k, dtype=y.dtype, device=y.device)
+    h = api.Handle(n, k, min(B, chunk), "fp64" if y.dtype == torch.float64 else "fp32", stream=stream)
+    for s in range(0, B, chunk):
+        h.initial_weights(D, y[s:s + chunk], w0[s:s + chunk])
+    h.close()
+    return w0
 
 
 def solve(x, D, y, cfg, w0, g0=None, tol=None, stream=None, precision="fp32"):
@@ -50,30 +55,29 @@ def solve(x, D, y, cfg, w0, g0=None, tol=None, stream=None, precision="fp32"):
     return w, g, t, it, err, st, secs
 
 
-def make_labels(x, D, y, cfg, chunk=4096):
-    """Targets [B][n + k] = [g / eps, log w] of the cold-start solutions (solved in chunks)."""
+def make_labels(net, x, D, y, cfg, chunk=4096):
+    """Targets [B][n + k] = [g / eps, log w] of the cold-start solutions (solved in chunks; the
+    transform runs in otlm_ws_make_targets)."""
     import torch
-    out = []
-    for s in range(0, y.shape[0], chunk):
+    B, n = y.shape
+    k = D.shape[1]
+    out = torch.empty(B, n + k, dtype=torch.float32, device=y.device)
+    for s in range(0, B, chunk):
         yb = y[s:s + chunk]
         w, g, _, _, _, st, _ = solve(x, D, yb, cfg, cold_weights(yb, D))
-        ge = torch.clamp(g / cfg["eps"], min=G_FLOOR)
-        ge = torch.where(torch.isfinite(g), ge, torch.full_like(ge, float("-inf")))
-        lw = torch.log(w)
-        lw = torch.where(w > 0, lw, torch.full_like(lw, float("-inf")))
-        out.append(torch.cat([ge, lw], dim=1))
-    return torch.cat(out, dim=0).contiguous()
+        net.make_targets(g, w, cfg["eps"], G_FLOOR, out[s:s + chunk])
+    return out
 
 
-def normalization(targets):
-    """Per-output mean and std over the finite entries (std floored at 1e-3)."""
+def normalization(net, targets):
+    """Per-output mean and std over the finite entries (std floored at 1e-3), fitted on the device
+    (otlm_ws_fit_normalization) and set on the network; returns (mean, std) device tensors."""
     import torch
-    fin = torch.isfinite(targets)
-    t0 = torch.where(fin, targets, torch.zeros_like(targets))
-    cnt = fin.sum(dim=0).clamp(min=1).float()
-    mean = t0.sum(dim=0) / cnt
-    var = (torch.where(fin, targets - mean, torch.zeros_like(targets)) ** 2).sum(dim=0) / cnt
-    return mean.contiguous(), torch.sqrt(var).clamp(min=1e-3).contiguous()
+    cols = targets.shape[1]
+    mean = torch.empty(cols, dtype=torch.float32, device=targets.device)
+    std = torch.empty_like(mean)
+    net.fit_normalization(targets, mean, std)
+    return mean, std
 
 
 def train(net, y, targets, epochs, batch, lr, weight_decay=0.0, seed=0, log_every=0):
@@ -103,13 +107,15 @@ def train(net, y, targets, epochs, batch, lr, weight_decay=0.0, seed=0, log_ever
     return losses
 
 
-def predict(net, y, D, eps, chunk=None):
+def predict(net, y, D, eps, chunk=None, cold_w=None):
+    """The network's initial state (g0, w0) for y; rows whose prediction is not finite take the
+    cold start (cold_w, computed here when not given)."""
     import torch
     B, n = y.shape
     k = D.shape[1]
     g0 = torch.empty_like(y)
     w0 = torch.empty(B, k, device=y.device)
-    cw = cold_weights(y, D)
+    cw = cold_weights(y, D) if cold_w is None else cold_w
     chunk = chunk or net.batch_max
     for s in range(0, B, chunk):
         net.predict(y[s:s + chunk], eps, cw[s:s + chunk], g0[s:s + chunk], w0[s:s + chunk])
@@ -123,7 +129,7 @@ def evaluate(net, x, D, y, cfg, precision="fp32"):
     wc, gc, tc, itc, _, stc, sc = solve(x, D, y, cfg, cw, precision=precision)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g0, w0 = predict(net, y, D, cfg["eps"])
+    g0, w0 = predict(net, y, D, cfg["eps"], cold_w=cw)
     torch.cuda.synchronize()
     t_pred = time.perf_counter() - t0
     ww, gw, tw, itw, _, stw, sw = solve(x, D, y, cfg, w0, g0, precision=precision)

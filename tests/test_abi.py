@@ -76,3 +76,16 @@ def test_banded_entry_point_rejects_a_null_handle():
     rc = api.lib().otlm_solve_banded(None, 1, 64, 3, 1, 4, 8, 1, 1, 1, 1, 1e-2, 1.0, 1e-3, 1, None, None, None, None,
                                      None)
     assert rc == api.OTLM_EINVAL
+
+
+@pytest.mark.parametrize("eps,lam,alpha,tol", [(float("inf"), 1.0, 1e-3, 0.0), (1e-2, float("inf"), 1e-3, 0.0),
+                                               (1e-2, 1.0, float("inf"), 0.0), (float("nan"), 1.0, 1e-3, 0.0),
+                                               (1e-2, 1.0, 1e-3, float("inf")), (1e-2, 1.0, -1e-3, 0.0)])
+def test_noalloc_rejects_non_finite_scalars_without_gpu(eps, lam, alpha, tol):
+    """otlm_solve_noalloc refuses the scalars otlm_solve refuses, before any CUDA call (the
+    pointers are dummies that are never dereferenced)."""
+    _ensure_built()
+    dummy = ctypes.c_void_p(1)
+    rc = api.lib().otlm_solve_noalloc(4, 64, 8, dummy, dummy, dummy, eps, lam, alpha, 1, 2, 10, tol, dummy,
+                                      None, None, None, None, None, None)
+    assert rc == api.OTLM_EINVAL

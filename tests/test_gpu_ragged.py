@@ -123,3 +123,60 @@ def test_ragged_graph_replay_is_deterministic():
     for w_, t_ in res[1:]:
         np.testing.assert_array_equal(w_, res[0][0])
         np.testing.assert_array_equal(t_, res[0][1])
+
+
+def _packed(problems, storage_order):
+    """A RaggedBatch whose problems are stored in `storage_order` (problem indices stay 0..B-1):
+    the offsets of problem p point at its place in that order, so they need not ascend."""
+    B = len(problems)
+    n = np.array([p["n"] for p in problems], np.int64)
+    k = np.array([p["k"] for p in problems], np.int64)
+    off_n, off_D, off_k = np.zeros(B, np.int64), np.zeros(B, np.int64), np.zeros(B, np.int64)
+    on = oD = ok = 0
+    for p in storage_order:
+        off_n[p], off_D[p], off_k[p] = on, oD, ok
+        on += n[p]
+        oD += n[p] * k[p]
+        ok += k[p]
+    cat = lambda key: np.concatenate([np.asarray(problems[p][key], np.float32).ravel() for p in storage_order])  # noqa
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")  # noqa: E731
+    w0 = np.concatenate([spectra.initial_weights(problems[p]["y"], problems[p]["D"]) for p in storage_order])
+    return (api.RaggedBatch(B, t(n.astype(np.int32)), t(k.astype(np.int32)),
+                            t(np.array([p["eps"] for p in problems], np.float32)), t(off_n), t(off_D), t(off_k),
+                            t(cat("x")), t(cat("D")), t(cat("y"))), w0.astype(np.float32))
+
+
+def test_ragged_offsets_in_any_order_and_out_of_range_offsets():
+    """Problems packed in reverse order (offsets descending) give the same results as the ascending
+    packing, through the tuner (whose temporary weights span sum k) and the solve; an offset range
+    that leaves the packed arrays is refused before any work is queued."""
+    probs = spectra.ragged(46, 7, n_range=(256, 600), k_range=(8, 40))
+    B = len(probs)
+    res = []
+    for order in (list(range(B)), list(range(B))[::-1]):
+        rb, w0 = _packed(probs, order)
+        h = api.Handle(600, 40, B, "fp32", "tv", "l1", 10, 0.0, stream=torch.cuda.current_stream().cuda_stream)
+        w = torch.tensor(w0, device="cuda")
+        assert h.tune_ragged(rb, 1.0, 1e-2, w, sample_every=2, iters=2) in (128, 256, 512)
+        t = torch.empty_like(rb.y)
+        it = torch.empty(B, dtype=torch.int32, device="cuda")
+        err = torch.empty(B, device="cuda")
+        st = torch.empty(B, dtype=torch.int32, device="cuda")
+        h.solve_ragged(rb, 1.0, 1e-2, w, None, t, it, err, st)
+        torch.cuda.synchronize()
+        on, ok = rb.off_n.cpu().numpy(), rb.off_k.cpu().numpy()
+        wn, tn = w.cpu().numpy(), t.cpu().numpy()
+        res.append([(wn[ok[p]:ok[p] + probs[p]["k"]], tn[on[p]:on[p] + probs[p]["n"]]) for p in range(B)])
+        assert np.all(st.cpu().numpy() == api.MAX_ITER)
+        if order[0] != 0:  # reversed packing: push one problem's weights past sum k
+            bad = rb.off_k.clone()
+            bad[0] = int(sum(p["k"] for p in probs)) - probs[0]["k"] + 1
+            rb_bad = api.RaggedBatch(rb.batch, rb.n, rb.k, rb.eps, rb.off_n, rb.off_D, bad, rb.x, rb.D, rb.y)
+            with pytest.raises(api.OTLMError):
+                h.solve_ragged(rb_bad, 1.0, 1e-2, w, None, t, it, err, st)
+            with pytest.raises(api.OTLMError):
+                h.tune_ragged(rb_bad, 1.0, 1e-2, w, sample_every=2, iters=2)
+        h.close()
+    for p in range(B):
+        np.testing.assert_array_equal(res[0][p][0], res[1][p][0])
+        np.testing.assert_array_equal(res[0][p][1], res[1][p][1])

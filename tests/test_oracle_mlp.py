@@ -35,3 +35,29 @@ def test_backward_matches_finite_differences():
                  - mlp.loss_and_grad(params - e, dims, y, t, mean, std, False)[0]) / (2 * h)
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
     assert loss > 0
+
+
+def test_gradient_magnitudes_bound_the_gradient():
+    """grad_magnitudes sums |terms| of the same chain rule, so it bounds |gradient| entry by entry
+    (triangle inequality) and equals it when every factor is non-negative (here: positive weights,
+    positive residuals, no GELU layers in play: a one-layer check through the output layer)."""
+    rng = np.random.default_rng(3)
+    n, k, H, B = 6, 2, 5, 4
+    dims = mlp.layer_dims(n, k, H)
+    P = sum(dims[l] * dims[l + 1] + dims[l + 1] for l in range(4))
+    params = rng.normal(0, 0.4, P)
+    y = rng.uniform(0.01, 1.0, (B, n))
+    t = rng.normal(0, 1, (B, n + k))
+    t[1, 2] = -np.inf
+    mean, std = np.zeros(n + k), np.ones(n + k)
+    _, g = mlp.loss_and_grad(params, dims, y, t, mean, std, round_weights=False)
+    M = mlp.grad_magnitudes(params, dims, y, t, mean, std, round_weights=False)
+    assert np.all(np.abs(g) <= M * (1 + 1e-12) + 1e-300)
+    # output-layer bias gradient: sum_b 2 r_bj / cnt; with every residual of a column of one sign
+    # the magnitude equals |gradient|
+    z, _, _ = mlp.forward(params, dims, y, round_weights=False)
+    t2 = z - 1.0  # residual z - t = +1 everywhere
+    _, g2 = mlp.loss_and_grad(params, dims, y, t2, mean, std, round_weights=False)
+    M2 = mlp.grad_magnitudes(params, dims, y, t2, mean, std, round_weights=False)
+    nb = dims[4]
+    np.testing.assert_allclose(g2[-nb:], M2[-nb:], rtol=1e-12)
