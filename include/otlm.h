@@ -62,7 +62,7 @@ typedef enum {            /* marginal datafit L(. | y), Table 1 */
   OTLM_DATAFIT_POISSON  = 4   /* lam sum (s - y log s): prox = (lam y/eps) / W0((lam y/(eps s))
                                  e^{lam/eps}), s e^{-lam/eps} where y = 0 (Table 1's last row; its
                                  "W0^{-1}" read as 1/W0, re-derived from the stationarity
-                                 condition of App. B); not accepted by otlm_objective */
+                                 condition of App. B) */
 } otlm_datafit;
 
 typedef enum {            /* weight penalty R(w), Table 2 */
@@ -82,7 +82,8 @@ typedef enum {
                                  per-problem max shift; potentials and updates in FP32.  Element
                                  type float.  Rows whose sum underflows (all significant terms
                                  below 2^-126 of the problem's largest) are recomputed exactly in
-                                 the log domain.  otlm_objective on such a handle runs FP32 applies. */
+                                 the log domain.  otlm_objective on such a handle runs FP32 applies
+                                 (the in-solve objective of check_every runs tensor-core ones). */
 } otlm_precision;
 
 typedef struct otlm_config {
@@ -101,6 +102,21 @@ typedef struct otlm_config {
   int    mm_steps;     /* MM steps of the weight update per iteration, all with the same
                           a = K u1 (Sec. 4.2: Algorithm 1 takes one; more approach
                           prox_{alpha P}(K u1 | X)); 0 or 1 = one step, at most 64             */
+  /* Further stopping criteria (Algorithm 1 leaves "converged" open; reading: every enabled
+   * criterion must hold at the same iteration, tol's violation test being the first).  Fields
+   * added after mm_steps; zero-initialise the struct to leave them off. */
+  int    check_every;  /* >= 0.  > 0: every this many iterations, and for every problem at the end,
+                          the FP64 primal and dual of the state the solve would return (Eq. OTLM and
+                          its Fenchel dual, as otlm_objective) are reduced on the GPU, with one extra
+                          kernel apply per check in the handle's own arithmetic (tensor cores on a
+                          BF16 handle); read them with otlm_solve_stats.  0: never (no extra memory
+                          or work).  otlm_solve, otlm_solve_cost, otlm_solve_host only.          */
+  double gap_tol;      /* >= 0, finite.  > 0 (needs check_every > 0): a problem stops only at a check
+                          where primal - dual <= gap_tol |primal|                               */
+  double dw_tol;       /* >= 0, finite.  > 0: a problem stops only where the last weight update's
+                          ||w_new - w_old||_1 / ||w_new||_1 <= dw_tol (the weights converge far more
+                          slowly than the marginals: reading A8).  otlm_solve, otlm_solve_cost,
+                          otlm_solve_host only.                                                  */
 } otlm_config;
 
 typedef struct otlm_ctx* otlm_handle;
@@ -108,9 +124,12 @@ typedef struct otlm_ctx* otlm_handle;
 /* Create a handle and its device workspace (about (8 n_max + 2 k_max + 16) * batch_max
  * elements).  `cuda_stream` is a cudaStream_t (NULL = default stream).  The workspace is
  * owned by the handle and released by otlm_destroy.
+ * With check_every > 0 the workspace also holds the objective scratch (3 batch_max n_max elements
+ * and 20 batch_max bytes).
  * Errors: OTLM_EINVAL (null pointers, sizes out of range, unknown enum, ELASTIC without a
- * finite beta > 0, mm_steps outside 0..64), OTLM_ENOMEM,
- * OTLM_ECUDA.  On error *h is set to NULL. */
+ * finite beta > 0, mm_steps outside 0..64, check_every < 0, gap_tol or dw_tol negative or not
+ * finite, gap_tol > 0 with check_every == 0), OTLM_ENOMEM, OTLM_ECUDA.  On error *h is set to
+ * NULL. */
 int otlm_create(otlm_handle* h, const otlm_config* cfg, void* cuda_stream);
 
 /* Release the workspace.  Waits for the handle's stream.  NULL is ignored. */
@@ -132,7 +151,9 @@ void otlm_destroy(otlm_handle h);
  *   err_out    [batch]  last measured violation e (device; float for an FP32 handle, double
  *                       for FP64; may be NULL)
  *   status_out [batch]  OTLM_CONVERGED / OTLM_MAX_ITER / OTLM_NONFINITE (device int32, may be NULL)
- * Problems stop independently; finished problems drop out of the remaining launches.
+ * Problems stop independently (once every enabled criterion holds: e <= tol, and the weight change
+ * and the FP64 gap when dw_tol / gap_tol are set); finished problems drop out of the remaining
+ * launches.
  * Errors: OTLM_EINVAL (batch/n/k beyond the handle, n < 2, k < 1, eps <= 0, lam <= 0 for a
  * soft datafit, alpha < 0, alpha == 0 with L2SQ, a NULL required pointer), OTLM_ECUDA. */
 int otlm_solve(otlm_handle h, int batch, int n, int k,
@@ -272,6 +293,18 @@ int otlm_ws_fit_normalization(otlm_ws w, int rows, const float* targets, float* 
 int otlm_ws_predict(otlm_ws w, int batch, const float* y, double eps, const float* cold_w, float* g0,
                     float* w0);
 
+/* Per-problem diagnostics of the handle's last otlm_solve / otlm_solve_cost / otlm_solve_host call
+ * (the paper has no counterpart; they support the stopping criteria of reading A8):
+ *   dw_out [batch]      ||w_new - w_old||_1 / ||w_new||_1 of each problem's last weight update
+ *                       (element type of the handle; NaN if it made none); may be NULL
+ *   primal_out, dual_out [batch]  FP64 primal and Fenchel dual of the returned state (w, g), as
+ *                       otlm_objective defines them, computed at the end of the solve; need a
+ *                       handle created with check_every > 0; may be NULL
+ * Device pointers; asynchronous on the handle's stream; batch must not exceed the last solve's.
+ * Errors: OTLM_EINVAL (NULL handle, batch out of range, primal/dual asked of a handle with
+ * check_every == 0), OTLM_ECUDA. */
+int otlm_solve_stats(otlm_handle h, int batch, void* dw_out, double* primal_out, double* dual_out);
+
 /* Cold start of Algorithm 1 on the device: w_out [batch][k] = sum_i y_pi / (k x_j), x_j = sum_i D_ij
  * (Algorithm 1 leaves the initial w open; this reading spreads the target's mass evenly over the
  * atoms; the matching initial potential is u1 = 1, i.e. g = NULL in otlm_solve).  D [n][k] and
@@ -288,9 +321,11 @@ int otlm_initial_weights(otlm_handle h, int batch, int n, int k, const void* D, 
  * at g' = the datafit step from K^T e^{f/eps} and f' = f shifted by the smallest constant that
  * makes it dual-feasible (l1 / no penalty), so dual_out <= optimum <= primal_out and
  * primal_out - dual_out is a duality gap.  BALANCED datafit: primal_out is +inf unless Q^T 1 = y.
- * The two kernel applies run in the handle's arithmetic; all sums are FP64.
+ * POISSON: the dual takes g' = lam y / v' - lam (v' the prox value, -lam where y = 0), the datafit
+ * step written so that lam + g' keeps its precision.
+ * The two kernel applies run in FP32 (FP32 and BF16 handles) or FP64; all sums are FP64.
  *   w [batch][k], g [batch][n] as returned by otlm_solve; primal_out, dual_out [batch] device
- *   doubles.  Errors as otlm_solve, plus OTLM_EUNSUPPORTED for the Poisson datafit. */
+ *   doubles.  Errors as otlm_solve. */
 int otlm_objective(otlm_handle h, int batch, int n, int k,
                    const void* x, const void* D, const void* y,
                    double eps, double lam, double alpha,

@@ -23,7 +23,9 @@ Readings of passages the paper leaves garbled or open:
       solves u e^u = (lam y / (eps b)) e^{lam / eps} and v = (lam y / eps) / W0(...): Table 1's
       "W0^{-1}" is read as the reciprocal 1 / W0.  For y = 0 the prox is b e^{-lam / eps}.
   A8  "not converged" (Algorithm 1): source-marginal violation
-      e = ||u2 * (K u1) - X w||_1 / ||X w||_1, measured with the u1 of the next iteration.
+      e = ||u2 * (K u1) - X w||_1 / ||X w||_1, measured with the u1 of the next iteration; the
+      weight change ||w_new - w_old||_1 / ||w_new||_1 and the duality gap of the current state
+      are reported beside it and may be required as well (every enabled criterion must hold).
   A6  Table 2, elastic net alpha l1 + (beta/2) l2^2: Table 2 prints the prefactor alpha/beta and a
       y_j inside the sum; App. A's stationarity condition ln w_j + gamma_j w_j = nu_j with
       gamma_j = beta/(eps x_j) and nu_j shifted by -alpha/(eps x_j) is followed instead:
@@ -315,13 +317,21 @@ def _log_datafit_potential(datafit, log_b, y, eps, lam):
     raise ValueError(datafit)
 
 
-def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g0=None, beta=0.0, mm_steps=1):
+def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g0=None, beta=0.0, mm_steps=1,
+              dw_tol=0.0, check_every=0, gap_tol=0.0):
     """Algorithm 1 with the scalings carried as potentials g = eps log u1, f = eps log u2.
 
     log (K u1)_i = LSE_j((g_j - C_ij)/eps), log (K^T u2)_j = LSE_i((f_i - C_ij)/eps); the MM step
     is `mm_step_log`; f = eps (log X w - log K u1) (-inf where X w = 0); g from
     `_log_datafit_potential`.  Same stopping rule, `beta`, `mm_steps` and outputs as `solve`, plus
-    f, g, log_a.
+    f, g, log_a and dw_hist (||w_new - w_old||_1 / ||w_new||_1 of every weight update).
+
+    Further stopping criteria (reading A8 reports the weight change and the duality gap beside the
+    violation; here they may also be required): with dw_tol > 0 a stop also needs the last update's
+    weight change <= dw_tol; with gap_tol > 0 it needs, at an iteration that is a multiple of
+    check_every, primal - dual <= gap_tol |primal| for the state (w, g) it would return
+    (`objective_and_dual`).  Every enabled criterion must hold at the same iteration; gap_hist
+    lists (iteration, primal, dual) of the checks.
     """
     C = np.asarray(C, dtype=np.float64)
     X = np.asarray(X, dtype=np.float64)
@@ -331,7 +341,8 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
     w = np.asarray(w0, dtype=np.float64).copy()
     s = None
     err = np.nan
-    hist = []
+    hist, dw_hist, gap_hist = [], [], []
+    any_rule = tol > 0 or dw_tol > 0 or gap_tol > 0
     it = 0
     log_a = None
     for it in range(n_iter + 1):
@@ -340,12 +351,21 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
             # u2 * K u1 = s * exp(log a_new - log a_old)
             err = float(np.sum(np.abs(s * np.expm1(log_a - log_a_old))) / np.sum(s))
             hist.append(err)
-            if tol > 0 and err <= tol:
+            gap_ok = True
+            if gap_tol > 0:
+                gap_ok = False
+                if check_every > 0 and it % check_every == 0:
+                    P, Dv, _ = objective_and_dual(w, g, C, X, y, eps, lam, alpha, datafit, penalty, beta)
+                    gap_hist.append((it, P, Dv))
+                    gap_ok = P - Dv <= gap_tol * abs(P)
+            if (any_rule and (tol <= 0 or err <= tol) and (dw_tol <= 0 or dw_hist[-1] <= dw_tol) and gap_ok):
                 break
         if it == n_iter:
             break
+        w_prev = w
         for _ in range(mm_steps):
             w = mm_step_log(penalty, log_a, w, X, eps, alpha, beta)
+        dw_hist.append(float(np.sum(np.abs(w - w_prev)) / np.sum(np.abs(w))))
         s = X @ w
         with np.errstate(divide="ignore"):
             f = eps * (np.log(s) - log_a)
@@ -356,8 +376,8 @@ def solve_log(C, X, y, eps, lam, alpha, datafit, penalty, w0, n_iter, tol=0.0, g
     with np.errstate(invalid="ignore"):
         logQ = (f[:, None] + g[None, :] - C) / eps
     Q = np.exp(logQ)
-    return dict(w=w, f=f, g=g, Q=Q, iters=it, err=err, err_hist=np.array(hist),
-                t=Q.sum(axis=0), s=Q.sum(axis=1), log_a=log_a)
+    return dict(w=w, f=f, g=g, Q=Q, iters=it, err=err, err_hist=np.array(hist), dw_hist=np.array(dw_hist),
+                gap_hist=gap_hist, t=Q.sum(axis=0), s=Q.sum(axis=1), log_a=log_a)
 
 
 def solve_converged(C, X, y, eps, lam, alpha, datafit, penalty, w0, rtol_w=1e-14, max_iter=10 ** 6, g0=None,

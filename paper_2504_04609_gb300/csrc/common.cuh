@@ -37,6 +37,7 @@ template <> struct Prec<float> {
   static __device__ __forceinline__ float expm1(float v) { return ::expm1f(v); }
   static __device__ __forceinline__ float log(float v) { return ::logf(v); }
   static __device__ __forceinline__ float ninf() { return -CUDART_INF_F; }
+  static __device__ __forceinline__ float nan() { return CUDART_NAN_F; }
   static __device__ __forceinline__ float tiny() { return 1.17549435e-38f; }  // smallest normal
   static constexpr int kOmegaIters = 3;
   static constexpr float kUnderflowZ = -80.f;  // omega(z) = e^z to working precision below this
@@ -49,6 +50,7 @@ template <> struct Prec<double> {
   static __device__ __forceinline__ double expm1(double v) { return ::expm1(v); }
   static __device__ __forceinline__ double log(double v) { return ::log(v); }
   static __device__ __forceinline__ double ninf() { return -CUDART_INF; }
+  static __device__ __forceinline__ double nan() { return CUDART_NAN; }
   static __device__ __forceinline__ double tiny() { return 4.9406564584124654e-324; }  // smallest subnormal
   static constexpr int kOmegaIters = 5;
   static constexpr double kUnderflowZ = -700.0;

@@ -406,11 +406,15 @@ struct MMArgs {
   T* mass;          // [P] sum_i S_i
   T* err_acc;       // [P] violation numerators (reset here)
   T* err;           // [P]
+  T* dw;            // [P] ||w_new - w_old||_1 / ||w_new||_1 of the iteration's MM update
+  const int* gap_ok;  // [P] relative duality gap <= gap_tol at this iteration's check
+  int gap_check;    // this iteration evaluated the gap (gap_ok is current)
   int* done;
   int* iters;
   int* status;
   int it, max_iter;
-  T tol;
+  T tol, dw_tol;
+  int gap_on;       // gap_tol > 0: the gap is a stopping criterion
   int penalty;
   int mm_steps = 1;  // MM steps with the same LA2 (a = K u1)
   T eps, alpha, beta;
@@ -437,6 +441,21 @@ __device__ __forceinline__ T source_marginal(const T* __restrict__ Dt, const T* 
   return block_sum(mass, red);
 }
 
+// The stopping test of Algorithm 1's "while not converged" (reading A8): the source-marginal
+// violation e <= tol, optionally together with the weight change ||dw||_1 / ||w||_1 <= dw_tol and a
+// relative FP64 duality gap <= gap_tol (taken at check iterations only).  Every enabled criterion
+// must hold; with none enabled the solve runs max_iter iterations.  Returns a status or -1.
+template <typename T>
+__device__ __forceinline__ int stop_decision(T e, T dw, T tol, T dw_tol, bool gap_on, bool gap_ok, int it,
+                                             int max_iter) {
+  if (e != e) return ST_NONFINITE;
+  const bool any = tol > T(0) || dw_tol > T(0) || gap_on;
+  if (any && (!(tol > T(0)) || e <= tol) && (!(dw_tol > T(0)) || dw <= dw_tol) && (!gap_on || gap_ok))
+    return ST_CONVERGED;
+  if (it >= max_iter) return ST_MAX_ITER;
+  return -1;
+}
+
 // Per active problem (one CTA of 256 threads): convergence decision for the previous iteration,
 // then Table 2's MM step  nu_j = log w_j + (ln2 / x_j) sum_i D_ij (LA2_i - log2 S_i)  (rows with
 // S_i = 0 dropped), the penalty update and S = D w, mm_steps times with the same LA2; the last
@@ -447,6 +466,7 @@ __global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
   constexpr int KP = KQ * 32;
   __shared__ T red_s[8][KP];
   __shared__ T w_s[KP];
+  __shared__ T w0_s[KP];
   __shared__ T red[32];
   __shared__ int stop;
   const int slot = blockIdx.x;
@@ -461,10 +481,8 @@ __global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
     if (threadIdx.x == 0) {
       const T e = A.err_acc[p] / A.mass[p];
       A.err[p] = e;
-      int st = -1;
-      if (e != e) st = ST_NONFINITE;
-      else if (A.tol > T(0) && e <= A.tol) st = ST_CONVERGED;
-      else if (A.it >= A.max_iter) st = ST_MAX_ITER;
+      const int st = stop_decision<T>(e, A.dw[p], A.tol, A.dw_tol, A.gap_on != 0,
+                                      A.gap_check && A.gap_ok && A.gap_ok[p], A.it, A.max_iter);
       if (st >= 0) {
         A.status[p] = st;
         A.iters[p] = A.it;
@@ -477,6 +495,7 @@ __global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
     if (stop) return;
   }
 
+  for (int j = threadIdx.x; j < k; j += blockDim.x) w0_s[j] = A.W[(size_t)p * k + j];
   for (int m = 0; m < A.mm_steps; ++m) {
     // phase A: Dt r, r_i = LA2_i - log2 S_i (log2 units), 32 rows per warp step
     T acc[KQ];
@@ -531,6 +550,15 @@ __global__ void __launch_bounds__(256) mm_kernel(MMArgs<T> A) {
     if (last && threadIdx.x == 0) A.mass[p] = mass;
     __syncthreads();
   }
+  // weight change of this iteration's update (all its MM steps): ||w - w_start||_1 / ||w||_1
+  T num = T(0), den = T(0);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    num += fabs(w_s[j] - w0_s[j]);
+    den += fabs(w_s[j]);
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
+  if (threadIdx.x == 0) A.dw[p] = num / den;
 }
 
 // S = D w0 and its mass for every problem of the batch (one CTA per problem).
@@ -583,6 +611,7 @@ struct PrepArgs {
   const T* x; const T* D; const T* w_in; const T* g_in; const T* y;
   T* xt; T* Dt; T* xcol; T* W; T* G2;
   int* active; int* done; int* n_active; T* err_acc; int* iters; int* status; T* err;
+  T* dw; int* all; int* all_count;
   int batch, n, k;
   T xscale;    // 1 / sqrt(eps ln2)
   T gscale;    // 1 / (eps ln2)
@@ -610,8 +639,13 @@ __global__ void prep_kernel(PrepArgs<T> A) {
     A.iters[e] = 0;
     A.status[e] = ST_MAX_ITER;
     A.err[e] = T(0);
+    A.dw[e] = Prec<T>::nan();
+    A.all[e] = (int)e;
   }
-  if (tid == 0) *A.n_active = A.batch;
+  if (tid == 0) {
+    *A.n_active = A.batch;
+    *A.all_count = A.batch;
+  }
 }
 
 // Column sums x_j of the dictionary (one warp per column).

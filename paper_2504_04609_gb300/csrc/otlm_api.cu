@@ -53,18 +53,32 @@ bool valid_enum(const otlm_config& c) {
          (c.datafit >= OTLM_DATAFIT_BALANCED && c.datafit <= OTLM_DATAFIT_POISSON) &&
          (c.penalty >= OTLM_PENALTY_NONE && c.penalty <= OTLM_PENALTY_ELASTIC) &&
          (c.penalty != OTLM_PENALTY_ELASTIC || (c.beta > 0 && std::isfinite(c.beta))) &&
-         c.mm_steps >= 0 && c.mm_steps <= 64;
+         c.mm_steps >= 0 && c.mm_steps <= 64 && c.check_every >= 0 && c.gap_tol >= 0 && std::isfinite(c.gap_tol) &&
+         c.dw_tol >= 0 && std::isfinite(c.dw_tol) && (c.gap_tol == 0 || c.check_every > 0);
 }
 
-size_t workspace_bytes(const otlm_config& c) {
-  if (c.precision == OTLM_PREC_FP64)
-    return otlm::carve_workspace<double>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
-  size_t bytes = otlm::carve_workspace<float>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
-  if (c.precision == OTLM_PREC_BF16_TC)
-    bytes += otlm::carve_tc_workspace(nullptr, c.n_max, c.k_max, c.batch_max, nullptr) +
-             otlm::carve_tc_mm(nullptr, c.k_max, c.batch_max, nullptr);
-  return bytes;
+// Byte offsets of the workspace parts: the solver state, then (tensor-core handles) the GEMM
+// operands and the MM partial sums, then (check_every > 0) the objective scratch.
+struct WsLayout {
+  size_t base = 0, tc = 0, mm = 0, obj = 0, total = 0;
+};
+WsLayout ws_layout(const otlm_config& c) {
+  WsLayout l;
+  const bool f64 = c.precision == OTLM_PREC_FP64;
+  l.base = f64 ? otlm::carve_workspace<double>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr)
+               : otlm::carve_workspace<float>(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
+  if (c.precision == OTLM_PREC_BF16_TC) {
+    l.tc = otlm::carve_tc_workspace(nullptr, c.n_max, c.k_max, c.batch_max, nullptr);
+    l.mm = otlm::carve_tc_mm(nullptr, c.k_max, c.batch_max, nullptr);
+  }
+  if (c.check_every > 0)
+    l.obj = f64 ? otlm::carve_obj_workspace<double>(nullptr, c.n_max, c.batch_max, nullptr)
+                : otlm::carve_obj_workspace<float>(nullptr, c.n_max, c.batch_max, nullptr);
+  l.total = l.base + l.tc + l.mm + l.obj;
+  return l;
 }
+
+size_t workspace_bytes(const otlm_config& c) { return ws_layout(c).total; }
 
 int check_problem(const otlm_ctx* h, int batch, int n, int k, double eps, double lam, double alpha) {
   const otlm_config& c = h->cfg;
@@ -82,6 +96,7 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
   sp.datafit = h->cfg.datafit; sp.penalty = h->cfg.penalty; sp.max_iter = h->cfg.max_iter;
   sp.poll_every = h->cfg.poll_every; sp.tol = h->cfg.tol;
   sp.beta = h->cfg.beta; sp.mm_steps = h->cfg.mm_steps > 1 ? h->cfg.mm_steps : 1;
+  sp.check_every = h->cfg.check_every; sp.gap_tol = h->cfg.gap_tol; sp.dw_tol = h->cfg.dw_tol;
   return sp;
 }
 
@@ -89,23 +104,27 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
 template <typename T>
 int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* C, const void* D, const void* y, void* w,
               void* g, void* t_out, int* iters_out, void* err_out, int* status_out) {
+  const otlm_config& c = h->cfg;
+  const WsLayout lay = ws_layout(c);
+  char* base = static_cast<char*>(h->ws);
   Workspace<T> ws;
-  otlm::carve_workspace<T>(h->ws, h->cfg.n_max, h->cfg.k_max, h->cfg.batch_max, &ws);
+  otlm::carve_workspace<T>(base, c.n_max, c.k_max, c.batch_max, &ws);
+  otlm::ObjWorkspace<T> ow;
+  if (lay.obj) otlm::carve_obj_workspace<T>(base + lay.base + lay.tc + lay.mm, c.n_max, c.batch_max, &ow);
   Launch L{h->stream, &h->launches, h->host_flag, &h->timer};
   cudaError_t e;
-  if (h->cfg.precision == OTLM_PREC_BF16_TC) {
+  if (c.precision == OTLM_PREC_BF16_TC) {
     otlm::TcWorkspace tw;
-    const size_t base = otlm::carve_workspace<float>(nullptr, h->cfg.n_max, h->cfg.k_max, h->cfg.batch_max, nullptr);
-    const size_t tcb = otlm::carve_tc_workspace(static_cast<char*>(h->ws) + base, h->cfg.n_max, h->cfg.k_max,
-                                                h->cfg.batch_max, &tw);
+    otlm::carve_tc_workspace(base + lay.base, c.n_max, c.k_max, c.batch_max, &tw);
     otlm::TcMMBuf mb;
-    otlm::carve_tc_mm(static_cast<char*>(h->ws) + base + tcb, h->cfg.k_max, h->cfg.batch_max, &mb);
-    e = otlm::solve_device_tc(L, reinterpret_cast<const Workspace<float>&>(ws), tw, mb, sp, (const float*)x,
-                              (const float*)C, (const float*)D, (const float*)y, (float*)w, (float*)g, (float*)t_out, iters_out,
-                              (float*)err_out, status_out);
+    otlm::carve_tc_mm(base + lay.base + lay.tc, c.k_max, c.batch_max, &mb);
+    e = otlm::solve_device_tc(L, reinterpret_cast<const Workspace<float>&>(ws), tw, mb,
+                              lay.obj ? reinterpret_cast<const otlm::ObjWorkspace<float>*>(&ow) : nullptr, sp,
+                              (const float*)x, (const float*)C, (const float*)D, (const float*)y, (float*)w,
+                              (float*)g, (float*)t_out, iters_out, (float*)err_out, status_out);
   } else {
-    e = otlm::solve_device<T>(L, ws, sp, (const T*)x, (const T*)D, (const T*)y, (T*)w, (T*)g, (T*)t_out, iters_out,
-                              (T*)err_out, status_out);
+    e = otlm::solve_device<T>(L, ws, lay.obj ? &ow : nullptr, sp, (const T*)x, (const T*)D, (const T*)y, (T*)w,
+                              (T*)g, (T*)t_out, iters_out, (T*)err_out, status_out);
   }
   if (e == cudaErrorLaunchTimeout) return OTLM_ETIMEOUT;
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
@@ -130,7 +149,7 @@ int run_objective(otlm_ctx* h, const SolveParams& sp, const void* x, const void*
 int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps, const long long* off_n,
                  const long long* off_D, const long long* off_k, std::vector<int>* order) {
   const otlm_config& c = h->cfg;
-  if (c.precision != OTLM_PREC_FP32_LOG) return OTLM_EUNSUPPORTED;
+  if (c.precision != OTLM_PREC_FP32_LOG || c.check_every > 0 || c.dw_tol > 0) return OTLM_EUNSUPPORTED;
   if (batch < 1 || batch > c.batch_max || c.n_max > 4096) return OTLM_EINVAL;
   std::vector<int> hn(batch), hk(batch);
   std::vector<float> he(batch);
@@ -368,7 +387,6 @@ int otlm_objective(otlm_handle h, int batch, int n, int k, const void* x, const 
   if (!h || !x || !D || !y || !w || !g || !primal_out || !dual_out) return OTLM_EINVAL;
   int rc = check_problem(h, batch, n, k, eps, lam, alpha);
   if (rc != OTLM_OK) return rc;
-  if (h->cfg.datafit == OTLM_DATAFIT_POISSON) return OTLM_EUNSUPPORTED;
   const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
   if (h->cfg.precision == OTLM_PREC_FP64) return run_objective<double>(h, sp, x, D, y, w, g, primal_out, dual_out);
   return run_objective<float>(h, sp, x, D, y, w, g, primal_out, dual_out);
@@ -378,7 +396,8 @@ int otlm_solve_banded(otlm_handle h, int batch, int n, int hw, const float* Cd, 
                       const int* row_idx, const float* val, const float* y, double eps, double lam, double alpha,
                       float* w, float* g, float* t_out, int* iters_out, float* err_out, int* status_out) {
   if (!h || !Cd || !col_ptr || !row_idx || !val || !y || !w) return OTLM_EINVAL;
-  if (h->cfg.precision != OTLM_PREC_FP32_LOG || h->cfg.mm_steps > 1) return OTLM_EUNSUPPORTED;
+  if (h->cfg.precision != OTLM_PREC_FP32_LOG || h->cfg.mm_steps > 1 || h->cfg.check_every > 0 || h->cfg.dw_tol > 0)
+    return OTLM_EUNSUPPORTED;
   if (batch < 1 || batch > h->cfg.batch_max || n < 2 || k < 1 || nnz < 1 || hw < 0 || hw > otlm::BAND_HMAX ||
       hw >= n || (long long)batch * n > (1LL << 40))
     return OTLM_EINVAL;
@@ -509,6 +528,41 @@ int otlm_initial_weights(otlm_handle h, int batch, int n, int k, const void* D, 
   L.end();
   h->launches += 1;  // two kernels, one timed region
   return cudaGetLastError() == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
+}
+
+int otlm_solve_stats(otlm_handle h, int batch, void* dw_out, double* primal_out, double* dual_out) {
+  if (!h || batch < 1 || batch > h->cfg.batch_max) return OTLM_EINVAL;
+  const otlm_config& c = h->cfg;
+  if ((primal_out || dual_out) && c.check_every < 1) return OTLM_EINVAL;
+  const WsLayout lay = ws_layout(c);
+  char* base = static_cast<char*>(h->ws);
+  cudaError_t e = cudaSuccess;
+  if (c.precision == OTLM_PREC_FP64) {
+    Workspace<double> ws;
+    otlm::carve_workspace<double>(base, c.n_max, c.k_max, c.batch_max, &ws);
+    if (dw_out) e = cudaMemcpyAsync(dw_out, ws.dw, sizeof(double) * batch, cudaMemcpyDeviceToDevice, h->stream);
+  } else {
+    Workspace<float> ws;
+    otlm::carve_workspace<float>(base, c.n_max, c.k_max, c.batch_max, &ws);
+    if (dw_out) e = cudaMemcpyAsync(dw_out, ws.dw, sizeof(float) * batch, cudaMemcpyDeviceToDevice, h->stream);
+  }
+  if (lay.obj && (primal_out || dual_out)) {
+    double *pr = nullptr, *du = nullptr;
+    if (c.precision == OTLM_PREC_FP64) {
+      otlm::ObjWorkspace<double> ow;
+      otlm::carve_obj_workspace<double>(base + lay.base + lay.tc + lay.mm, c.n_max, c.batch_max, &ow);
+      pr = ow.primal; du = ow.dual;
+    } else {
+      otlm::ObjWorkspace<float> ow;
+      otlm::carve_obj_workspace<float>(base + lay.base + lay.tc + lay.mm, c.n_max, c.batch_max, &ow);
+      pr = ow.primal; du = ow.dual;
+    }
+    if (e == cudaSuccess && primal_out)
+      e = cudaMemcpyAsync(primal_out, pr, sizeof(double) * batch, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && dual_out)
+      e = cudaMemcpyAsync(dual_out, du, sizeof(double) * batch, cudaMemcpyDeviceToDevice, h->stream);
+  }
+  return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
 long long otlm_launch_count(otlm_handle h) { return h ? h->launches : -1; }

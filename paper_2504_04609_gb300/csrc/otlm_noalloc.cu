@@ -80,6 +80,6 @@ extern "C" int otlm_solve_noalloc(int batch, int n, int k, const float* x, const
   sp.batch = batch; sp.n = n; sp.k = k; sp.eps = eps; sp.lam = lam; sp.alpha = alpha;
   sp.datafit = datafit; sp.penalty = penalty; sp.max_iter = max_iter; sp.poll_every = 8; sp.tol = tol;
   const cudaError_t e =
-      otlm::solve_device<float>(L, ws, sp, x, D, y, w, g, t_out, iters_out, err_out, status_out);
+      otlm::solve_device<float>(L, ws, nullptr, sp, x, D, y, w, g, t_out, iters_out, err_out, status_out);
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }

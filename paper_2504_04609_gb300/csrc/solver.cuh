@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "objective_kernels.cuh"
 
 namespace otlm {
 
@@ -75,8 +76,24 @@ struct Launch {
 template <typename T>
 struct Workspace {
   T *xt, *Dt, *xcol, *G2, *LA2, *LB2, *F2, *S, *W, *mass, *err_acc, *err;
+  T* dw;      // [batch] ||dw||_1 / ||w||_1 of the last MM update
+  T* Wprev;   // [batch][k] weights before the last update (tensor-core path)
   int *active, *n_active, *done, *iters, *status;
+  int *all, *all_count;  // every problem of the batch, in order (the final objective's list)
   double* kmass;
+};
+
+// Scratch of the in-solve objective (handles created with check_every > 0): the state's source
+// potential, its target sums and datafit step, and the per-problem FP64 primal, dual and gap test.
+template <typename T>
+struct ObjWorkspace {
+  T* F2;          // [batch][n]
+  T* LB2;         // [batch][n] (tensor-core path: the raw target sums first, decoded in place)
+  T* G2n;         // [batch][n]
+  T* M;           // [batch] target shift of the tensor-core operand
+  double *primal, *dual;  // [batch]
+  int* gap_ok;    // [batch]
+  double* kmass;  // sum_ij K_ij
 };
 
 inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
@@ -105,6 +122,10 @@ size_t carve_workspace(void* base, int n_max, int k_max, int batch_max, Workspac
   w.mass = (T*)take(sizeof(T) * batch_max);
   w.err_acc = (T*)take(sizeof(T) * batch_max);
   w.err = (T*)take(sizeof(T) * batch_max);
+  w.dw = (T*)take(sizeof(T) * batch_max);
+  w.Wprev = (T*)take(sizeof(T) * bk);
+  w.all = (int*)take(sizeof(int) * batch_max);
+  w.all_count = (int*)take(sizeof(int) * 32);
   w.active = (int*)take(sizeof(int) * batch_max);
   w.n_active = (int*)take(sizeof(int) * 32);
   w.done = (int*)take(sizeof(int) * batch_max);
@@ -115,6 +136,29 @@ size_t carve_workspace(void* base, int n_max, int k_max, int batch_max, Workspac
   return off;
 }
 
+template <typename T>
+size_t carve_obj_workspace(void* base, int n_max, int batch_max, ObjWorkspace<T>* ow) {
+  const size_t bn = (size_t)batch_max * n_max;
+  size_t off = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? b + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  ObjWorkspace<T> o;
+  o.F2 = (T*)take(sizeof(T) * bn);
+  o.LB2 = (T*)take(sizeof(T) * bn);
+  o.G2n = (T*)take(sizeof(T) * bn);
+  o.M = (T*)take(sizeof(T) * batch_max);
+  o.primal = (double*)take(sizeof(double) * batch_max);
+  o.dual = (double*)take(sizeof(double) * batch_max);
+  o.gap_ok = (int*)take(sizeof(int) * batch_max);
+  o.kmass = (double*)take(sizeof(double) * 4);
+  if (ow) *ow = o;
+  return off;
+}
+
 struct SolveParams {
   int batch, n, k;
   double eps, lam, alpha;
@@ -122,7 +166,23 @@ struct SolveParams {
   double tol;
   double beta = 0.0;  // elastic net's squared-l2 weight
   int mm_steps = 1;   // MM steps per iteration
+  int check_every = 0;   // FP64 objective / gap every this many iterations and at the end (0: never)
+  double gap_tol = 0.0;  // stop also requires (primal - dual) <= gap_tol |primal| at a check
+  double dw_tol = 0.0;   // stop also requires ||dw||_1 / ||w||_1 <= dw_tol
 };
+
+// Argument block of the FP64 reduction for a state held in the workspaces (S, G2, the weights)
+// with its source potential, target sums and datafit step in the objective scratch.
+template <typename T>
+ObjArgs<T> obj_args(const SolveParams& sp, const T* D, const T* xcol, const T* W, const T* y, const T* S,
+                    const T* G2, const ObjWorkspace<T>& ow) {
+  ObjArgs<T> oa{};
+  oa.D = D; oa.xcol = xcol; oa.W = W; oa.y = y; oa.S = S; oa.F2 = ow.F2; oa.G2 = G2; oa.LB2 = ow.LB2;
+  oa.G2n = ow.G2n; oa.kmass = ow.kmass; oa.primal = ow.primal; oa.dual = ow.dual; oa.n = sp.n; oa.k = sp.k;
+  oa.datafit = sp.datafit; oa.penalty = sp.penalty; oa.eps = sp.eps; oa.lam = sp.lam; oa.alpha = sp.alpha;
+  oa.beta = sp.beta; oa.balanced_rtol = sizeof(T) == 4 ? 1e-4 : 1e-10; oa.gap_tol = sp.gap_tol;
+  return oa;
+}
 
 template <typename T> struct TileFor;
 // FP32 apply tile (problems per thread, rows per thread, warps along problems, warps along rows,
@@ -193,18 +253,42 @@ void launch_mm(const Launch& L, const MMArgs<T>& a, int batch) {
   L.end();
 }
 
-// Run Algorithm 1 on device buffers.  Returns cudaSuccess or the first launch/copy error.
+// FP64 objective and dual (Eq. OTLM, reading A1) of the listed problems' states (w, g) from the
+// a = K u1 already in LA2 and the s = D w in S: F2 = log2 s - log2 a, one target apply of F2 into
+// the scratch (its datafit step g' into G2n), then the reduction; gap = true also records the gap
+// test.  One extra kernel apply beside the solve's own.
 template <typename T>
-cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const SolveParams& sp, const T* x, const T* D,
-                         const T* y, T* w, T* g, T* t_out, int* iters_out, T* err_out, int* status_out) {
+void objective_eval(const Launch& L, const Workspace<T>& ws, const ObjWorkspace<T>& ow, const SolveParams& sp,
+                    const ApplyArgs<T>& tgt, const T* D, const T* y, const int* list, const int* count, bool gap) {
+  L.begin(KIND_OTHER);
+  obj_f2_kernel<T><<<sp.batch, 256, 0, L.stream>>>(list, count, ws.S, ws.LA2, ow.F2, sp.n);
+  L.end();
+  ApplyArgs<T> t = tgt;
+  t.in = ow.F2; t.out = ow.LB2; t.G2 = ow.G2n; t.active = list; t.n_active = count; t.check = 0;
+  launch_apply<T, EPI_TARGET>(L, t, true, sp.batch, sp.n);
+  ObjArgs<T> oa = obj_args<T>(sp, D, ws.xcol, ws.W, y, ws.S, ws.G2, ow);
+  oa.list = list; oa.count = count; oa.gap_ok = gap ? ow.gap_ok : nullptr;
+  L.begin(KIND_OTHER);
+  objective_reduce_kernel<T><<<sp.batch, 256, 0, L.stream>>>(oa);
+  L.end();
+}
+
+// Run Algorithm 1 on device buffers.  Returns cudaSuccess or the first launch/copy error.
+// ow (may be null when sp.check_every == 0): the objective scratch of the gap checks.
+template <typename T>
+cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorkspace<T>* ow, const SolveParams& sp,
+                         const T* x, const T* D, const T* y, T* w, T* g, T* t_out, int* iters_out, T* err_out,
+                         int* status_out) {
   const int batch = sp.batch, n = sp.n, k = sp.k;
   const double eps_ln2 = sp.eps * kLn2;
+  const bool checks = ow && sp.check_every > 0;
 
   PrepArgs<T> pa;
   pa.x = x; pa.D = D; pa.w_in = w; pa.g_in = g; pa.y = y;
   pa.xt = ws.xt; pa.Dt = ws.Dt; pa.xcol = ws.xcol; pa.W = ws.W; pa.G2 = ws.G2;
   pa.active = ws.active; pa.done = ws.done; pa.n_active = ws.n_active; pa.err_acc = ws.err_acc;
   pa.iters = ws.iters; pa.status = ws.status; pa.err = ws.err;
+  pa.dw = ws.dw; pa.all = ws.all; pa.all_count = ws.all_count;
   pa.batch = batch; pa.n = n; pa.k = k;
   pa.xscale = T(1.0 / sqrt(eps_ln2));
   pa.gscale = T(1.0 / eps_ln2);
@@ -217,6 +301,13 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const SolvePar
   L.begin(KIND_OTHER);
   source_init_kernel<T><<<batch, 256, 0, L.stream>>>(ws.Dt, ws.W, ws.S, ws.mass, n, k);
   L.end();
+  if (checks) {  // sum_ij K_ij, FP64, once per solve
+    cudaError_t e = cudaMemsetAsync(ow->kmass, 0, sizeof(double), L.stream);
+    if (e != cudaSuccess) return e;
+    L.begin(KIND_OTHER);
+    kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass);
+    L.end();
+  }
 
   ApplyArgs<T> src{};
   src.in = ws.G2; src.out = ws.LA2; src.xt = ws.xt; src.active = ws.active; src.n_active = ws.n_active;
@@ -234,11 +325,18 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const SolvePar
   mm.err_acc = ws.err_acc; mm.err = ws.err; mm.done = ws.done; mm.iters = ws.iters; mm.status = ws.status;
   mm.max_iter = sp.max_iter; mm.tol = T(sp.tol); mm.penalty = sp.penalty; mm.eps = T(sp.eps);
   mm.alpha = T(sp.alpha); mm.beta = T(sp.beta); mm.mm_steps = sp.mm_steps;
+  mm.dw = ws.dw; mm.dw_tol = T(sp.dw_tol); mm.gap_on = checks && sp.gap_tol > 0;
+  mm.gap_ok = checks ? ow->gap_ok : nullptr;
 
   for (int it = 0;; ++it) {
     src.check = it > 0;
     launch_apply<T, EPI_SOURCE>(L, src, it == 0, batch, n);
+    // a check: the state (w, g) whose a = K u1 was just computed is the one this iteration returns
+    // if it stops here; its FP64 objective and gap come before the stopping decision
+    const bool check = checks && it > 0 && it % sp.check_every == 0;
+    if (check) objective_eval<T>(L, ws, *ow, sp, tgt, D, y, ws.active, ws.n_active, true);
     mm.it = it;
+    mm.gap_check = check;
     launch_mm<T>(L, mm, batch);
     L.begin(KIND_COMPACT);
     compact_kernel<<<1, 1024, 0, L.stream>>>(ws.active, ws.n_active, ws.done);
@@ -253,6 +351,10 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const SolvePar
       if (*L.host_flag == 0) break;
     }
   }
+
+  // the returned states' objective: for every problem LA2 holds a = K u1 of its final g (computed
+  // at the iteration it stopped), S = D w of its final w
+  if (checks) objective_eval<T>(L, ws, *ow, sp, tgt, D, y, ws.all, ws.all_count, false);
 
   FinArgs<T> fa;
   fa.W = ws.W; fa.G2 = ws.G2; fa.LB2 = ws.LB2; fa.iters = ws.iters; fa.status = ws.status; fa.err = ws.err;

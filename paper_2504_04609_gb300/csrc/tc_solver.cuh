@@ -281,6 +281,11 @@ struct TcIterArgs {
   float* W;
   float* mass;
   float* err;
+  float* dw;         // [P] ||dw||_1 / ||w||_1 of the last weight update
+  float* Wprev;      // [P][k] weights before the last update
+  const int* gap_ok; // [P] gap test of this iteration's check
+  int gap_check, gap_on;
+  float dw_tol;
   int* done;
   int* iters;
   int* status;
@@ -455,13 +460,22 @@ __device__ __forceinline__ void tc_violation_body(const TcIterArgs& A) {
   }
   if (!check) return;
   part = block_sum(part, red);
+  // weight change of the previous iteration's update (k <= 256 entries)
+  float num = 0.f, den = 0.f;
+  for (int j = threadIdx.x; j < A.k; j += NT) {
+    const float wv = A.W[(size_t)p * A.k + j];
+    num += fabsf(wv - A.Wprev[(size_t)p * A.k + j]);
+    den += fabsf(wv);
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
   if (threadIdx.x == 0) {
     const float e = part / A.mass[p];
+    const float dw = num / den;
     A.err[p] = e;
-    int st = -1;
-    if (e != e) st = ST_NONFINITE;
-    else if (A.tol > 0.f && e <= A.tol) st = ST_CONVERGED;
-    else if (A.it >= A.max_iter) st = ST_MAX_ITER;
+    A.dw[p] = dw;
+    const int st = stop_decision<float>(e, dw, A.tol, A.dw_tol, A.gap_on != 0,
+                                        A.gap_check && A.gap_ok && A.gap_ok[p], A.it, A.max_iter);
     if (st >= 0) {
       A.status[p] = st;
       A.iters[p] = A.it;
@@ -504,7 +518,7 @@ inline size_t carve_tc_mm(void* base, int k_max, int batch_max, TcMMBuf* mb) {
   };
   TcMMBuf m;
   m.ldnu = (k_max + 3) / 4 * 4;
-  m.plane = (size_t)batch_max * k_max;
+  m.plane = (size_t)batch_max * m.ldnu;  // rows of a split are written with pitch ldnu
   m.NU = (float*)take(4 * (size_t)TC_MAX_SPLITS * m.plane);
   if (mb) *mb = m;
   return off;
@@ -513,7 +527,10 @@ inline size_t carve_tc_mm(void* base, int k_max, int batch_max, TcMMBuf* mb) {
 // One thread per (slot, j) of the slots before compaction.  A problem that has just stopped keeps
 // its weights (and with update = 0 every problem does); every slot writes its weight row as the
 // TF32 hi/lo B operand of s = D w.
-__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, int splits, int update) {
+// save_prev: the first update of an iteration also keeps the weights it starts from (Wprev), for
+// the weight-change measure of the next stopping decision.
+__global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, int splits, int update,
+                                                      int save_prev) {
   using P = Prec<float>;
   const int na = *A.n_active, k = A.k;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -522,6 +539,7 @@ __global__ void __launch_bounds__(256) tc_wupd_kernel(TcIterArgs A, TcMMBuf M, i
   const int p = A.active[slot];
   float wn = A.W[(size_t)p * k + j];
   if (update && !A.done[p]) {
+    if (save_prev) A.Wprev[(size_t)p * k + j] = wn;
     float sum = 0.f;
     for (int z = 0; z < splits; ++z) sum += M.NU[z * M.plane + (size_t)slot * M.ldnu + j];
     const float xj = A.xcol[j];
@@ -602,6 +620,54 @@ __global__ void __launch_bounds__(NT) tc_operand_kernel(TcIterArgs A) {
   }
 }
 
+// ---- FP64 objective of a state on the tensor-core path (gap checks and the returned states) ----
+// Per listed problem (CTA = slot): F2 = log2 s - log2 a of the state, with a from the source sums of
+// parity `par` (a check: this iteration's), or of the parity of the problem's own last iteration
+// (par < 0: the returned states); the target shift M = max F2 and the operand row U = 2^(F2 - M)
+// (BF16 hi/lo) of the slot.  Rare, so the row is streamed.
+__global__ void __launch_bounds__(256) tc_obj_operand_kernel(TcIterArgs A, const int* list, const int* count,
+                                                             int par, float* F2o, float* Mo) {
+  using P = Prec<float>;
+  __shared__ float red[32];
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int p = list[slot], n = A.n;
+  const int cur = par >= 0 ? par : (A.iters[p] & 1);
+  const float* S = A.S + (size_t)p * n;
+  const float* acc = A.t.ACC_src[cur] + (size_t)p * n;
+  const float mc = A.t.Msrc[cur][p];
+  float* F2 = F2o + (size_t)p * n;
+  __nv_bfloat16* vhi = A.t.Vhi + (size_t)slot * A.t.ld;
+  __nv_bfloat16* vlo = A.t.Vlo + (size_t)slot * A.t.ld;
+  float fm = -CUDART_INF_F;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float sv = S[i];
+    const float f2 = sv > 0.f ? P::log2(sv) - tc_log2_sum(acc[i], mc) : P::ninf();
+    F2[i] = f2;
+    fm = fmaxf(fm, f2);
+  }
+  fm = block_max(fm, red);  // its barriers also order the F2 writes before the reads below
+  const float m = fm > -CUDART_INF_F ? fm : 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tc_store_operand(P::exp2(F2[i] - m), vhi, vlo, i);
+  if (threadIdx.x == 0) Mo[p] = m;
+}
+
+// The state's target sums (raw, in LB2o) decoded in place to log2 b, and the datafit step g' from
+// them (Table 1), for the listed problems.
+__global__ void tc_obj_decode_kernel(TcIterArgs A, const int* list, const int* count, float* LB2o, const float* Mo,
+                                     float* G2no) {
+  const int n = A.n;
+  const size_t total = (size_t)(*count) * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(e / n), j = (int)(e - (size_t)slot * n);
+    const int p = list[slot];
+    const size_t idx = (size_t)p * n + j;
+    const float lb = tc_log2_sum(LB2o[idx], Mo[p]);
+    LB2o[idx] = lb;
+    G2no[idx] = tc_datafit(A, lb, A.y[idx]);
+  }
+}
+
 // t = Q^T 1 = 2^{G2 + LB2}, LB2 = Mtgt + log2(target sum); w, g and the per-problem statistics.
 __global__ void tc_finalize_kernel(FinArgs<float> F, const float* ACC_tgt, const float* Mtgt) {
   using P = Prec<float>;
@@ -626,18 +692,20 @@ __global__ void tc_finalize_kernel(FinArgs<float> F, const float* ACC_tgt, const
 
 // Run Algorithm 1 with tensor-core applies and dictionary contractions (float buffers; x, D, y, w,
 // g as in solve_device).  Returns cudaErrorLaunchTimeout when a GEMM reported an expired wait.
+// ow (may be null when sp.check_every == 0): the objective scratch of the FP64 gap checks.
 inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, const TcWorkspace& tw,
-                                   const TcMMBuf& mb, const SolveParams& sp, const float* x, const float* C,
-                                   const float* D,
-                                   const float* y, float* w, float* g, float* t_out, int* iters_out, float* err_out,
-                                   int* status_out) {
+                                   const TcMMBuf& mb, const ObjWorkspace<float>* ow, const SolveParams& sp,
+                                   const float* x, const float* C, const float* D, const float* y, float* w, float* g,
+                                   float* t_out, int* iters_out, float* err_out, int* status_out) {
   const int batch = sp.batch, n = sp.n, k = sp.k;
   const double eps_ln2 = sp.eps * kLn2;
+  const bool checks = ow && sp.check_every > 0;
   PrepArgs<float> pa;
   pa.x = x; pa.D = D; pa.w_in = w; pa.g_in = g; pa.y = y;
   pa.xt = ws.xt; pa.Dt = ws.Dt; pa.xcol = ws.xcol; pa.W = ws.W; pa.G2 = ws.G2;
   pa.active = ws.active; pa.done = ws.done; pa.n_active = ws.n_active; pa.err_acc = ws.err_acc;
   pa.iters = ws.iters; pa.status = ws.status; pa.err = ws.err;
+  pa.dw = ws.dw; pa.all = ws.all; pa.all_count = ws.all_count;
   pa.batch = batch; pa.n = n; pa.k = k;
   pa.xscale = float(1.0 / sqrt(eps_ln2));
   pa.gscale = float(1.0 / eps_ln2);
@@ -658,7 +726,14 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   L.end();
   cudaError_t e = cudaMemsetAsync(tw.err, 0, sizeof(int), L.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(tw.fix_cnt, 0, 2 * sizeof(unsigned long long), L.stream);
+  if (e == cudaSuccess && checks) e = cudaMemsetAsync(ow->kmass, 0, sizeof(double), L.stream);
   if (e != cudaSuccess) return e;
+  if (checks) {  // sum_ij K_ij in FP64, once per solve
+    L.begin(KIND_OTHER);
+    if (C) kernel_mass_dense_kernel<<<592, 256, 0, L.stream>>>(C, n, 1.0 / sp.eps, ow->kmass);
+    else kernel_mass_kernel<float><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass);
+    L.end();
+  }
 
   TcIterArgs ta{};
   ta.active = ws.active; ta.n_active = ws.n_active; ta.n = n; ta.k = k; ta.ld = tw.ld;
@@ -668,6 +743,8 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   ta.lam_over_eps = float(sp.lam / sp.eps); ta.log_lam_over_eps = float(log(sp.lam / sp.eps));
   ta.y = y; ta.D = D; ta.Dt = ws.Dt; ta.xcol = ws.xcol; ta.G2 = ws.G2; ta.S = ws.S; ta.F2 = ws.F2; ta.W = ws.W;
   ta.mass = ws.mass; ta.err = ws.err; ta.done = ws.done; ta.iters = ws.iters; ta.status = ws.status; ta.t = tw;
+  ta.dw = ws.dw; ta.Wprev = ws.Wprev; ta.dw_tol = float(sp.dw_tol); ta.gap_on = checks && sp.gap_tol > 0;
+  ta.gap_ok = checks ? ow->gap_ok : nullptr;
 
   // the applies K V^T (BF16): M = bins, N = slots mapped to problems, reduction over bins
   tc::GemmArgs ga{};
@@ -713,10 +790,48 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   gw.ld_out = n; gw.err = tw.err; gw.flush_tiny = 1; gw.splits = 1;
   const int row_cfg = tc_row_cfg(n);
 
+  // FP64 objective of the listed problems' states (w, g) on the tensor-core applies: the state's
+  // source sums (parity par, or each problem's last when par < 0) give F2, one target GEMM of its
+  // operand (into the objective scratch, with its own fix-up list count) gives b and g', then the
+  // FP64 reduction; gap = true also records the gap test.
+  auto objective_tc = [&](const int* list, const int* count, int par, bool gap) -> cudaError_t {
+    L.begin(KIND_OTHER);
+    tc_obj_operand_kernel<<<batch, 256, 0, L.stream>>>(ta, list, count, par, ow->F2, ow->M);
+    L.end();
+    cudaError_t r = cudaMemsetAsync(tw.fix_cnt + 2, 0, sizeof(unsigned long long), L.stream);
+    if (r != cudaSuccess) return r;
+    tc::GemmArgs go = ga;
+    go.col_map = list; go.n_cols = count; go.fix_cnt = tw.fix_cnt + 2;
+    go.out = go.splits > 1 ? tw.ACCP : ow->LB2;
+    L.begin(KIND_APPLY);
+    r = tc::launch_gemm3<tc::KIND_BF16>(C ? tw.Kthi : tw.Khi, C ? tw.Ktlo : tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n,
+                                        batch, n, go, L.stream);
+    if (r == cudaSuccess && go.splits > 1) {
+      tc_split_reduce_kernel<<<red_grid, 256, 0, L.stream>>>(tw.ACCP, go.splits, go.split_stride, list, count, n,
+                                                              ow->LB2, tw.fix_list, tw.fix_cnt + 2, go.fix_cap);
+      r = cudaGetLastError();
+    }
+    L.end();
+    if (r != cudaSuccess) return r;
+    L.begin(KIND_OTHER);
+    tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt + 2, tw.fix_cnt + 3, ga.fix_cap, n,
+                                                    cost_tgt, ow->F2, ow->LB2, ow->M);
+    L.end();
+    L.begin(KIND_OTHER);
+    tc_obj_decode_kernel<<<red_grid, 256, 0, L.stream>>>(ta, list, count, ow->LB2, ow->M, ow->G2n);
+    L.end();
+    ObjArgs<float> oa = obj_args<float>(sp, D, ws.xcol, ws.W, y, ws.S, ws.G2, *ow);
+    oa.list = list; oa.count = count; oa.gap_ok = gap ? ow->gap_ok : nullptr;
+    L.begin(KIND_OTHER);
+    objective_reduce_kernel<float><<<batch, 256, 0, L.stream>>>(oa);
+    L.end();
+    return cudaGetLastError();
+  };
+
   // the initial source marginal s = D w0, through the same operand and GEMM as every iteration
   // (the mass sum_i s_i is first needed by the violation at it = 1 and set by the operand kernel)
   L.begin(KIND_OTHER);
-  tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, 0, 0);
+  tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, 0, 0, 0);
   L.end();
   L.begin(KIND_OTHER);
   e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
@@ -734,6 +849,14 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     tc_fixup_kernel<<<TC_FIX_GRID, 256, 0, L.stream>>>(tw.fix_list, tw.fix_cnt, tw.fix_cnt + 1, ga.fix_cap, n,
                                                     cost_src, ws.G2, tw.ACC_src[it & 1], tw.Msrc[it & 1]);
     L.end();
+    // a check: the state (w, g) whose source sums were just computed is the one this iteration
+    // returns if it stops here; its FP64 objective and gap come before the stopping decision
+    const bool check = checks && it > 0 && it % sp.check_every == 0;
+    if (check) {
+      e = objective_tc(ws.active, ws.n_active, it & 1, true);
+      if (e != cudaSuccess) return e;
+    }
+    ta.gap_check = check;
     L.begin(KIND_MM);
     TC_ROW_LAUNCH(tc_violation_kernel, row_cfg, batch, L.stream, ta);
     L.end();
@@ -743,7 +866,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     L.end();
     if (e != cudaSuccess) return e;
     L.begin(KIND_MM);
-    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1);
+    tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1, 1);
     L.end();
     L.begin(KIND_MM);
     e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
@@ -759,7 +882,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
       L.end();
       if (e != cudaSuccess) return e;
       L.begin(KIND_MM);
-      tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1);
+      tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1, 0);
       L.end();
       L.begin(KIND_MM);
       e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
@@ -787,6 +910,11 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
       if (e != cudaSuccess) return e;
       if (*L.host_flag == 0) break;
     }
+  }
+  // the returned states' objective (every problem's last source sums are those of its final g)
+  if (checks) {
+    e = objective_tc(ws.all, ws.all_count, -1, false);
+    if (e != cudaSuccess) return e;
   }
   FinArgs<float> fa;
   fa.W = ws.W; fa.G2 = ws.G2; fa.LB2 = nullptr; fa.iters = ws.iters; fa.status = ws.status; fa.err = ws.err;

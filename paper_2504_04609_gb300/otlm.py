@@ -25,7 +25,8 @@ EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm
            "otlm_launch_count", "otlm_set_timing", "otlm_get_timing", "otlm_solve_noalloc", "otlm_solve_ragged", "otlm_solve_banded",
            "otlm_tune_ragged", "otlm_ws_create", "otlm_ws_destroy", "otlm_ws_num_params", "otlm_ws_set_normalization",
            "otlm_ws_get_params", "otlm_ws_set_params", "otlm_ws_gradients", "otlm_ws_train_step", "otlm_ws_predict",
-           "otlm_ws_make_targets", "otlm_ws_fit_normalization", "otlm_initial_weights", "otlm_strerror")
+           "otlm_ws_make_targets", "otlm_ws_fit_normalization", "otlm_initial_weights", "otlm_solve_stats",
+           "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 
 
@@ -33,7 +34,8 @@ class otlm_config(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int), ("k_max", ctypes.c_int), ("batch_max", ctypes.c_int),
                 ("precision", ctypes.c_int), ("datafit", ctypes.c_int), ("penalty", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("poll_every", ctypes.c_int),
-                ("beta", ctypes.c_double), ("mm_steps", ctypes.c_int)]
+                ("beta", ctypes.c_double), ("mm_steps", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("gap_tol", ctypes.c_double), ("dw_tol", ctypes.c_double)]
 
 
 _LIB = None
@@ -99,6 +101,8 @@ def lib() -> ctypes.CDLL:
         L.otlm_ws_fit_normalization.restype = i
         L.otlm_initial_weights.argtypes = [vp, i, i, i, vp, vp, vp]
         L.otlm_initial_weights.restype = i
+        L.otlm_solve_stats.argtypes = [vp, i, vp, vp, vp]
+        L.otlm_solve_stats.restype = i
         L.otlm_strerror.argtypes = [i]
         L.otlm_strerror.restype = ctypes.c_char_p
         _LIB = L
@@ -139,12 +143,16 @@ class Handle:
     """Owns one otlm handle (workspace sized for n_max x k_max x batch_max).
 
     beta: squared-l2 weight of the "elastic" penalty (alpha sum w + (beta/2) ||w||^2);
-    mm_steps: MM steps of the weight update per iteration (1 in Algorithm 1)."""
+    mm_steps: MM steps of the weight update per iteration (1 in Algorithm 1);
+    check_every, gap_tol, dw_tol: the FP64 objective / gap checks and the further stopping
+    criteria of otlm_config."""
 
     def __init__(self, n_max, k_max, batch_max, precision="fp32", datafit="kl", penalty="l2sq",
-                 max_iter=1000, tol=0.0, poll_every=8, stream=None, beta=0.0, mm_steps=1):
+                 max_iter=1000, tol=0.0, poll_every=8, stream=None, beta=0.0, mm_steps=1, check_every=0,
+                 gap_tol=0.0, dw_tol=0.0):
         self.cfg = otlm_config(n_max, k_max, batch_max, PRECISION[precision], DATAFIT[datafit], PENALTY[penalty],
-                               max_iter, float(tol), poll_every, float(beta), mm_steps)
+                               max_iter, float(tol), poll_every, float(beta), mm_steps, check_every, float(gap_tol),
+                               float(dw_tol))
         self.precision = precision
         self._h = ctypes.c_void_p()
         _check(lib().otlm_create(ctypes.byref(self._h), ctypes.byref(self.cfg), stream), "otlm_create")
@@ -228,6 +236,11 @@ class Handle:
                                     _ptr(w), sample_every, iters, ctypes.byref(out))
         _check(rc, "otlm_tune_ragged")
         return out.value
+
+    def solve_stats(self, batch, dw_out=None, primal_out=None, dual_out=None):
+        """otlm_solve_stats: per-problem weight change, FP64 primal and dual of the last solve."""
+        _check(lib().otlm_solve_stats(self._h, batch, _ptr(dw_out), _ptr(primal_out), _ptr(dual_out)),
+               "otlm_solve_stats")
 
     def initial_weights(self, D, y, w_out):
         """otlm_initial_weights: the cold-start weights sum(y) / (k x_j) into w_out [B, k]."""

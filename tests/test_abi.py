@@ -44,7 +44,9 @@ def test_strerror_names_every_code():
 @pytest.mark.parametrize("field,value", [("n_max", 1), ("k_max", 0), ("k_max", 257), ("batch_max", 0),
                                          ("max_iter", 0), ("poll_every", 0), ("precision", 7),
                                          ("datafit", 9), ("penalty", -1), ("penalty", 4), ("mm_steps", -1),
-                                         ("mm_steps", 65)])
+                                         ("mm_steps", 65), ("check_every", -1), ("gap_tol", -1e-3),
+                                         ("gap_tol", float("nan")), ("dw_tol", float("inf")), ("dw_tol", -1.0),
+                                         ("gap_tol", 1e-4)])  # the last: a gap tolerance with no checks
 def test_create_rejects_bad_config_without_gpu(field, value):
     _ensure_built()
     cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)

@@ -56,6 +56,20 @@ def test_tensorcore_trajectory_parity_small(datafit, penalty, eps, lam, alpha):
         assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
 
 
+@pytest.mark.parametrize("n,k,B", [(200, 10, 4), (256, 9, 20), (300, 5, 3)])
+def test_tensorcore_dictionary_sizes_off_the_tf32_row_pitch(n, k, B):
+    """k not a multiple of 4: the dictionary contractions keep their rows at a pitch of k rounded up
+    to 4 (TF32 tensor-map strides), and the D^T r partial sums of the reduction splits must not
+    overlap.  TV + l1 at eps = 2e-2, where t equals y almost regardless of w, so w is compared
+    separately (it was the quantity this layout broke)."""
+    d = spectra.batch(84, B, n, k, 3)
+    r = _solve(d, 2e-2, 1.0, 1e-2, "tv", "l1", 12)
+    for p in range(B):
+        o = _oracle(d, p, 2e-2, 1.0, 1e-2, "tv", "l1", 12)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
+
+
 def test_tensorcore_matches_fp32_path_with_tolerance_stop():
     d = spectra.batch(32, 40, 512, 32, 4)
     args = (1e-2, 1.0, 1e-3, "l2", "l2sq", 500, 1e-5)

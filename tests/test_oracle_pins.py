@@ -442,3 +442,55 @@ def test_violation_is_the_source_marginal_error_of_the_explicit_plan(datafit, pe
         s = X @ r["w"]
         assert r["err"] == pytest.approx(np.abs(Q.sum(axis=1) - s).sum() / s.sum(), rel=1e-12)
         assert len(r["err_hist"]) == T
+
+
+def test_weight_change_history_and_its_stopping_rule():
+    """dw_hist[j] is ||w_{j+1} - w_j||_1 / ||w_{j+1}||_1 of the weights after j and j + 1 iterations
+    (each taken from its own shorter run), and with dw_tol alone the solve stops at the first
+    iteration whose previous update changed w by at most dw_tol (reading A8's weight change)."""
+    d = spectra.batch(71, 1, 60, 5, 2)
+    x, D, y = (d[key].astype(np.float64) for key in ("x", "D", "y"))
+    y = y[0]
+    C = spectra.squared_cost(x)
+    w0 = spectra.initial_weights(y, D)
+    args = (C, D, y, 1e-2, 1.0, 1e-2, "kl", "l1")
+    full = oracle.solve_log(*args, w0, 30)
+    ws = [oracle.solve_log(*args, w0, j)["w"] for j in range(1, 8)]
+    for j in range(6):
+        want = np.abs(ws[j + 1] - ws[j]).sum() / np.abs(ws[j + 1]).sum()
+        assert full["dw_hist"][j + 1] == pytest.approx(want, rel=1e-12)
+    dw_tol = float(np.sort(full["dw_hist"])[len(full["dw_hist"]) // 2])  # reached part-way
+    first = int(np.argmax(full["dw_hist"] <= dw_tol))
+    r = oracle.solve_log(*args, w0, 30, dw_tol=dw_tol)
+    assert r["iters"] == first + 1
+    np.testing.assert_array_equal(r["w"], oracle.solve_log(*args, w0, first + 1)["w"])
+
+
+@pytest.mark.parametrize("datafit,penalty", [("kl", "l2sq"), ("l2", "l2sq"), ("tv", "l1")])
+def test_gap_stopping_rule_stops_at_the_first_check_under_tolerance(datafit, penalty):
+    """With gap_tol (checked every 3 iterations) and tol, the solve returns at the first check where
+    the violation and the relative gap of the returned state are both under their tolerances; the
+    gap recorded there is the returned state's own (objective_and_dual on it), and it is >= 0."""
+    d = spectra.batch(72, 1, 50, 4, 2)
+    x, D, y = (d[key].astype(np.float64) for key in ("x", "D", "y"))
+    y = y[0]
+    C = spectra.squared_cost(x)
+    w0 = spectra.initial_weights(y, D)
+    eps, lam, alpha = 2e-2, 1.0, 1e-2
+    args = (C, D, y, eps, lam, alpha, datafit, penalty)
+    ref = oracle.solve_log(*args, w0, 400)
+    gaps = {}
+    for it in range(3, 400, 3):
+        st = oracle.solve_log(*args, w0, it)  # the state a stop at iteration `it` returns
+        P, Dv, _ = oracle.objective_and_dual(st["w"], st["g"], *args)
+        gaps[it] = (P, Dv)
+        assert P - Dv >= -1e-10 * abs(P)
+        if (P - Dv) <= 1e-5 * abs(P) and ref["err_hist"][it - 1] <= 1e-6:
+            break
+    r = oracle.solve_log(*args, w0, 400, tol=1e-6, check_every=3, gap_tol=1e-5)
+    assert r["iters"] == it
+    assert r["gap_hist"][-1][0] == it
+    assert r["gap_hist"][-1][1] == pytest.approx(gaps[it][0], rel=1e-12)
+    assert r["gap_hist"][-1][2] == pytest.approx(gaps[it][1], rel=1e-12)
+    P, Dv, _ = oracle.objective_and_dual(r["w"], r["g"], *args)
+    assert P == pytest.approx(gaps[it][0], rel=1e-12) and P - Dv <= 1e-5 * abs(P)
