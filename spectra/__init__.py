@@ -121,6 +121,22 @@ def ragged(workload: int, count: int, n_range=(256, 4096), k_range=(8, 128), eps
     return out
 
 
+def ragged_sizes(workload: int, count: int, n_range=(256, 4096), k_range=(8, 128), eps_range=(2e-3, 5e-2),
+                 first: int = 0):
+    """The (n, k, eps) of each problem of `ragged(workload, count, ..., first=first)` without the
+    arrays: the first three draws of each problem's stream (int64, int64, float64 arrays), so that a
+    packed layout can be planned before the problems are generated."""
+    n = np.empty(count, np.int64)
+    k = np.empty(count, np.int64)
+    eps = np.empty(count, np.float64)
+    for p in range(count):
+        rng = _rng(workload, 2, first + p)
+        n[p] = int(rng.integers(n_range[0], n_range[1] + 1))
+        k[p] = int(rng.integers(k_range[0], k_range[1] + 1))
+        eps[p] = float(np.exp(rng.uniform(np.log(eps_range[0]), np.log(eps_range[1]))))
+    return n, k, eps
+
+
 def scaling_dictionary(n: int, k: int, sigma_b: float = 2.0, trunc: float = 5.0):
     """Sparse dictionary of the paper's scalability test (App. "Performance Scalability Tests"):
     k Gaussians of height 1 on the sample grid x_i = i, means m n / k (m = 0..k-1), width sigma_b,

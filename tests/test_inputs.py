@@ -61,3 +61,12 @@ def test_scaling_targets_are_nonnegative_mixtures_of_the_stated_size():
     # each skew-normal density has unit mass and each amplitude is |N(1, 0.2)| + 0.01; components
     # near the ends lose part of their mass
     assert 0.8 * k < y.sum() < 1.2 * k + 0.002 * n
+
+
+def test_ragged_sizes_replay_the_generator():
+    """ragged_sizes gives the n, k and eps of ragged() problem by problem (the packed layout of
+    the uneven batch is planned from it before the arrays are generated in parallel)."""
+    probs = spectra.ragged(4, 12, first=37)
+    n, k, eps = spectra.ragged_sizes(4, 12, first=37)
+    assert list(n) == [p["n"] for p in probs] and list(k) == [p["k"] for p in probs]
+    assert list(eps) == [p["eps"] for p in probs]
