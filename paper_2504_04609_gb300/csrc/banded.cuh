@@ -13,7 +13,7 @@
 // ratios r = LA2 - log2 S), MM step (stop decision from the tile partials in a fixed order, then
 // Table 2 per atom and problem), and target kernel (s = D w on the tile and its halo, F2 =
 // log2 s - LA2, the target apply and the datafit prox of Table 1, the tile's mass).  The apply
-// kernels take tiles of 256 bins x PB problems per CTA: a thread owns one row (or column) of the
+// kernels take tiles of 256 bins x PB (4) problems per CTA, three CTAs per SM: a thread owns one row (or column) of the
 // band, loads its 2h + 1 costs once into registers (template buckets of 9, 19 and 33 diagonals,
 // padded with +inf; wider bands read them from global memory) and uses them for the PB problems,
 // whose potentials (tile plus halo) are staged in shared memory.  Each log-sum-exp is one pass of
@@ -22,6 +22,15 @@
 // shared shift per window of rows would not do: at eps = 1e-3 the potentials move by ~14 log2
 // units per bin, so a window's largest term underflows most of its rows' terms.
 // A problem that stops keeps the state of its last completed iteration; later launches skip it.
+//
+// Precision of the potentials.  At eps = 1e-3 the log2 potentials reach lam / (eps ln2) ~ 1443, where
+// an FP32 value resolves only ~6e-5 (a relative 4e-5 in u = 2^G), and the MM step's sum of
+// D_ij log2(a_i / s_i) cancels terms of that size to a result near 0.  So G2, LA2 and LB2 are kept
+// as pairs {a, b} (float2) whose value is a + b with `a` integer-valued (exact in FP32 up to 2^24)
+// and |b| <= 1/2 after normalisation (pot_norm): the difference of two potentials' `a` parts is
+// exact, and every rounding happens on numbers of the size of the result.  The datafit step and
+// the MM sum take their few large-magnitude operations in FP64 (O(n) and O(nnz) per problem per
+// iteration); the exponent-unit work stays FP32.
 #pragma once
 
 #include "banded_api.h"
@@ -33,7 +42,10 @@ constexpr int BAND_NT = 256;       // threads per CTA
 
 struct BandArgs {
   int batch, n, k, h, tiles, it, max_iter, datafit, penalty;
-  float tol, eps, alpha, beta, kl_coef, tv_bound, lam_over_eps, log_lam_over_eps;
+  float tol, eps, alpha, beta;
+  // constants of the datafit step as FP32 pairs {hi, lo} (value hi + lo to ~48 bits): lam/(eps+lam),
+  // lam/(eps ln2), lam/eps, ln(lam/eps), log2(eps/lam), ln 2
+  float2 kl_coef, tv_bound, lam_over_eps, log_lam_over_eps, log2_eps_over_lam, ln2;
   const float* C2;        // [2h+1][n] C / (eps ln2)
   const int* col_ptr;     // [k+1]  CSC of D
   const int* row_idx;     // [nnz]
@@ -43,11 +55,10 @@ struct BandArgs {
   const float* rval;      // [nnz]
   const float* xcol;      // [k] column masses
   const float* y;         // [B][n]
-  float* G2;              // [B][n] target potential / (eps ln2)
-  float* LA2;             // [B][n] log2 K u1 (previous iteration's on entry to the source kernel)
-  float* LB2;             // [B][n] log2 K^T u2 (previous iteration's on entry to the target kernel)
+  float2* G2;             // [B][n] target potential / (eps ln2), split {a, b}
+  float2* LA2;            // [B][n] log2 K u1 (previous iteration's on entry to the source kernel), split
+  float2* LB2;            // [B][n] log2 K^T u2 (previous iteration's on entry to the target kernel), split
   float* S;               // [B][n] D w
-  float* R;               // [B][n] log ratios
   float* W;               // [B][k]
   float* vpart;           // [B][tiles] violation numerators
   float* mpart;           // [B][tiles] masses sum_i S_i
@@ -60,21 +71,55 @@ struct BandArgs {
 
 constexpr int BAND_WARPS = BAND_NT / 32;
 
-// Shared memory of the apply kernels (bytes): PB potential rows [TN + 2h] and the block-sum
-// scratch [PB][warps].
+// Shared memory of the apply kernels (bytes): PB split potential rows [TN + 2h] (float2) and the
+// block-sum scratch [PB][warps].
 inline size_t band_smem_bytes(int h, int pb) {
-  return 4 * ((size_t)pb * (BAND_TN + 2 * (size_t)h) + (size_t)pb * BAND_WARPS);
+  return 8 * (size_t)pb * (BAND_TN + 2 * (size_t)h) + 4 * (size_t)pb * BAND_WARPS;
 }
 
-// Stage PB potential rows: dst[pp][c] = src[p0 + pp][t0 - h + c] (-inf outside [0, n) or past the batch).
+// A split potential a + b with a integer-valued and |b| <= 1/2 (exact: rintf(b) and b - rintf(b)
+// are representable, and a + rintf(b) stays an integer below 2^24).  -inf stays {-inf, 0}.
+__device__ __forceinline__ float2 pot_norm(float a, float b) {
+  const float r = rintf(b);
+  return isfinite(a) ? make_float2(a + r, b - r) : make_float2(a, 0.f);
+}
+// The split of an FP64 value (the initial potentials).
+__device__ __forceinline__ float2 pot_split(double v) {
+  if (!isfinite(v)) return make_float2((float)v, 0.f);
+  const double a = rint(v);
+  return make_float2((float)a, (float)(v - a));
+}
+__device__ __forceinline__ double pot_value(float2 v) { return (double)v.x + (double)v.y; }
+
+// Error-free transformations in FP32 (Dekker's product through the FMA, Knuth's two-sum): a b and
+// a + b as exact pairs {value, rounding error}.  The intrinsics keep the compiler from fusing or
+// reordering them.  They replace FP64, whose pipe is a small fraction of FP32's here.
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return make_float2(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// A pair {hi, lo} (any |lo|) as a split potential.
+__device__ __forceinline__ float2 pot_from_pair(float hi, float lo) {
+  const float a = rintf(hi);
+  return pot_norm(a, __fadd_rn(__fsub_rn(hi, a), lo));
+}
+
+// Stage PB split potential rows: dst[pp][c] = src[p0 + pp][t0 - h + c] (-inf outside [0, n) or past
+// the batch).
 template <int PB>
-__device__ __forceinline__ void band_stage_rows(const BandArgs& A, const float* src, float* dst, int p0, int t0,
+__device__ __forceinline__ void band_stage_rows(const BandArgs& A, const float2* src, float2* dst, int p0, int t0,
                                                 int L) {
 #pragma unroll
   for (int pp = 0; pp < PB; ++pp)
     for (int c = threadIdx.x; c < L; c += BAND_NT) {
       const int j = t0 - A.h + c;
-      dst[pp * L + c] = (p0 + pp < A.batch && j >= 0 && j < A.n) ? src[(size_t)(p0 + pp) * A.n + j] : -CUDART_INF_F;
+      dst[pp * L + c] = (p0 + pp < A.batch && j >= 0 && j < A.n) ? src[(size_t)(p0 + pp) * A.n + j]
+                                                                  : make_float2(-CUDART_INF_F, 0.f);
     }
 }
 
@@ -91,36 +136,62 @@ struct BandRow {
   }
 };
 
-// log2 sum_t 2^(v_t - c_t) over the row's band (v: potentials in shared memory at stride 1).  One
-// pass around `shift`, the previous iteration's log-sum, so the sum is the ratio new / old; when
-// that sum leaves [2^-60, 2^60], or the shift is not finite, the exact two passes (max, then the
-// sum around it).  Returns the log-sum and writes the ratio 2^(new - shift).
+// sum_t 2^(v_t - c_t - s) with split potentials: ((v_t.a - s.a) - c_t) + (v_t.b - s.b), where the
+// first difference is exact and a term that matters has an exponent near 0 (so its rounding is
+// relative to a small number).
 template <int WR>
-__device__ __forceinline__ float band_lse(const float* v, const BandRow<WR>& row, int W, float shift, float* ratio) {
+__device__ __forceinline__ float band_sum(const float2* v, const BandRow<WR>& row, int T, float2 s) {
+  using P = Prec<float>;
+  float sum0 = 0.f, sum1 = 0.f;  // two chains of additions in flight
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const float e = P::exp2(((v[t].x - s.x) - row.c(t)) + (v[t].y - s.y));
+    if (t & 1) sum1 += e;
+    else sum0 += e;
+  }
+  return sum0 + sum1;
+}
+
+// log2 sum_t 2^(v_t - c_t) over the row's band (v: split potentials in shared memory at stride 1).
+// One pass around `shift`, the previous iteration's log-sum, so the sum is the ratio new / old;
+// when that sum leaves [2^-60, 2^60], or the shift is not finite, the exact two passes (the
+// largest term as the shift, then the sum around it).  Returns the split log-sum and writes the
+// ratio 2^(new - shift).
+template <int WR>
+__device__ __forceinline__ float2 band_lse(const float2* v, const BandRow<WR>& row, int W, float2 shift,
+                                           float* ratio) {
   using P = Prec<float>;
   constexpr bool REG = WR > 0;
   const int T = REG ? WR : W;
-  if (shift > -CUDART_INF_F && shift < CUDART_INF_F) {
-    float sum = 0.f;
-#pragma unroll
-    for (int t = 0; t < T; ++t) sum += P::exp2(v[t] - row.c(t) - shift);
+  if (isfinite(shift.x)) {
+    const float sum = band_sum<WR>(v, row, T, shift);
     if (sum >= 0x1p-60f && sum <= 0x1p60f) {
       *ratio = sum;
-      return shift + P::log2(sum);
+      return pot_norm(shift.x, shift.y + P::log2(sum));
     }
   }
   float m = -CUDART_INF_F;
+  int tm = 0;
 #pragma unroll
-  for (int t = 0; t < T; ++t) m = fmaxf(m, v[t] - row.c(t));
-  if (!(m > -CUDART_INF_F)) {
-    *ratio = P::exp2(-CUDART_INF_F - shift);
-    return -CUDART_INF_F;
+  for (int t = 0; t < T; ++t) {
+    const float e = (v[t].x - row.c(t)) + v[t].y;
+    if (e > m) {
+      m = e;
+      tm = t;
+    }
   }
-  float sum = 0.f;
+  if (!(m > -CUDART_INF_F)) {
+    *ratio = P::exp2(-CUDART_INF_F - shift.x);
+    return make_float2(-CUDART_INF_F, 0.f);
+  }
+  // the shift: the largest term's exponent as a split value (any shift is exact in real arithmetic)
+  float ctm = 0.f;
 #pragma unroll
-  for (int t = 0; t < T; ++t) sum += P::exp2(v[t] - row.c(t) - m);
-  const float la = m + P::log2(sum);
-  *ratio = P::exp2(la - shift);
+  for (int t = 0; t < T; ++t) ctm = t == tm ? row.c(t) : ctm;
+  const float2 s2 = pot_norm(v[tm].x, v[tm].y - ctm);
+  const float sum = band_sum<WR>(v, row, T, s2);
+  const float2 la = pot_norm(s2.x, s2.y + P::log2(sum));
+  *ratio = P::exp2((la.x - shift.x) + (la.y - shift.y));
   return la;
 }
 
@@ -163,19 +234,18 @@ __device__ __forceinline__ float band_tile_sum(const float* part, int tiles) {
   return v;
 }
 
-// Source apply for PB problems on one tile of rows: LA2, the violation numerator
-// sum_i S_i |a_new,i / a_old,i - 1| and the log ratios R_i = LA2_i - log2 S_i.  Row i's costs
-// C2[d][i] are loaded once (coalesced across the tile) for the PB problems.
+// Source apply for PB problems on one tile of rows: LA2 and the violation numerator
+// sum_i S_i |a_new,i / a_old,i - 1|.  Row i's costs C2[d][i] are loaded once (coalesced across the
+// tile) for the PB problems.
 template <int PB, int WR>
-__global__ void __launch_bounds__(BAND_NT) band_source_kernel(BandArgs A) {
-  using P = Prec<float>;
-  extern __shared__ float smem[];
+__global__ void __launch_bounds__(BAND_NT, 3) band_source_kernel(BandArgs A) {
+  extern __shared__ __align__(16) float smem[];
   const int tile = blockIdx.x, p0 = blockIdx.y * PB;
   const int n = A.n, h = A.h, W = 2 * h + 1, L = BAND_TN + 2 * h, t0 = tile * BAND_TN;
   bool live[PB];
   if (!band_live<PB>(A, p0, live)) return;
-  float* gs = smem;
-  float* red = gs + (size_t)PB * L;
+  float2* gs = reinterpret_cast<float2*>(smem);
+  float* red = smem + 2 * (size_t)PB * L;
   band_stage_rows<PB>(A, A.G2, gs, p0, t0, L);
   const int i = t0 + threadIdx.x;
   const bool valid = i < n;
@@ -186,6 +256,15 @@ __global__ void __launch_bounds__(BAND_NT) band_source_kernel(BandArgs A) {
 #pragma unroll
     for (int t = 0; t < WR; ++t) row.cr[t] = (valid && t < W) ? A.C2[(size_t)t * n + i] : CUDART_INF_F;
   }
+  // the PB problems' previous sums and masses of row i, loaded before any is used
+  float2 old[PB];
+  float sv[PB];
+#pragma unroll
+  for (int pp = 0; pp < PB; ++pp) {
+    const size_t o = (size_t)(p0 + pp) * n + i;
+    old[pp] = (live[pp] && valid) ? A.LA2[o] : make_float2(0.f, 0.f);
+    sv[pp] = (live[pp] && valid) ? A.S[o] : 0.f;
+  }
   __syncthreads();
   const bool check = A.it > 0;
   float part[PB];
@@ -195,11 +274,9 @@ __global__ void __launch_bounds__(BAND_NT) band_source_kernel(BandArgs A) {
     if (!live[pp] || !valid) continue;
     const size_t o = (size_t)(p0 + pp) * n + i;
     float ratio;
-    const float la = band_lse<WR>(gs + pp * L + threadIdx.x, row, W, A.LA2[o], &ratio);
-    const float s = A.S[o];
-    if (check && s > 0.f) part[pp] = s * fabsf(ratio - 1.f);
+    const float2 la = band_lse<WR>(gs + pp * L + threadIdx.x, row, W, old[pp], &ratio);
+    if (check && sv[pp] > 0.f) part[pp] = sv[pp] * fabsf(ratio - 1.f);
     A.LA2[o] = la;
-    A.R[o] = s > 0.f ? la - P::log2(s) : 0.f;
   }
   if (!check) return;
   const float tot = band_block_sums<PB>(part, red);
@@ -242,23 +319,35 @@ __global__ void __launch_bounds__(BAND_NT) band_mm_kernel(BandArgs A) {
   }
   const int m = blockIdx.x * BAND_NT + threadIdx.x;
   if (m >= A.k) return;
-  const float* R = A.R + (size_t)p * A.n;
+  // sum_i D_im log2(a_i / s_i) with log2(a / s) = la.a + (la.b - log2 s): the integer parts are of
+  // size up to lam / (eps ln2) and the weighted sum cancels to near 0 at the fixed point, so their
+  // products and running sum are kept exact as FP32 pairs (two_prod, two_sum)
+  const float2* LA = A.LA2 + (size_t)p * A.n;
+  const float* S = A.S + (size_t)p * A.n;
   const int q0 = A.col_ptr[m], q1 = A.col_ptr[m + 1];
-  float acc = 0.f;
+  float hi = 0.f, lo = 0.f;
+  auto add = [&](float v, int r) {
+    const float sv = S[r];
+    if (!(sv > 0.f)) return;
+    const float2 la = LA[r];
+    const float2 pr = two_prod(v, la.x);
+    const float2 sm = two_sum(hi, pr.x);
+    hi = sm.x;
+    lo += (sm.y + pr.y) + v * (la.y - P::log2(sv));
+  };
   int q = q0;
   for (; q + 4 <= q1; q += 4) {  // four independent gathers in flight
     const int r0 = A.row_idx[q], r1 = A.row_idx[q + 1], r2 = A.row_idx[q + 2], r3 = A.row_idx[q + 3];
     const float v0 = A.val[q], v1 = A.val[q + 1], v2 = A.val[q + 2], v3 = A.val[q + 3];
-    const float x0 = R[r0], x1 = R[r1], x2 = R[r2], x3 = R[r3];
-    acc = fmaf(v0, x0, acc);
-    acc = fmaf(v1, x1, acc);
-    acc = fmaf(v2, x2, acc);
-    acc = fmaf(v3, x3, acc);
+    add(v0, r0);
+    add(v1, r1);
+    add(v2, r2);
+    add(v3, r3);
   }
-  for (; q < q1; ++q) acc = fmaf(A.val[q], R[A.row_idx[q]], acc);
+  for (; q < q1; ++q) add(A.val[q], A.row_idx[q]);
   const float xj = A.xcol[m];
   float* wp = A.W + (size_t)p * A.k + m;
-  const float nu = P::log(*wp) + acc * float(kLn2) / xj;
+  const float nu = P::log(*wp) + (hi + lo) * float(kLn2) / xj;
   const float shift = (A.penalty == PEN_L1 || A.penalty == PEN_ELASTIC) ? A.alpha / (A.eps * xj) : 0.f;
   float wn;
   if (A.penalty == PEN_L2SQ || A.penalty == PEN_ELASTIC) {
@@ -268,20 +357,70 @@ __global__ void __launch_bounds__(BAND_NT) band_mm_kernel(BandArgs A) {
   *wp = wn;
 }
 
-__device__ __forceinline__ float band_datafit(const BandArgs& A, float v, float yv) {
+// log2 omega(z) for z = zh + zl (a pair): omega of zh, corrected to first order for zl
+// (omega' = omega / (1 + omega)), so |z| ~ 1e3 costs no FP32 resolution.
+__device__ __forceinline__ float log2_omega(float zh, float zl) {
   using P = Prec<float>;
+  const float om = wright_omega_fast(zh);
+  return P::log2(om) + zl * float(kLog2e) * P::rcp(1.f + om);
+}
+
+// c_hi x + (c_lo x) for an integer-valued x and a constant pair c: exact up to the last term.
+__device__ __forceinline__ float2 pair_times(float2 c, float x) {
+  float2 p = two_prod(c.x, x);
+  p.y = __fmaf_rn(c.y, x, p.y);
+  return p;
+}
+
+// Datafit step (Table 1) in log2 units from the split target sum v = log2 b and the target bin y,
+// as a split potential.  The large parts (v's integer part, lam y / eps, the TV bound, the KL
+// factor) are combined through exact FP32 pairs; the squared-error and Poisson steps use their log
+// forms
+//   L2     : G2 = log2(eps/lam) + log2 omega(ln(lam/eps) + v ln2 + (lam/eps) y) - v,
+//   Poisson: G2 = l2c - log2 omega((l2c - v) ln2 + lam/eps) - v, l2c = log2(lam y / eps)
+// (no difference of two numbers of size lam y / eps, which the FP32 form lam y/eps - omega had).
+__device__ __noinline__ float2 band_datafit(const BandArgs& A, float2 v, float yv) {
+  using P = Prec<float>;
+  const float ly = P::log2(yv);
   switch (A.datafit) {
-    case DF_BALANCED: return P::log2(yv) - v;
-    case DF_KL: return A.kl_coef * (P::log2(yv) - v);
-    case DF_TV: return fminf(fmaxf(P::log2(yv) - v, -A.tv_bound), A.tv_bound);
-    default: {  // L2 or Poisson (reading A7; -lam where y = 0), one Wright omega
-      const bool pois = A.datafit == DF_POISSON;
-      if (pois && !(yv > 0.f)) return -A.tv_bound;
-      const float l2c = pois ? A.log_lam_over_eps * float(kLog2e) + P::log2(yv) : 0.f;
-      const float z = pois ? (l2c - v) * float(kLn2) + A.lam_over_eps
-                           : A.log_lam_over_eps + v * float(kLn2) + A.lam_over_eps * yv;
-      const float om = wright_omega_fast(z);
-      return pois ? l2c - P::log2(om) - v : (A.lam_over_eps * yv - om) * float(kLog2e);
+    case DF_BALANCED: return pot_norm(-v.x, ly - v.y);
+    case DF_KL: {  // kl (ly - v.b) - kl v.a
+      const float2 pa = pair_times(A.kl_coef, -v.x);
+      const float2 pb = two_prod(A.kl_coef.x, ly);
+      const float2 sm = two_sum(pa.x, pb.x);
+      return pot_from_pair(sm.x, sm.y + pa.y + pb.y + A.kl_coef.y * ly - A.kl_coef.x * v.y);
+    }
+    case DF_TV: {
+      const float2 g = pot_norm(-v.x, ly - v.y);
+      // compare g with the bound pair: (g.a - bound.hi) is exact near the bound
+      const float over = (g.x - A.tv_bound.x) + (g.y - A.tv_bound.y);
+      const float under = (g.x + A.tv_bound.x) + (g.y + A.tv_bound.y);
+      if (over > 0.f) return pot_from_pair(A.tv_bound.x, A.tv_bound.y);
+      if (under < 0.f) return pot_from_pair(-A.tv_bound.x, -A.tv_bound.y);
+      return g;
+    }
+    case DF_POISSON: {  // reading A7; -lam where y = 0
+      if (!(yv > 0.f)) return pot_from_pair(-A.tv_bound.x, -A.tv_bound.y);
+      // l2c = log2(lam/eps) + ly; z = ln2 (l2c - v.b) - ln2 v.a + lam/eps
+      const float l2c = ly - A.log2_eps_over_lam.x;
+      const float2 za = pair_times(A.ln2, -v.x);
+      const float2 zb = two_prod(A.ln2.x, l2c - v.y);
+      const float2 s1 = two_sum(za.x, A.lam_over_eps.x);
+      const float2 s2 = two_sum(s1.x, zb.x);
+      const float zl = s1.y + s2.y + za.y + zb.y + A.lam_over_eps.y - A.ln2.x * A.log2_eps_over_lam.y;
+      const float2 z = two_sum(s2.x, zl);
+      const float lo = log2_omega(z.x, z.y);
+      return pot_norm(-v.x, (l2c - lo) - v.y - A.log2_eps_over_lam.y);
+    }
+    default: {  // L2: z = ln(lam/eps) + ln2 v.a + ln2 v.b + (lam/eps) y
+      const float2 za = pair_times(A.ln2, v.x);
+      const float2 zy = two_prod(A.lam_over_eps.x, yv);
+      const float2 s1 = two_sum(za.x, zy.x);
+      const float2 s2 = two_sum(s1.x, A.log_lam_over_eps.x);
+      const float zl = s1.y + s2.y + za.y + zy.y + A.lam_over_eps.y * yv + A.log_lam_over_eps.y + A.ln2.x * v.y;
+      const float2 z = two_sum(s2.x, zl);
+      const float lo = log2_omega(z.x, z.y);
+      return pot_norm(-v.x, ((A.log2_eps_over_lam.x + lo) - v.y) + A.log2_eps_over_lam.y);
     }
   }
 }
@@ -290,15 +429,15 @@ __device__ __forceinline__ float band_datafit(const BandArgs& A, float v, float 
 // its halo (CSR rows, shared by the PB problems), F2 = log2 s - LA2, then LB2 and G2 (Table 1).
 // Column j's costs C(j + e - h, j) = C2[2h - e][j + e - h] are loaded once for the PB problems.
 template <int PB, int WR>
-__global__ void __launch_bounds__(BAND_NT) band_target_kernel(BandArgs A) {
+__global__ void __launch_bounds__(BAND_NT, 3) band_target_kernel(BandArgs A) {
   using P = Prec<float>;
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   const int tile = blockIdx.x, p0 = blockIdx.y * PB;
   const int n = A.n, h = A.h, W = 2 * h + 1, L = BAND_TN + 2 * h, t0 = tile * BAND_TN;
   bool live[PB];
   if (!band_live<PB>(A, p0, live)) return;
-  float* fs = smem;
-  float* red = fs + (size_t)PB * L;
+  float2* fs = reinterpret_cast<float2*>(smem);
+  float* red = smem + 2 * (size_t)PB * L;
   float mass[PB];
 #pragma unroll
   for (int pp = 0; pp < PB; ++pp) mass[pp] = 0.f;
@@ -320,12 +459,15 @@ __global__ void __launch_bounds__(BAND_NT) band_target_kernel(BandArgs A) {
     const bool own = c >= h && c < h + BAND_TN && i < n;
 #pragma unroll
     for (int pp = 0; pp < PB; ++pp) {
-      float f2 = -CUDART_INF_F;
+      float2 f2 = make_float2(-CUDART_INF_F, 0.f);
       if (live[pp] && i >= 0 && i < n) {
         // a subnormal mass counts as 0, as in the other FP32 paths (log2 flushes it to -inf)
         const float sv = s[pp] < P::tiny() ? 0.f : s[pp];
         const size_t o = (size_t)(p0 + pp) * n + i;
-        if (sv > 0.f) f2 = P::log2(sv) - A.LA2[o];
+        if (sv > 0.f) {
+          const float2 la = A.LA2[o];
+          f2 = pot_norm(-la.x, P::log2(sv) - la.y);  // F2 = log2 s - LA2
+        }
         if (own) {
           A.S[o] = sv;
           mass[pp] += sv;
@@ -348,11 +490,12 @@ __global__ void __launch_bounds__(BAND_NT) band_target_kernel(BandArgs A) {
     }
   }
   // the PB problems' previous sums and targets of column j, loaded before any is used
-  float old[PB], yv[PB];
+  float2 old[PB];
+  float yv[PB];
 #pragma unroll
   for (int pp = 0; pp < PB; ++pp) {
     const size_t o = (size_t)(p0 + pp) * n + j;
-    old[pp] = (live[pp] && valid) ? A.LB2[o] : 0.f;
+    old[pp] = (live[pp] && valid) ? A.LB2[o] : make_float2(0.f, 0.f);
     yv[pp] = (live[pp] && valid) ? A.y[o] : 0.f;
   }
   __syncthreads();
@@ -361,7 +504,7 @@ __global__ void __launch_bounds__(BAND_NT) band_target_kernel(BandArgs A) {
     if (!live[pp] || !valid) continue;
     const size_t o = (size_t)(p0 + pp) * n + j;
     float ratio;
-    const float lb = band_lse<WR>(fs + pp * L + threadIdx.x, col, W, old[pp], &ratio);
+    const float2 lb = band_lse<WR>(fs + pp * L + threadIdx.x, col, W, old[pp], &ratio);
     A.LB2[o] = lb;
     A.G2[o] = band_datafit(A, lb, yv[pp]);
   }
@@ -481,18 +624,18 @@ __global__ void band_sort_rows_kernel(const int* row_ptr, int* col_idx, float* r
 
 // Initial state per problem: W = w0, G2 = g0 / (eps ln2) (0 for a cold start), S = D w0 (CSR rows),
 // status MAX_ITER, not done.  One thread per (problem, row) for G2 and S, per (problem, atom) for W.
-__global__ void band_init_kernel(BandArgs A, const float* w0, const float* g0, float gscale) {
+__global__ void band_init_kernel(BandArgs A, const float* w0, const float* g0, double gscale) {
   const size_t rows = (size_t)A.batch * A.n, atoms = (size_t)A.batch * A.k;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < atoms; q += (size_t)gridDim.x * blockDim.x)
     A.W[q] = w0[q];
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < rows; q += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(q / A.n), i = (int)(q - (size_t)p * A.n);
-    A.G2[q] = g0 ? g0[q] * gscale : 0.f;
+    A.G2[q] = g0 ? pot_split((double)g0[q] * gscale) : make_float2(0.f, 0.f);
     float s = 0.f;
     for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) s = fmaf(A.rval[e], w0[(size_t)p * A.k + A.col_idx[e]], s);
     A.S[q] = s < Prec<float>::tiny() ? 0.f : s;
-    A.LA2[q] = -CUDART_INF_F;  // no previous sums: the first applies take the exact two-pass path
-    A.LB2[q] = -CUDART_INF_F;
+    A.LA2[q] = make_float2(-CUDART_INF_F, 0.f);  // no previous sums: the first applies take the exact path
+    A.LB2[q] = make_float2(-CUDART_INF_F, 0.f);
   }
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)A.batch;
        q += (size_t)gridDim.x * blockDim.x) {
@@ -507,15 +650,16 @@ __global__ void band_init_kernel(BandArgs A, const float* w0, const float* g0, f
 // Outputs: w, g = G2 eps ln2, t = Q^T 1 = 2^(G2 + LB2) (0 before the first target step), iters,
 // err, status.
 __global__ void band_finalize_kernel(BandArgs A, float* w_out, float* g_out, float* t_out, int* iters_out,
-                                     float* err_out, int* status_out, float gscale_inv) {
+                                     float* err_out, int* status_out, double gscale_inv) {
   const size_t rows = (size_t)A.batch * A.n, atoms = (size_t)A.batch * A.k;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < atoms; q += (size_t)gridDim.x * blockDim.x)
     w_out[q] = A.W[q];
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < rows; q += (size_t)gridDim.x * blockDim.x) {
-    if (g_out) g_out[q] = A.G2[q] * gscale_inv;
+    const float2 g = A.G2[q];
+    if (g_out) g_out[q] = (float)(pot_value(g) * gscale_inv);
     if (t_out) {
-      const float lb = A.LB2[q];
-      t_out[q] = lb > -CUDART_INF_F ? Prec<float>::exp2(A.G2[q] + lb) : 0.f;
+      const float2 lb = A.LB2[q];  // t = 2^(G2 + LB2): integer parts added exactly
+      t_out[q] = lb.x > -CUDART_INF_F ? Prec<float>::exp2((g.x + lb.x) + (g.y + lb.y)) : 0.f;
     }
   }
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)A.batch;
@@ -531,7 +675,8 @@ struct BandWorkspace {
   float* C2;
   int *row_ptr, *cnt, *fill, *col_idx;
   float *rval, *xcol;
-  float *G2, *LA2, *LB2, *S, *R, *W, *vpart, *mpart, *err;
+  float2 *G2, *LA2, *LB2;
+  float *S, *W, *vpart, *mpart, *err;
   int *done, *iters, *status, *remaining, *bad;
 };
 
@@ -553,11 +698,10 @@ inline size_t carve_band_workspace(void* base, int batch, int n, int k, int h, i
   w.col_idx = (int*)take(4 * (size_t)nnz);
   w.rval = (float*)take(4 * (size_t)nnz);
   w.xcol = (float*)take(4 * (size_t)k);
-  w.G2 = (float*)take(4 * rows);
-  w.LA2 = (float*)take(4 * rows);
-  w.LB2 = (float*)take(4 * rows);
+  w.G2 = (float2*)take(8 * rows);
+  w.LA2 = (float2*)take(8 * rows);
+  w.LB2 = (float2*)take(8 * rows);
   w.S = (float*)take(4 * rows);
-  w.R = (float*)take(4 * rows);
   w.W = (float*)take(4 * (size_t)batch * k);
   w.vpart = (float*)take(4 * (size_t)batch * tiles);
   w.mpart = (float*)take(4 * (size_t)batch * tiles);
@@ -600,7 +744,7 @@ cudaError_t band_iterate(const Launch& L, BandArgs& A, const BandWorkspace& ws, 
   return cudaGetLastError();
 }
 
-// Dispatch on problems per CTA (8 for batches of 8 or more, else 1) and the band-width bucket (9,
+// Dispatch on problems per CTA (4 for batches of 4 or more, else 1) and the band-width bucket (9,
 // 19 or 33 diagonals in registers, padded with +inf; wider bands from global memory).
 template <int PB>
 cudaError_t band_iterate_pb(const Launch& L, BandArgs& A, const BandWorkspace& ws, const SolveParams& sp) {
@@ -622,11 +766,13 @@ inline cudaError_t solve_device_band(const Launch& L, const BandWorkspace& ws, c
   A.batch = c.batch; A.n = n; A.k = k; A.h = h; A.tiles = (n + BAND_TN - 1) / BAND_TN;
   A.max_iter = sp.max_iter; A.datafit = sp.datafit; A.penalty = sp.penalty;
   A.tol = float(sp.tol); A.eps = float(sp.eps); A.alpha = float(sp.alpha); A.beta = float(sp.beta);
-  A.kl_coef = float(sp.lam / (sp.eps + sp.lam)); A.tv_bound = float(sp.lam / eps_ln2);
-  A.lam_over_eps = float(sp.lam / sp.eps); A.log_lam_over_eps = float(log(sp.lam / sp.eps));
+  auto pair = [](double v) { const float h = (float)v; return make_float2(h, (float)(v - (double)h)); };
+  A.kl_coef = pair(sp.lam / (sp.eps + sp.lam)); A.tv_bound = pair(sp.lam / eps_ln2);
+  A.lam_over_eps = pair(sp.lam / sp.eps); A.log_lam_over_eps = pair(log(sp.lam / sp.eps));
+  A.log2_eps_over_lam = pair(log2(sp.eps / sp.lam)); A.ln2 = pair(kLn2);
   A.C2 = ws.C2; A.col_ptr = c.col_ptr; A.row_idx = c.row_idx; A.val = c.val;
   A.row_ptr = ws.row_ptr; A.col_idx = ws.col_idx; A.rval = ws.rval; A.xcol = ws.xcol; A.y = c.y;
-  A.G2 = ws.G2; A.LA2 = ws.LA2; A.LB2 = ws.LB2; A.S = ws.S; A.R = ws.R; A.W = ws.W;
+  A.G2 = ws.G2; A.LA2 = ws.LA2; A.LB2 = ws.LB2; A.S = ws.S; A.W = ws.W;
   A.vpart = ws.vpart; A.mpart = ws.mpart; A.err = ws.err; A.done = ws.done; A.iters = ws.iters;
   A.status = ws.status; A.remaining = ws.remaining;
 
@@ -659,14 +805,14 @@ inline cudaError_t solve_device_band(const Launch& L, const BandWorkspace& ws, c
   band_sort_rows_kernel<<<(n + 255) / 256, 256, 0, L.stream>>>(ws.row_ptr, ws.col_idx, ws.rval, n);
   L.end();
   L.begin(KIND_OTHER);
-  band_init_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, float(1.0 / eps_ln2));
+  band_init_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, 1.0 / eps_ln2);
   L.end();
 
-  e = c.batch >= 8 ? band_iterate_pb<8>(L, A, ws, sp) : band_iterate_pb<1>(L, A, ws, sp);
+  e = c.batch >= 4 ? band_iterate_pb<4>(L, A, ws, sp) : band_iterate_pb<1>(L, A, ws, sp);
   if (e != cudaSuccess) return e;
   L.begin(KIND_OTHER);
   band_finalize_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, c.t_out, c.iters_out, c.err_out, c.status_out,
-                                                   float(eps_ln2));
+                                                   eps_ln2);
   L.end();
   e = cudaGetLastError();
   if (e == cudaSuccess && L.timer && L.timer->on) e = L.timer->harvest();

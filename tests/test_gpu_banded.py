@@ -4,12 +4,10 @@ scalability test (App. "Performance Scalability Tests": x_i = i, cost rho |x_i -
 samples, k = n / 10 truncated Gaussians, lam = 1, alpha = eps = 1e-3) and on a non-symmetric
 truncated cost with holes.
 
-Bar: relative L1 1e-5 in w and t = Q^T 1, as for the other FP32 paths, except where the potentials
-themselves limit FP32: at eps = 1e-3 the target potential g / (eps ln2) reaches about
-lam / (eps ln2) = 1443 log2 units (TV clamp) and, for the squared-error datafit, the difference of
-two terms of that size, so its FP32 rounding alone is 1443 x 2^-24 ~ 9e-5 log2 units, a relative
-6e-5 in u1 = 2^(g / (eps ln2)).  Those cases carry a bar of 3e-4 (a few such roundings), stated
-beside them."""
+Bar: relative L1 1e-5 in w and t = Q^T 1, as for the other FP32 paths, at every eps including the
+scalability test's 1e-3, where the log2 potentials reach lam / (eps ln2) = 1443: the kernels carry
+them as split pairs (an integer-valued part and a fraction) so that FP32 rounding acts on numbers of
+the size of the result, and take the datafit step and the MM sum through FP64."""
 import numpy as np
 import pytest
 
@@ -23,7 +21,6 @@ from paper_2504_04609_gb300 import otlm as api  # noqa: E402
 from scipy.sparse import csc_matrix  # noqa: E402
 
 TOL32 = 1e-5
-TOL_EPS1E3 = 3e-4
 
 
 def rel_l1(a, b):
@@ -69,22 +66,22 @@ def _oracle(d, p, datafit, penalty, eps, lam, alpha, iters, tol=0.0, beta=0.0):
                                    penalty, _w0(y, d["x_col"]), iters, tol=tol, beta=beta)
 
 
-@pytest.mark.parametrize("datafit,penalty,bar", [
-    ("l2", "l2sq", TOL_EPS1E3),   # OT ridge of the scalability test (potentials near 1e3 log2 units)
-    ("tv", "l1", TOL_EPS1E3),     # OT-TV of the scalability test (TV clamp at 1443 log2 units)
-    ("kl", "elastic", TOL32),
-    ("poisson", "l1", TOL_EPS1E3),  # Poisson at eps = 1e-3: potentials up to lam / (eps ln2) as for TV
+@pytest.mark.parametrize("datafit,penalty", [
+    ("l2", "l2sq"),       # OT ridge of the scalability test (potentials near 1e3 log2 units)
+    ("tv", "l1"),         # OT-TV of the scalability test (TV clamp at 1443 log2 units)
+    ("kl", "elastic"),
+    ("poisson", "l1"),    # Poisson at eps = 1e-3: potentials up to lam / (eps ln2) as for TV
 ])
-def test_scalability_inputs_trajectory_parity(datafit, penalty, bar):
-    """3 targets (two groups of 2 per CTA, the second one short), n = 2300 (nine 256-bin tiles, the
+def test_scalability_inputs_trajectory_parity(datafit, penalty):
+    """5 targets (a group of 4 per CTA and a short group of 1), n = 2300 (nine 256-bin tiles, the
     last ragged), k = 230, hw = 9, eps = alpha = 1e-3, 40 iterations."""
-    d = spectra.scaling_batch(61, 3, 2300)
+    d = spectra.scaling_batch(61, 5, 2300)
     r = _gpu(d, datafit, penalty, 1e-3, 1.0, 1e-3, 40, beta=2e-3)
     assert np.all(r["iters"] == 40) and np.all(r["status"] == api.MAX_ITER)
-    for p in range(3):
+    for p in range(5):
         o = _oracle(d, p, datafit, penalty, 1e-3, 1.0, 1e-3, 40, beta=2e-3)
         ew, et = rel_l1(r["w"][p], o["w"]), rel_l1(r["t"][p], o["t"])
-        assert ew <= bar and et <= bar, (p, ew, et)
+        assert ew <= TOL32 and et <= TOL32, (p, ew, et)
 
 
 @pytest.mark.parametrize("datafit,penalty", [("l2", "l2sq"), ("tv", "l1"), ("kl", "l1")])
@@ -106,16 +103,23 @@ def test_nonsymmetric_truncated_cost_with_holes(datafit, penalty):
         assert ew <= TOL32 and et <= TOL32, (p, ew, et)
 
 
-def test_full_size_n100000_trajectory_parity():
-    """The measured configuration: 32 targets at n = 100000, k = 10000, OT ridge; after 15
-    iterations two of the targets are compared with the oracle's banded solve."""
+def test_full_size_n100000_to_tolerance():
+    """The measured configuration: 32 targets at n = 100000, k = 10000, OT ridge, solved to the
+    1e-5 tolerance as the benchmark solves them (about 700 iterations).  Target 0 is compared with
+    the oracle's banded solve run for the GPU's own iteration count, and its stop with the oracle's
+    stop under the same rule (equal, or one apart where the oracle's violation at the deciding
+    iteration lies within 1 % of tol)."""
     d = spectra.scaling_batch(7, 32, 100000)
-    r = _gpu(d, "l2", "l2sq", 1e-3, 1.0, 1e-3, 15)
-    assert np.all(r["iters"] == 15)
-    for p in (0, 31):
-        o = _oracle(d, p, "l2", "l2sq", 1e-3, 1.0, 1e-3, 15)
-        ew, et = rel_l1(r["w"][p], o["w"]), rel_l1(r["t"][p], o["t"])
-        assert ew <= TOL_EPS1E3 and et <= TOL_EPS1E3, (p, ew, et)
+    r = _gpu(d, "l2", "l2sq", 1e-3, 1.0, 1e-3, 2000, tol=1e-5, poll_every=16)
+    assert np.all(r["status"] == api.CONVERGED)
+    gi = int(r["iters"][0])
+    o = _oracle(d, 0, "l2", "l2sq", 1e-3, 1.0, 1e-3, gi + 1, tol=1e-5)
+    if gi != o["iters"]:
+        near = np.abs(o["err_hist"] / 1e-5 - 1) < 1e-2
+        assert abs(gi - o["iters"]) == 1 and near.any(), (gi, o["iters"])
+        o = _oracle(d, 0, "l2", "l2sq", 1e-3, 1.0, 1e-3, gi)
+    ew, et = rel_l1(r["w"][0], o["w"]), rel_l1(r["t"][0], o["t"])
+    assert ew <= TOL32 and et <= TOL32, (gi, ew, et)
 
 
 def test_stopping_rule_matches_oracle():
@@ -174,7 +178,7 @@ def test_invalid_inputs_are_refused():
 @pytest.mark.parametrize("delta,B", [(41.0, 5), (41.0, 9), (4.0, 9), (15.0, 9), (10.0, 1)])
 def test_band_buckets_and_problem_groups(delta, B):
     """Every band-width bucket (half-width 3: 9 diagonals in registers; 9: 19; 14: 33; 40: read
-    from global memory) with one problem per CTA (B < 8) and eight (B = 9: the second group one
+    from global memory) with one problem per CTA (B < 4) and four (B = 5, 9: a last group of one
     problem), n = 700 (a ragged third tile), eps = 5e-2 so that the far diagonals carry weight."""
     n, k = 700, 70
     Cd, h = spectra.truncated_cost_band(n, rho=0.01, delta=delta)
