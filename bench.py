@@ -607,7 +607,7 @@ def run_ragged(args, rank, world, local_rank, pool=None):
     stream = torch.cuda.current_stream(dev)
     h = api.Handle(4096, 128, B, "fp32", c["datafit"], c["penalty"], c["iters"], c["tol"],
                    stream=stream.cuda_stream)
-    cta = h.tune_ragged(rb, c["lam"], c["alpha"], w0, sample_every=40, iters=6)
+    cta, rows_tab = h.tune_ragged(rb, c["lam"], c["alpha"], w0, sample_every=40, iters=6, with_rows=True)
     w = torch.empty_like(w0)
     t = torch.empty_like(rb.y)
     iters = torch.empty(B, dtype=torch.int32, device=dev)
@@ -687,6 +687,7 @@ def run_ragged(args, rank, world, local_rank, pool=None):
         "config": {"workload": args.workload, "problems_per_gpu": B, "n": "U{256..4096}", "k": "U{8..128}",
                    "eps": "logU[2e-3, 5e-2]", "datafit": c["datafit"], "penalty": c["penalty"], "lam": c["lam"],
                    "alpha": c["alpha"], "tol": c["tol"], "cta_threads_tuned": cta,
+                   "rows_per_thread_log2_by_bucket": rows_tab,
                    "l2": "inputs larger than L2 (dictionaries 6 GB)",
                    "converged": int(np.sum(st_np == 0)), "iters_p50": float(np.percentile(it_np, 50)),
                    "iters_p99": float(np.percentile(it_np, 99)), "iters_mean": float(it_np.mean())},

@@ -117,6 +117,11 @@ typedef struct otlm_config {
                           ||w_new - w_old||_1 / ||w_new||_1 <= dw_tol (the weights converge far more
                           slowly than the marginals: reading A8).  otlm_solve, otlm_solve_cost,
                           otlm_solve_host only.                                                  */
+  /* Tile shapes of otlm_solve_ragged, as otlm_tune_ragged reports them (0 everywhere = defaults) */
+  int    ragged_cta;   /* threads per CTA: 128, 256 or 512; 0 = 256                             */
+  int    ragged_rows_log2[16];  /* rows per thread for problems with n in (256 b, 256 (b + 1)],
+                          b = 0..15 (the last bucket also takes larger n), as log2: 1..5 (2..32 rows),
+                          raised where needed to cover n; 0 = the fewest that cover n          */
 } otlm_config;
 
 typedef struct otlm_ctx* otlm_handle;
@@ -128,8 +133,8 @@ typedef struct otlm_ctx* otlm_handle;
  * and 20 batch_max bytes).
  * Errors: OTLM_EINVAL (null pointers, sizes out of range, unknown enum, ELASTIC without a
  * finite beta > 0, mm_steps outside 0..64, check_every < 0, gap_tol or dw_tol negative or not
- * finite, gap_tol > 0 with check_every == 0), OTLM_ENOMEM, OTLM_ECUDA.  On error *h is set to
- * NULL. */
+ * finite, gap_tol > 0 with check_every == 0, ragged_cta not 0/128/256/512, a ragged_rows_log2
+ * entry outside 0..5), OTLM_ENOMEM, OTLM_ECUDA.  On error *h is set to NULL. */
 int otlm_create(otlm_handle* h, const otlm_config* cfg, void* cuda_stream);
 
 /* Release the workspace.  Waits for the handle's stream.  NULL is ignored. */
@@ -236,14 +241,21 @@ int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, cons
                       float* w, float* g, float* t_out, int* iters_out, float* err_out,
                       int* status_out);
 
-/* Autotuner for otlm_solve_ragged (the paper has no counterpart): times each CTA size (128, 256,
- * 512 threads) on every sample_every-th problem of the largest-first order for `iters`
- * iterations, keeps the fastest on the handle and writes its thread count to *cta_threads_out.
- * Caller buffers are not modified (w is copied).  Same argument rules as otlm_solve_ragged. */
+/* Autotuner for otlm_solve_ragged (the paper has no counterpart): chooses the tile shape of the
+ * persistent kernel, i.e. the CTA size (128, 256 or 512 threads) and, for each size bucket of
+ * otlm_config.ragged_rows_log2, the rows each thread owns (more rows reuse each staged column for
+ * more exponentials; fewer keep more threads busy).  Every sample_every-th problem of the
+ * largest-first order joins its bucket's sample; for each CTA size, each bucket times its feasible
+ * choices (the fewest rows that cover the bucket and up to four times as many) on its sample
+ * repeated over two waves of CTAs, `iters` iterations each, and keeps the fastest; the CTA size
+ * with the smallest total wins.  The choice is kept on the handle; *cta_threads_out (may be NULL)
+ * and rows_log2_out [16] (may be NULL) receive it in otlm_config's form, so that a later
+ * otlm_create can take it without tuning.  Caller buffers are not modified (w is copied).  Same
+ * argument rules as otlm_solve_ragged. */
 int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
                      const long long* off_n, const long long* off_D, const long long* off_k,
                      const float* x, const float* D, const float* y, double lam, double alpha,
-                     const float* w, int sample_every, int iters, int* cta_threads_out);
+                     const float* w, int sample_every, int iters, int* cta_threads_out, int* rows_log2_out);
 
 /* ---- learned warm start (an extension: the paper starts every solve from u1 = 1) -------------
  * A 4-layer MLP maps a target y [n] to an initial state for Algorithm 1: features

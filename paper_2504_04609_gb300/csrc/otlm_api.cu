@@ -40,6 +40,7 @@ struct otlm_ctx {
   cudaGraphExec_t rg_exec = nullptr;
   unsigned char rg_key[sizeof(otlm::RaggedArgs) + 2 * sizeof(int)] = {};
   int rg_variant = 1;              // CTA size chosen by otlm_tune_ragged (default 256 threads)
+  unsigned char rg_rows[otlm::RAGGED_BUCKETS] = {};  // log2 rows per thread by size bucket (0: fewest)
   long long rg_tot[3] = {0, 0, 0}; // packed sizes sum n, sum n k, sum k of the last batch
   // banded path (allocated on first use, grown when a call needs more)
   void* bd = nullptr;
@@ -54,7 +55,9 @@ bool valid_enum(const otlm_config& c) {
          (c.penalty >= OTLM_PENALTY_NONE && c.penalty <= OTLM_PENALTY_ELASTIC) &&
          (c.penalty != OTLM_PENALTY_ELASTIC || (c.beta > 0 && std::isfinite(c.beta))) &&
          c.mm_steps >= 0 && c.mm_steps <= 64 && c.check_every >= 0 && c.gap_tol >= 0 && std::isfinite(c.gap_tol) &&
-         c.dw_tol >= 0 && std::isfinite(c.dw_tol) && (c.gap_tol == 0 || c.check_every > 0);
+         c.dw_tol >= 0 && std::isfinite(c.dw_tol) && (c.gap_tol == 0 || c.check_every > 0) &&
+         (c.ragged_cta == 0 || c.ragged_cta == 128 || c.ragged_cta == 256 || c.ragged_cta == 512) &&
+         std::all_of(c.ragged_rows_log2, c.ragged_rows_log2 + 16, [](int v) { return v >= 0 && v <= 5; });
 }
 
 // Byte offsets of the workspace parts: the solver state, then (tensor-core handles) the GEMM
@@ -147,7 +150,8 @@ int run_objective(otlm_ctx* h, const SolveParams& sp, const void* x, const void*
 // header's contract), so every problem's range must lie inside them; the kernel repeats the check
 // as a backstop.
 int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps, const long long* off_n,
-                 const long long* off_D, const long long* off_k, std::vector<int>* order) {
+                 const long long* off_D, const long long* off_k, std::vector<int>* order,
+                 std::vector<int>* n_host = nullptr) {
   const otlm_config& c = h->cfg;
   if (c.precision != OTLM_PREC_FP32_LOG || c.check_every > 0 || c.dw_tol > 0) return OTLM_EUNSUPPORTED;
   if (batch < 1 || batch > c.batch_max || c.n_max > 4096) return OTLM_EINVAL;
@@ -175,6 +179,7 @@ int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float
         hok[p] > tk - hk[p])
       return OTLM_EINVAL;
   h->rg_tot[0] = tn; h->rg_tot[1] = tD; h->rg_tot[2] = tk;
+  if (n_host) *n_host = hn;
   order->resize(batch);
   for (int p = 0; p < batch; ++p) (*order)[p] = p;
   std::stable_sort(order->begin(), order->end(),
@@ -196,7 +201,8 @@ int ragged_run(otlm_ctx* h, const otlm::RaggedArgs& a0, int variant, bool use_gr
   size_t smem = 0;
   if (otlm::ragged_prepare(variant, h->cfg.n_max, h->cfg.k_max, &bps, &smem) != cudaSuccess || bps < 1)
     return OTLM_ECUDA;
-  otlm::RaggedArgs a = a0;
+  otlm::RaggedArgs a;
+  std::memcpy(&a, &a0, sizeof(a));  // padding included: the struct's bytes key the cached graph
   a.smem_floats = (int)(smem / 4);
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -244,11 +250,12 @@ int ragged_run(otlm_ctx* h, const otlm::RaggedArgs& a0, int variant, bool use_gr
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
 }
 
-otlm::RaggedArgs ragged_args(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps,
-                             const long long* off_n, const long long* off_D, const long long* off_k, const float* x,
-                             const float* D, const float* y, double lam, double alpha, float* w, float* g,
-                             float* t_out, int* iters_out, float* err_out, int* status_out) {
-  otlm::RaggedArgs a{};
+void ragged_args(otlm_ctx* h, int batch, const int* n, const int* k, const float* eps, const long long* off_n,
+                 const long long* off_D, const long long* off_k, const float* x, const float* D, const float* y,
+                 double lam, double alpha, float* w, float* g, float* t_out, int* iters_out, float* err_out,
+                 int* status_out, otlm::RaggedArgs* out) {
+  otlm::RaggedArgs& a = *out;
+  std::memset(&a, 0, sizeof(a));
   a.batch = batch; a.order = h->rg_order; a.next = h->rg_order + h->cfg.batch_max;
   a.n = n; a.k = k; a.eps = eps; a.off_n = off_n; a.off_D = off_D; a.off_k = off_k;
   a.x = x; a.D = D; a.y = y; a.w = w; a.g_in = g; a.g_out = g; a.t_out = t_out;
@@ -258,7 +265,7 @@ otlm::RaggedArgs ragged_args(otlm_ctx* h, int batch, const int* n, const int* k,
   a.beta = (float)h->cfg.beta; a.mm_steps = h->cfg.mm_steps > 1 ? h->cfg.mm_steps : 1;
   a.n_max = h->cfg.n_max; a.k_max = h->cfg.k_max;
   a.tot_n = h->rg_tot[0]; a.tot_D = h->rg_tot[1]; a.tot_k = h->rg_tot[2];
-  return a;
+  std::memcpy(a.rows_log2, h->rg_rows, sizeof(a.rows_log2));
 }
 
 }  // namespace
@@ -278,6 +285,8 @@ int otlm_create(otlm_handle* out, const otlm_config* cfg, void* cuda_stream) {
   if (!h) return OTLM_ENOMEM;
   h->cfg = c;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->rg_variant = c.ragged_cta == 128 ? 0 : (c.ragged_cta == 512 ? 2 : 1);
+  for (int b = 0; b < otlm::RAGGED_BUCKETS; ++b) h->rg_rows[b] = (unsigned char)c.ragged_rows_log2[b];
   h->elem = c.precision == OTLM_PREC_FP64 ? 8 : 4;
   if (cudaMalloc(&h->ws, workspace_bytes(c)) != cudaSuccess) {
     delete h;
@@ -442,8 +451,9 @@ int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, cons
   if (cudaMemcpyAsync(h->rg_order, order.data(), sizeof(int) * batch, cudaMemcpyHostToDevice, h->stream) !=
       cudaSuccess)
     return OTLM_ECUDA;
-  const otlm::RaggedArgs a = ragged_args(h, batch, n, k, eps, off_n, off_D, off_k, x, D, y, lam, alpha, w, g, t_out,
-                                         iters_out, err_out, status_out);
+  otlm::RaggedArgs a;
+  ragged_args(h, batch, n, k, eps, off_n, off_D, off_k, x, D, y, lam, alpha, w, g, t_out, iters_out, err_out,
+              status_out, &a);
   rc = ragged_run(h, a, h->rg_variant, true);
   if (rc == OTLM_OK && h->timer.on && cudaStreamSynchronize(h->stream) == cudaSuccess) h->timer.harvest();
   return rc;
@@ -452,15 +462,16 @@ int otlm_solve_ragged(otlm_handle h, int batch, const int* n, const int* k, cons
 int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const float* eps,
                      const long long* off_n, const long long* off_D, const long long* off_k, const float* x,
                      const float* D, const float* y, double lam, double alpha, const float* w, int sample_every,
-                     int iters, int* cta_threads_out) {
+                     int iters, int* cta_threads_out, int* rows_log2_out) {
   if (!h || !n || !k || !eps || !off_n || !off_D || !off_k || !x || !D || !y || !w || sample_every < 1 || iters < 1)
     return OTLM_EINVAL;
-  std::vector<int> order;
-  int rc = ragged_setup(h, batch, n, k, eps, off_n, off_D, off_k, &order);
+  std::vector<int> order, hn;
+  int rc = ragged_setup(h, batch, n, k, eps, off_n, off_D, off_k, &order, &hn);
   if (rc != OTLM_OK) return rc;
-  // sample: every sample_every-th problem of the work order (so the sample spans the sizes)
-  std::vector<int> sample;
-  for (int i = 0; i < batch; i += sample_every) sample.push_back(order[i]);
+  // sample: every sample_every-th problem of the work order (so the sample spans the sizes),
+  // grouped by size bucket
+  std::vector<std::vector<int>> by_bucket(otlm::RAGGED_BUCKETS);
+  for (int i = 0; i < batch; i += sample_every) by_bucket[otlm::ragged_bucket(hn[order[i]])].push_back(order[i]);
   // the weights' packed length sum k (the setup checked every problem's range against it)
   const size_t wn = (size_t)h->rg_tot[2];
   float *wtmp = nullptr, *etmp = nullptr;
@@ -471,26 +482,69 @@ int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const
             cudaMalloc(&itmp, sizeof(int) * batch) == cudaSuccess &&
             cudaMalloc(&stmp, sizeof(int) * batch) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
             cudaEventCreate(&e1) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(h->rg_order, sample.data(), sizeof(int) * sample.size(), cudaMemcpyHostToDevice,
-                             h->stream) == cudaSuccess;
+  int sms = 0, dev = 0;
+  ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
   const int saved_iter = h->cfg.max_iter;
   const double saved_tol = h->cfg.tol;
+  unsigned char saved_rows[otlm::RAGGED_BUCKETS];
+  std::memcpy(saved_rows, h->rg_rows, sizeof(saved_rows));
   h->cfg.max_iter = iters;
   h->cfg.tol = 0.0;
-  float best = 1e30f;
-  int best_v = h->rg_variant;
-  for (int v = 0; ok && v < otlm::RAGGED_VARIANTS; ++v) {
-    otlm::RaggedArgs a = ragged_args(h, (int)sample.size(), n, k, eps, off_n, off_D, off_k, x, D, y, lam, alpha,
-                                     wtmp, nullptr, nullptr, itmp, etmp, stmp);
-    for (int rep = 0; ok && rep < 2; ++rep) {  // the first run warms up
-      ok = cudaMemcpyAsync(wtmp, w, sizeof(float) * wn, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess &&
-           cudaEventRecord(e0, h->stream) == cudaSuccess && ragged_run(h, a, v, false) == OTLM_OK &&
-           cudaEventRecord(e1, h->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+  // Time one bucket with one table: the bucket's sampled problems repeated to fill two waves of
+  // CTAs (a throughput measure, as in the full launch; the repeats write the tuner's own buffers).
+  auto time_bucket = [&](int v, const std::vector<int>& probs, float* ms_out) -> bool {
+    int bps = 0;
+    size_t smem = 0;
+    if (otlm::ragged_prepare(v, h->cfg.n_max, h->cfg.k_max, &bps, &smem) != cudaSuccess || bps < 1) return false;
+    const int len = std::min(h->cfg.batch_max, std::max((int)probs.size(), 2 * sms * bps));
+    std::vector<int> list(len);
+    for (int i = 0; i < len; ++i) list[i] = probs[i % probs.size()];
+    otlm::RaggedArgs a;
+    ragged_args(h, len, n, k, eps, off_n, off_D, off_k, x, D, y, lam, alpha, wtmp, nullptr, nullptr, itmp, etmp,
+                stmp, &a);
+    bool good = true;
+    for (int rep = 0; good && rep < 2; ++rep) {  // the first run warms up
+      good = cudaMemcpyAsync(h->rg_order, list.data(), sizeof(int) * len, cudaMemcpyHostToDevice, h->stream) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(wtmp, w, sizeof(float) * wn, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess &&
+             cudaEventRecord(e0, h->stream) == cudaSuccess && ragged_run(h, a, v, false) == OTLM_OK &&
+             cudaEventRecord(e1, h->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
     }
-    float ms = 0.f;
-    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
-      best = ms;
+    return good && cudaEventElapsedTime(ms_out, e0, e1) == cudaSuccess;
+  };
+  float best_total = 1e30f;
+  int best_v = h->rg_variant;
+  unsigned char best_rows[otlm::RAGGED_BUCKETS] = {};
+  for (int v = 0; ok && v < otlm::RAGGED_VARIANTS; ++v) {
+    const int nt = otlm::ragged_nt(v), rmax_l = otlm::ragged_rmax_log2(v);
+    unsigned char rows[otlm::RAGGED_BUCKETS] = {};
+    float total = 0.f;
+    for (int b = 0; ok && b < otlm::RAGGED_BUCKETS; ++b) {
+      if (by_bucket[b].empty()) continue;
+      int nmax = 0;
+      for (int p : by_bucket[b]) nmax = std::max(nmax, hn[p]);
+      int need_l = 1;  // the fewest rows per thread that cover every sampled size (at least 2)
+      while ((1 << need_l) * nt < nmax) ++need_l;
+      float best_b = 1e30f;
+      int best_l = need_l;
+      for (int l = need_l; ok && l <= std::min(need_l + 2, rmax_l); ++l) {
+        std::memcpy(h->rg_rows, rows, sizeof(rows));
+        h->rg_rows[b] = (unsigned char)l;
+        float ms = 0.f;
+        ok = time_bucket(v, by_bucket[b], &ms);
+        if (ok && ms < best_b) {
+          best_b = ms;
+          best_l = l;
+        }
+      }
+      rows[b] = (unsigned char)best_l;
+      total += best_b;
+    }
+    if (ok && total < best_total) {
+      best_total = total;
       best_v = v;
+      std::memcpy(best_rows, rows, sizeof(rows));
     }
   }
   h->cfg.max_iter = saved_iter;
@@ -498,13 +552,19 @@ int otlm_tune_ragged(otlm_handle h, int batch, const int* n, const int* k, const
   cudaFree(wtmp); cudaFree(etmp); cudaFree(itmp); cudaFree(stmp);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  if (!ok) return OTLM_ECUDA;
+  if (!ok) {
+    std::memcpy(h->rg_rows, saved_rows, sizeof(saved_rows));
+    return OTLM_ECUDA;
+  }
   h->rg_variant = best_v;
+  std::memcpy(h->rg_rows, best_rows, sizeof(best_rows));
   if (h->rg_exec) {  // the cached graph was built for the previous order buffer contents / variant
     cudaGraphExecDestroy(h->rg_exec);
     h->rg_exec = nullptr;
   }
   if (cta_threads_out) *cta_threads_out = otlm::ragged_nt(best_v);
+  if (rows_log2_out)
+    for (int b = 0; b < otlm::RAGGED_BUCKETS; ++b) rows_log2_out[b] = best_rows[b];
   return OTLM_OK;
 }
 

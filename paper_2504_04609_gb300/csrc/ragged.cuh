@@ -45,7 +45,13 @@ struct RaggedArgs {
   int n_max, k_max;
   long long tot_n, tot_D, tot_k;  // packed sizes of x/y, D and w (sum n, sum n k, sum k)
   int smem_floats;                // dynamic shared memory of the launch, in floats
+  // rows per thread by size bucket (n in (256 b, 256 (b + 1)]), as log2 R; raised to the fewest
+  // that cover n with this CTA size (0: always the fewest)
+  unsigned char rows_log2[16];
 };
+
+constexpr int RAGGED_BUCKETS = 16;
+__host__ __device__ inline int ragged_bucket(int n) { return n <= 256 ? 0 : (n - 1) / 256 < 15 ? (n - 1) / 256 : 15; }
 
 template <int NT>
 struct RaggedSmem {
@@ -352,7 +358,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ragged_kernel(RaggedArg
     if (idx >= A.batch) break;
     const int p = A.order[idx];
     const int n = A.n[p];
-    const int rows = (n + NT - 1) / NT;  // rows per thread needed
+    // rows per thread: the tuned choice for n's size bucket, at least the fewest that cover n
+    // (more rows per thread amortise each column's shared-memory reads over more exponentials,
+    // fewer keep more threads busy)
+    const int need = (n + NT - 1) / NT;
+    int rows = 1 << (A.rows_log2[ragged_bucket(n)] > 0 ? A.rows_log2[ragged_bucket(n)] : 1);
+    while (rows < need) rows <<= 1;
     if (rows <= 2) ragged_solve_one<NT, 2>(A, p, sm);
     else if (RMAX >= 4 && rows <= 4) ragged_solve_one<NT, (RMAX >= 4 ? 4 : 2)>(A, p, sm);
     else if (RMAX >= 8 && rows <= 8) ragged_solve_one<NT, (RMAX >= 8 ? 8 : 2)>(A, p, sm);
@@ -373,6 +384,7 @@ namespace otlm {
 // Variants the tuner chooses among: CTA size NT with rows per thread up to RMAX (n <= 4096).
 constexpr int RAGGED_VARIANTS = 3;
 inline int ragged_nt(int v) { return v == 0 ? 128 : (v == 1 ? 256 : 512); }
+inline int ragged_rmax_log2(int v) { return v == 0 ? 5 : (v == 1 ? 4 : 3); }
 
 inline cudaError_t ragged_prepare(int v, int n_max, int k_max, int* blocks_per_sm, size_t* smem) {
   const int nt = ragged_nt(v);

@@ -35,7 +35,8 @@ class otlm_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("datafit", ctypes.c_int), ("penalty", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("poll_every", ctypes.c_int),
                 ("beta", ctypes.c_double), ("mm_steps", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("gap_tol", ctypes.c_double), ("dw_tol", ctypes.c_double)]
+                ("gap_tol", ctypes.c_double), ("dw_tol", ctypes.c_double), ("ragged_cta", ctypes.c_int),
+                ("ragged_rows_log2", ctypes.c_int * 16)]
 
 
 _LIB = None
@@ -75,7 +76,7 @@ def lib() -> ctypes.CDLL:
         L.otlm_solve_banded.argtypes = [vp, i, i, i, vp, i, i, vp, vp, vp, vp, d, d, d, vp, vp, vp, vp, vp, vp]
         L.otlm_solve_banded.restype = i
         L.otlm_tune_ragged.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp, i, i,
-                                       ctypes.POINTER(ctypes.c_int)]
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.otlm_tune_ragged.restype = i
         L.otlm_ws_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, ctypes.c_ulonglong, vp]
         L.otlm_ws_create.restype = i
@@ -149,10 +150,11 @@ class Handle:
 
     def __init__(self, n_max, k_max, batch_max, precision="fp32", datafit="kl", penalty="l2sq",
                  max_iter=1000, tol=0.0, poll_every=8, stream=None, beta=0.0, mm_steps=1, check_every=0,
-                 gap_tol=0.0, dw_tol=0.0):
+                 gap_tol=0.0, dw_tol=0.0, ragged_cta=0, ragged_rows_log2=None):
+        rows = (ctypes.c_int * 16)(*(list(ragged_rows_log2) if ragged_rows_log2 is not None else [0] * 16))
         self.cfg = otlm_config(n_max, k_max, batch_max, PRECISION[precision], DATAFIT[datafit], PENALTY[penalty],
                                max_iter, float(tol), poll_every, float(beta), mm_steps, check_every, float(gap_tol),
-                               float(dw_tol))
+                               float(dw_tol), ragged_cta, rows)
         self.precision = precision
         self._h = ctypes.c_void_p()
         _check(lib().otlm_create(ctypes.byref(self._h), ctypes.byref(self.cfg), stream), "otlm_create")
@@ -228,14 +230,16 @@ class Handle:
                                      _ptr(w), _ptr(g), _ptr(t_out), _ptr(iters), _ptr(err), _ptr(status))
         _check(rc, "otlm_solve_ragged")
 
-    def tune_ragged(self, rb, lam, alpha, w, sample_every=40, iters=6):
-        """otlm_tune_ragged: returns the CTA size the tuner kept on this handle."""
+    def tune_ragged(self, rb, lam, alpha, w, sample_every=40, iters=6, with_rows=False):
+        """otlm_tune_ragged: returns the CTA size the tuner kept on this handle, and with
+        with_rows=True also the rows-per-thread table (log2 by size bucket, otlm_config's form)."""
         out = ctypes.c_int(0)
+        rows = (ctypes.c_int * 16)()
         rc = lib().otlm_tune_ragged(self._h, rb.batch, _ptr(rb.n), _ptr(rb.k), _ptr(rb.eps), _ptr(rb.off_n),
                                     _ptr(rb.off_D), _ptr(rb.off_k), _ptr(rb.x), _ptr(rb.D), _ptr(rb.y), lam, alpha,
-                                    _ptr(w), sample_every, iters, ctypes.byref(out))
+                                    _ptr(w), sample_every, iters, ctypes.byref(out), rows)
         _check(rc, "otlm_tune_ragged")
-        return out.value
+        return (out.value, list(rows)) if with_rows else out.value
 
     def solve_stats(self, batch, dw_out=None, primal_out=None, dual_out=None):
         """otlm_solve_stats: per-problem weight change, FP64 primal and dual of the last solve."""

@@ -46,7 +46,8 @@ def test_strerror_names_every_code():
                                          ("datafit", 9), ("penalty", -1), ("penalty", 4), ("mm_steps", -1),
                                          ("mm_steps", 65), ("check_every", -1), ("gap_tol", -1e-3),
                                          ("gap_tol", float("nan")), ("dw_tol", float("inf")), ("dw_tol", -1.0),
-                                         ("gap_tol", 1e-4)])  # the last: a gap tolerance with no checks
+                                         ("gap_tol", 1e-4),  # a gap tolerance with no checks
+                                         ("ragged_cta", 64), ("ragged_cta", 384)])
 def test_create_rejects_bad_config_without_gpu(field, value):
     _ensure_built()
     cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)
@@ -91,3 +92,13 @@ def test_noalloc_rejects_non_finite_scalars_without_gpu(eps, lam, alpha, tol):
     rc = api.lib().otlm_solve_noalloc(4, 64, 8, dummy, dummy, dummy, eps, lam, alpha, 1, 2, 10, tol, dummy,
                                       None, None, None, None, None, None)
     assert rc == api.OTLM_EINVAL
+
+
+@pytest.mark.parametrize("bad", [-1, 6])
+def test_create_rejects_a_bad_rows_per_thread_entry(bad):
+    _ensure_built()
+    cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)
+    cfg.ragged_rows_log2[7] = bad
+    h = ctypes.c_void_p(123)
+    assert api.lib().otlm_create(ctypes.byref(h), ctypes.byref(cfg), None) == api.OTLM_EINVAL
+    assert h.value is None

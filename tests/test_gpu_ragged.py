@@ -180,3 +180,60 @@ def test_ragged_offsets_in_any_order_and_out_of_range_offsets():
     for p in range(B):
         np.testing.assert_array_equal(res[0][p][0], res[1][p][0])
         np.testing.assert_array_equal(res[0][p][1], res[1][p][1])
+
+
+@pytest.mark.parametrize("cta,rows_log2", [(128, 3), (256, 3), (512, 1), (256, 5)])
+def test_ragged_tile_shapes_from_the_table(cta, rows_log2):
+    """Every size bucket forced to 2^rows_log2 rows per thread (raised where a CTA of `cta` threads
+    needs more to cover n, and capped by what that CTA size compiles: 32 / 16 / 8 rows): each tile
+    shape gives the oracle's trajectory at the 1e-5 bar (sizes span buckets 0-15)."""
+    probs = spectra.ragged(47, 6, n_range=(256, 4096), k_range=(8, 64))
+    B = len(probs)
+    rb = api.ragged_batch(probs)
+    w = torch.tensor(np.concatenate([spectra.initial_weights(p["y"], p["D"]) for p in probs]).astype(np.float32),
+                     device="cuda")
+    cap = {128: 5, 256: 4, 512: 3}[cta]
+    h = api.Handle(4096, 64, B, "fp32", "tv", "l1", 6, 0.0, stream=torch.cuda.current_stream().cuda_stream,
+                   ragged_cta=cta, ragged_rows_log2=[min(rows_log2, cap)] * 16)
+    t = torch.empty_like(rb.y)
+    it = torch.empty(B, dtype=torch.int32, device="cuda")
+    err = torch.empty(B, device="cuda")
+    st = torch.empty(B, dtype=torch.int32, device="cuda")
+    h.solve_ragged(rb, 1.0, 1e-2, w, None, t, it, err, st)
+    torch.cuda.synchronize()
+    h.close()
+    assert np.all(st.cpu().numpy() == api.MAX_ITER)
+    on, ok = rb.off_n.cpu().numpy(), rb.off_k.cpu().numpy()
+    wn, tn = w.cpu().numpy(), t.cpu().numpy()
+    for i, p in enumerate(probs):
+        o = _oracle(p, "tv", "l1", 1.0, 1e-2, 6)
+        assert rel_l1(wn[ok[i]:ok[i] + p["k"]], o["w"]) <= TOL32, (i, p["n"])
+        assert rel_l1(tn[on[i]:on[i] + p["n"]], o["t"]) <= TOL32, (i, p["n"])
+
+
+def test_tuned_table_round_trips_through_otlm_create():
+    """otlm_tune_ragged's table, given to a new handle through otlm_config, reproduces the tuned
+    handle's results bit for bit."""
+    probs = spectra.ragged(48, 40, n_range=(256, 2400), k_range=(8, 40))
+    B = len(probs)
+    rb = api.ragged_batch(probs)
+    w0 = torch.tensor(np.concatenate([spectra.initial_weights(p["y"], p["D"]) for p in probs]).astype(np.float32),
+                      device="cuda")
+    res = []
+    h = api.Handle(2400, 40, B, "fp32", "kl", "l1", 8, 0.0, stream=torch.cuda.current_stream().cuda_stream)
+    cta, rows = h.tune_ragged(rb, 1.0, 1e-2, w0, sample_every=2, iters=2, with_rows=True)
+    assert cta in (128, 256, 512) and all(0 <= r <= 5 for r in rows)
+    h2 = api.Handle(2400, 40, B, "fp32", "kl", "l1", 8, 0.0, stream=torch.cuda.current_stream().cuda_stream,
+                    ragged_cta=cta, ragged_rows_log2=rows)
+    for hh in (h, h2):
+        w = w0.clone()
+        t = torch.empty_like(rb.y)
+        it = torch.empty(B, dtype=torch.int32, device="cuda")
+        err = torch.empty(B, device="cuda")
+        st = torch.empty(B, dtype=torch.int32, device="cuda")
+        hh.solve_ragged(rb, 1.0, 1e-2, w, None, t, it, err, st)
+        torch.cuda.synchronize()
+        res.append((w.cpu().numpy(), t.cpu().numpy()))
+        hh.close()
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
