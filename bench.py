@@ -384,6 +384,11 @@ class ClockSampler:
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
+# Precision schedule of the tensor-core applies (otlm_config.bf16_single_until) by workload: used
+# where the tests show the 1e-5 bar holds with it (the squared-error datafit); 0 = hi/lo throughout.
+SINGLE_UNTIL = {"batch4096_n4096_l2_l2sq": 1e-2}
+
+
 def run_ours(args, rank, world, local_rank, pool=None):
     import torch
     import torch.distributed as dist
@@ -406,7 +411,7 @@ def run_ours(args, rank, world, local_rank, pool=None):
         if world > 1:
             dist.barrier()
 
-    def measure(precision, steps, warmup):
+    def measure(precision, steps, warmup, single_until=0.0):
         """Device-resident inputs; returns timing of `steps` whole-batch solves."""
         w = torch.empty_like(w0)
         t = torch.empty_like(y)
@@ -414,7 +419,7 @@ def run_ours(args, rank, world, local_rank, pool=None):
         err = torch.empty(B, dtype=torch.float32, device=dev)
         status = torch.empty(B, dtype=torch.int32, device=dev)
         h = api.Handle(n, k, B, precision, c["datafit"], c["penalty"], c["iters"], c["tol"], poll_every=4,
-                       stream=stream.cuda_stream)
+                       stream=stream.cuda_stream, bf16_single_until=single_until)
 
         def step():
             w.copy_(w0)
@@ -447,7 +452,11 @@ def run_ours(args, rank, world, local_rank, pool=None):
         return dict(ms=e0.elapsed_time(e1), launches=launches, timing=timing, iters=iters.cpu().numpy(),
                     status=status.cpu().numpy(), clocks=clk.summary(), handle=h, w=w, t=t)
 
-    tc = measure("bf16tc", args.steps, args.warmup)
+    sched = SINGLE_UNTIL.get(args.workload, 0.0)
+    tc = measure("bf16tc", args.steps, args.warmup, sched)
+    tc3 = measure("bf16tc", max(1, min(args.steps, 3)), max(3, min(args.warmup, 3))) if sched > 0 else None
+    if tc3 is not None:
+        tc3["handle"].close()
     fp = measure("fp32", max(1, min(args.steps, 3)), max(1, min(args.warmup, 3)))
     fp["handle"].close()
 
@@ -477,7 +486,7 @@ def run_ours(args, rank, world, local_rank, pool=None):
     h2d = hx.numel() * 4 + hD.numel() * 4 + hy.numel() * 4 + hw.numel() * 4
     d2h = hw.numel() * 4 + ht.numel() * 4 + B * 4 * 3
 
-    tc_ms, fp_ms, e2e_s = max_over_ranks([tc["ms"], fp["ms"], e2e_s], world, dev)
+    tc_ms, fp_ms, e2e_s, tc3_ms = max_over_ranks([tc["ms"], fp["ms"], e2e_s, tc3["ms"] if tc3 else 0.0], world, dev)
     if rank != 0:
         return None
 
@@ -530,11 +539,12 @@ def run_ours(args, rank, world, local_rank, pool=None):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16x3 tensor (hi/lo split) + f32",
+        "dtype": "bf16x3 tensor (hi/lo split) + f32" + (", bf16x1 until a violation <= %g" % sched if sched else ""),
         "data": "synthetic (seeded Gaussian-peak spectra, no dataset)",
         "config": {"workload": args.workload, "B_per_gpu": B, "n": n, "k": k, "eps": c["eps"],
                    "datafit": c["datafit"], "lam": c["lam"], "penalty": c["penalty"], "alpha": c["alpha"],
                    "tol": c["tol"], "path": "tensor-core applies (tcgen05, BF16 hi/lo, FP32 accumulate)",
+                   "bf16_single_until": sched,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (4096 x 4096 FP32 state arrays, 64 MiB each, several per step)",
                    "mean_iters": float(it_tc.mean()), "max_iters": int(it_tc.max()),
@@ -542,6 +552,10 @@ def run_ours(args, rank, world, local_rank, pool=None):
         "iters_per_s": float(it_tc.sum()) * world * args.steps / (tc_ms / 1e3),
         "speedup_vs_plain_fp32": value / fp_value,
         "plain_fp32": plain,
+        "tensor_hilo_throughout": ({"value": whole_job_rate(B, world, max(1, min(args.steps, 3)), tc3_ms / 1e3),
+                                    "unit": "problems/s", "kernel_ms_per_step": {kk: v[0] for kk, v in
+                                                                                 tc3["timing"].items()},
+                                    "mean_iters": float(tc3["iters"].mean())} if tc3 else None),
         "roofline": roofline,
         "kernel_ms_per_step": {kk: v[0] for kk, v in tc["timing"].items()},
         "e2e": {"value": whole_job_rate(B, world, e2e_steps, e2e_s), "unit": "problems/s", "h2d_bytes_per_step": h2d,

@@ -122,6 +122,14 @@ typedef struct otlm_config {
   int    ragged_rows_log2[16];  /* rows per thread for problems with n in (256 b, 256 (b + 1)],
                           b = 0..15 (the last bucket also takes larger n), as log2: 1..5 (2..32 rows),
                           raised where needed to cover n; 0 = the fewest that cover n          */
+  double bf16_single_until;  /* OTLM_PREC_BF16_TC only, in [0, 1).  0 (default): the kernel applies
+                          always take the three BF16 hi/lo products.  > 0: a precision schedule: the
+                          applies take the single product hi x hi (one third of the tensor work)
+                          until some problem's violation e is <= this value, then hi/lo to the end.
+                          Early errors of ~2^-9 per apply are contracted away for the squared-error
+                          datafit (the measured workload stays at the 1e-5 bar: tests), but persist
+                          in w where the weights converge slowly (e.g. KL + l1 at eps = 5e-3: ~2e-5),
+                          so it is off by default.                                              */
 } otlm_config;
 
 typedef struct otlm_ctx* otlm_handle;

@@ -57,7 +57,9 @@ bool valid_enum(const otlm_config& c) {
          c.mm_steps >= 0 && c.mm_steps <= 64 && c.check_every >= 0 && c.gap_tol >= 0 && std::isfinite(c.gap_tol) &&
          c.dw_tol >= 0 && std::isfinite(c.dw_tol) && (c.gap_tol == 0 || c.check_every > 0) &&
          (c.ragged_cta == 0 || c.ragged_cta == 128 || c.ragged_cta == 256 || c.ragged_cta == 512) &&
-         std::all_of(c.ragged_rows_log2, c.ragged_rows_log2 + 16, [](int v) { return v >= 0 && v <= 5; });
+         std::all_of(c.ragged_rows_log2, c.ragged_rows_log2 + 16, [](int v) { return v >= 0 && v <= 5; }) &&
+         c.bf16_single_until >= 0 && c.bf16_single_until < 1 &&
+         (c.bf16_single_until == 0 || c.precision == OTLM_PREC_BF16_TC);
 }
 
 // Byte offsets of the workspace parts: the solver state, then (tensor-core handles) the GEMM
@@ -100,6 +102,7 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
   sp.poll_every = h->cfg.poll_every; sp.tol = h->cfg.tol;
   sp.beta = h->cfg.beta; sp.mm_steps = h->cfg.mm_steps > 1 ? h->cfg.mm_steps : 1;
   sp.check_every = h->cfg.check_every; sp.gap_tol = h->cfg.gap_tol; sp.dw_tol = h->cfg.dw_tol;
+  sp.single_until = h->cfg.bf16_single_until;
   return sp;
 }
 

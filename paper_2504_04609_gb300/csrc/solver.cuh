@@ -169,6 +169,7 @@ struct SolveParams {
   int check_every = 0;   // FP64 objective / gap every this many iterations and at the end (0: never)
   double gap_tol = 0.0;  // stop also requires (primal - dual) <= gap_tol |primal| at a check
   double dw_tol = 0.0;   // stop also requires ||dw||_1 / ||w||_1 <= dw_tol
+  double single_until = 0.0;  // tensor cores: single BF16 product until a violation is <= this
 };
 
 // Argument block of the FP64 reduction for a state held in the workspaces (S, G2, the weights)

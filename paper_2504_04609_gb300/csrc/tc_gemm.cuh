@@ -2,6 +2,9 @@
 //
 //   out[map(c)][r] = sum_j ( Ahi[r][j] Bhi[c][j] + Ahi[r][j] Blo[c][j] + Alo[r][j] Bhi[c][j] )
 //
+// (or, on request through a device flag read at launch, the single product Ahi Bhi^T: one MMA per
+// k step on the hi tiles alone; the solver uses it while every problem is far from convergence)
+//
 // Both operands are K-major (contiguous along j) and carried as hi/lo pairs (x = hi + lo), so the
 // three products recover most of the precision the single-pass type drops:
 //   KIND_BF16 (kind::f16, BF16 operands): ~16 mantissa bits; the kernel applies K V^T, where A = the
@@ -158,6 +161,8 @@ struct GemmArgs {
   int bulk;            // set by launch_gemm3: every output column segment is 16-byte aligned and a
                        // multiple of 16 bytes long, so the tile leaves through shared memory as
                        // one bulk copy per column
+  const int* hilo;     // null: the three products; otherwise, while *hilo == 0 (read at launch),
+                       // the single product hi x hi: only the hi tiles are loaded
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncols = g.n_cols ? *g.n_cols : g.N;
+  const bool three = !g.hilo || *g.hilo != 0;  // the three products, or hi x hi alone
   const int mt = (g.M + BM - 1) / BM, nt = (g.N + BN - 1) / BN;
   const int units = mt * nt * g.splits;
   const int nkb_all = (g.Kd + BK - 1) / BK;
@@ -265,11 +271,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         const int kc = (kb0 + kb) * BK;
-        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        mbar_expect_tx(full0 + 8 * s, three ? STAGE_BYTES : A_TILE + B_TILE);
         tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kc, m0);
-        tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kc, m0);
         tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kc, n0);
-        tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kc, n0);
+        if (three) {
+          tma_load_2d(a_lo(s), &tA_lo, full0 + 8 * s, kc, m0);
+          tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kc, n0);
+        }
         last_round[s] = r;
       }
     }
@@ -311,8 +319,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
           const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
           umma<KIND>(d, ah, bh, id, issued);
-          umma<KIND>(d, ah, bl, id, 1);
-          umma<KIND>(d, al, bh, id, 1);
+          if (three) {
+            umma<KIND>(d, ah, bl, id, 1);
+            umma<KIND>(d, al, bh, id, 1);
+          }
           issued = 1;
         }
         umma_commit(empty0 + 8 * s);

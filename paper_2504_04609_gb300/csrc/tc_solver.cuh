@@ -49,6 +49,7 @@ struct TcWorkspace {
   float* Msrc[2];            // [batch] source shifts, ping-pong
   float* Mtgt;               // [batch] target shifts
   int* err;                  // GEMM error flag
+  int* hilo;                 // 0: the applies use the single BF16 product, 1: hi/lo (three products)
   int2* fix_list;            // [batch x n] underflowed sums (problem, row) listed by a GEMM
   unsigned long long* fix_cnt;  // [2] list lengths: source GEMM, target GEMM
   unsigned long long fix_cap;
@@ -94,6 +95,7 @@ inline size_t carve_tc_workspace(void* base, int n_max, int k_max, int batch_max
   w.Msrc[1] = (float*)take(4 * (size_t)batch_max);
   w.Mtgt = (float*)take(4 * (size_t)batch_max);
   w.err = (int*)take(64);
+  w.hilo = (int*)take(64);
   w.fix_cap = (unsigned long long)batch_max * n_max;
   w.fix_list = (int2*)take(8 * (size_t)batch_max * n_max);
   w.fix_cnt = (unsigned long long*)take(64);
@@ -286,6 +288,7 @@ struct TcIterArgs {
   const int* gap_ok; // [P] gap test of this iteration's check
   int gap_check, gap_on;
   float dw_tol;
+  float single_until;  // > 0: switch the applies to hi/lo once a violation is <= this
   int* done;
   int* iters;
   int* status;
@@ -474,6 +477,9 @@ __device__ __forceinline__ void tc_violation_body(const TcIterArgs& A) {
     const float dw = num / den;
     A.err[p] = e;
     A.dw[p] = dw;
+    // the precision schedule: the first problem whose violation reaches single_until switches every
+    // later apply to the hi/lo products (a violation this large is far from any stop at tol)
+    if (A.single_until > 0.f && e <= A.single_until) atomicExch(A.t.hilo, 1);
     const int st = stop_decision<float>(e, dw, A.tol, A.dw_tol, A.gap_on != 0,
                                         A.gap_check && A.gap_ok && A.gap_ok[p], A.it, A.max_iter);
     if (st >= 0) {
@@ -725,6 +731,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   tc_dsplit_kernel<<<1184, 256, 0, L.stream>>>(D, n, k, tw.kp, tw.ld, tw.Dhi, tw.Dlo, tw.Dthi, tw.Dtlo);
   L.end();
   cudaError_t e = cudaMemsetAsync(tw.err, 0, sizeof(int), L.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tw.hilo, sp.single_until > 0 ? 0 : 0xFF, sizeof(int), L.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(tw.fix_cnt, 0, 2 * sizeof(unsigned long long), L.stream);
   if (e == cudaSuccess && checks) e = cudaMemsetAsync(ow->kmass, 0, sizeof(double), L.stream);
   if (e != cudaSuccess) return e;
@@ -745,11 +752,13 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   ta.mass = ws.mass; ta.err = ws.err; ta.done = ws.done; ta.iters = ws.iters; ta.status = ws.status; ta.t = tw;
   ta.dw = ws.dw; ta.Wprev = ws.Wprev; ta.dw_tol = float(sp.dw_tol); ta.gap_on = checks && sp.gap_tol > 0;
   ta.gap_ok = checks ? ow->gap_ok : nullptr;
+  ta.single_until = float(sp.single_until);
 
   // the applies K V^T (BF16): M = bins, N = slots mapped to problems, reduction over bins
   tc::GemmArgs ga{};
   ga.col_map = ws.active; ga.n_cols = ws.n_active; ga.M = n; ga.N = batch; ga.Kd = n; ga.ld_out = n;
   ga.err = tw.err; ga.fix_list = tw.fix_list; ga.fix_cap = (unsigned long long)batch * n; ga.splits = 1;
+  ga.hilo = tw.hilo;
   {
     const int units = ((n + tc::BM - 1) / tc::BM) * ((batch + tc::BN - 1) / tc::BN);
     if (batch <= TC_SMALL_BATCH && units < tc::num_sms()) {
@@ -802,6 +811,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     if (r != cudaSuccess) return r;
     tc::GemmArgs go = ga;
     go.col_map = list; go.n_cols = count; go.fix_cnt = tw.fix_cnt + 2;
+    go.hilo = nullptr;  // the objective's apply always takes the three products
     go.out = go.splits > 1 ? tw.ACCP : ow->LB2;
     L.begin(KIND_APPLY);
     r = tc::launch_gemm3<tc::KIND_BF16>(C ? tw.Kthi : tw.Khi, C ? tw.Ktlo : tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n,

@@ -47,7 +47,9 @@ def test_strerror_names_every_code():
                                          ("mm_steps", 65), ("check_every", -1), ("gap_tol", -1e-3),
                                          ("gap_tol", float("nan")), ("dw_tol", float("inf")), ("dw_tol", -1.0),
                                          ("gap_tol", 1e-4),  # a gap tolerance with no checks
-                                         ("ragged_cta", 64), ("ragged_cta", 384)])
+                                         ("ragged_cta", 64), ("ragged_cta", 384),
+                                         ("bf16_single_until", 1e-2),  # the schedule on an FP32 handle
+                                         ("bf16_single_until", -1.0)])
 def test_create_rejects_bad_config_without_gpu(field, value):
     _ensure_built()
     cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)
@@ -102,3 +104,19 @@ def test_create_rejects_a_bad_rows_per_thread_entry(bad):
     h = ctypes.c_void_p(123)
     assert api.lib().otlm_create(ctypes.byref(h), ctypes.byref(cfg), None) == api.OTLM_EINVAL
     assert h.value is None
+
+
+def test_precision_schedule_needs_a_tensor_core_handle_and_a_value_below_one():
+    _ensure_built()
+    for prec, v, rc in ((2, 1e-2, api.OTLM_OK), (2, 1.0, api.OTLM_EINVAL), (2, float("nan"), api.OTLM_EINVAL)):
+        cfg = api.otlm_config(64, 8, 4, prec, 1, 2, 10, 0.0, 4)
+        cfg.bf16_single_until = v
+        h = ctypes.c_void_p()
+        got = api.lib().otlm_create(ctypes.byref(h), ctypes.byref(cfg), None)
+        if rc == api.OTLM_OK:
+            # creation needs device memory: without a GPU it fails after validation, not with EINVAL
+            assert got != api.OTLM_EINVAL
+            if got == api.OTLM_OK:
+                api.lib().otlm_destroy(h)
+        else:
+            assert got == rc

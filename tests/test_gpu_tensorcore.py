@@ -20,12 +20,12 @@ def rel_l1(a, b):
     return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
 
 
-def _solve(d, eps, lam, alpha, datafit, penalty, iters, tol=0.0, precision="bf16tc"):
+def _solve(d, eps, lam, alpha, datafit, penalty, iters, tol=0.0, precision="bf16tc", single_until=0.0):
     dev = "cuda"
     x, D, y = (torch.tensor(d[k], device=dev) for k in ("x", "D", "y"))
     w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=torch.float32, device=dev)
     r = api.solve(x, D, y, eps, lam, alpha, datafit, penalty, w, max_iter=iters, tol=tol, precision=precision,
-                  poll_every=4)
+                  poll_every=4, bf16_single_until=single_until)
     return {k: getattr(r, k).cpu().numpy() for k in ("w", "g", "t", "iters", "err", "status")}
 
 
@@ -83,12 +83,15 @@ def test_tensorcore_matches_fp32_path_with_tolerance_stop():
         assert rel_l1(a["t"][p], b["t"][p]) <= 2 * TOL
 
 
-def test_tensorcore_full_workload_sampled_against_oracle():
-    """4096 problems at n = 4096, k = 128 (the measured workload) solved to tol in one call."""
+@pytest.mark.parametrize("single_until", [0.0, 1e-2])
+def test_tensorcore_full_workload_sampled_against_oracle(single_until):
+    """4096 problems at n = 4096, k = 128 (the measured workload) solved to tol in one call, with and
+    without the precision schedule (the benchmark's form is 1e-2)."""
     c = spectra.WORKLOADS["batch4096_n4096_l2_l2sq"]
     B, n, k = c["B"], c["n"], c["k"]
     d = spectra.batch(c["id"], B, n, k, c["nnz"])
-    r = _solve(d, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"], tol=c["tol"])
+    r = _solve(d, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"], tol=c["tol"],
+               single_until=single_until)
     assert np.all(r["status"] == api.CONVERGED)
     assert np.all(r["err"] <= c["tol"])
     assert np.all(r["w"] >= 0) and np.all(r["t"] >= 0)
@@ -213,3 +216,23 @@ def test_dense_cost_of_the_grid_matches_the_grid_solve():
     with pytest.raises(api.OTLMError):
         h32.solve_cost(C, D, y, 1e-2, 1.0, 1e-3, w)
     h32.close()
+
+
+def test_precision_schedule_on_the_squared_error_workload():
+    """bf16_single_until = 1e-2: the applies take the single BF16 product until some problem's
+    violation reaches 1e-2, then the hi/lo products.  On the measured workload's configuration (L2
+    datafit + squared l2, eps = 1e-2), n = 2048, 16 problems, solved to 1e-5: each problem matches
+    the oracle at its own iteration count at the 1e-5 bar, and the results differ from the all hi/lo
+    solve's (so the single product did run)."""
+    c = spectra.WORKLOADS["batch4096_n4096_l2_l2sq"]
+    d = spectra.batch(c["id"], 16, 2048, 128, c["nnz"], first=500)
+    args = (c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"])
+    r = _solve(d, *args, tol=c["tol"], single_until=1e-2)
+    r3 = _solve(d, *args, tol=c["tol"])
+    assert np.all(r["status"] == api.CONVERGED)
+    assert not np.array_equal(r["w"], r3["w"])
+    for p in range(16):
+        gi = int(r["iters"][p])
+        o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], gi)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
