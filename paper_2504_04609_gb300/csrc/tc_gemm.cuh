@@ -17,8 +17,10 @@
 //
 // Persistent kernel, one CTA per SM; work units (128 x 128 output tile, reduction split) are dealt
 // round-robin over the CTAs:
-//   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, 3-stage ring that runs
-//                  on across units)
+//   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, a 192 KiB ring that runs
+//                  on across units: 3 stages of the four hi/lo tiles, or 6 stages of the two hi
+//                  tiles when the single product is requested, so that twice as many k blocks are
+//                  in flight while each one feeds a third of the tensor work)
 //   warp 1 lane 0: MMA issuer  (3 x 4 tcgen05.mma per 128-byte k block) into one of two TMEM
 //                  accumulators, so the epilogue of unit i overlaps the MMAs of unit i + 1
 //   warps 4..7   : epilogue    (tcgen05.ld 32x32b, one TMEM lane quarter per warp; 64 columns at a
@@ -39,9 +41,11 @@ enum { KIND_BF16 = 0, KIND_TF32 = 1 };
 constexpr int BM = 128, BN = 128, BK_BYTES = 128, STAGES = 3;
 constexpr int A_TILE = BM * BK_BYTES;                     // 16 KiB
 constexpr int B_TILE = BN * BK_BYTES;                     // 16 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;      // 64 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;      // 64 KiB: A hi, B hi, A lo, B lo
+constexpr int STAGES_SINGLE = STAGE_BYTES * STAGES / (A_TILE + B_TILE);  // 6 stages of A hi, B hi
 constexpr int EPI_BYTES = 64 * BM * 4;                    // 32 KiB: 64 output columns of 128 rows
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + 128;
+constexpr int NBARS = 2 * STAGES_SINGLE + 5;              // full[6], empty[6], acc_full[2], acc_empty[2], drain
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + NBARS * 8 + 16;
 constexpr int THREADS = 256;
 constexpr uint32_t TMEM_COLS = 2 * BN;                    // two accumulators (double buffer)
 // Sums below 2^-90 (relative to the operand's shift) are listed for an exact recomputation: their
@@ -192,6 +196,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncols = g.n_cols ? *g.n_cols : g.N;
   const bool three = !g.hilo || *g.hilo != 0;  // the three products, or hi x hi alone
+  const int nst = three ? STAGES : STAGES_SINGLE;  // ring stages of this launch
+  const uint32_t st_bytes = three ? STAGE_BYTES : A_TILE + B_TILE;
   const int mt = (g.M + BM - 1) / BM, nt = (g.N + BN - 1) / BN;
   const int units = mt * nt * g.splits;
   const int nkb_all = (g.Kd + BK - 1) / BK;
@@ -211,20 +217,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* const stage_out = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);  // [64 columns][128 rows]
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES + EPI_BYTES);
-  // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  // full[STAGES_SINGLE], empty[STAGES_SINGLE], acc_full[2], acc_empty[2], drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
   int* fail = reinterpret_cast<int*>(tmem_slot + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
-  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES_SINGLE);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES_SINGLE), acce0 = smem_u32(bars + 2 * STAGES_SINGLE + 2);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES_SINGLE + 4);
   const uint32_t ring = smem_u32(base), stage_s = smem_u32(stage_out);
-  auto a_hi = [&](int s) { return ring + s * STAGE_BYTES; };
-  auto a_lo = [&](int s) { return ring + s * STAGE_BYTES + A_TILE; };
-  auto b_hi = [&](int s) { return ring + s * STAGE_BYTES + 2 * A_TILE; };
-  auto b_lo = [&](int s) { return ring + s * STAGE_BYTES + 2 * A_TILE + B_TILE; };
+  // stage s of this launch's ring: A hi, B hi, then (three products) A lo, B lo; every tile starts on
+  // a 16 KiB boundary, as the 128-byte swizzle wants
+  auto a_hi = [&](int s) { return ring + static_cast<uint32_t>(s) * st_bytes; };
+  auto b_hi = [&](int s) { return a_hi(s) + A_TILE; };
+  auto a_lo = [&](int s) { return a_hi(s) + A_TILE + B_TILE; };
+  auto b_lo = [&](int s) { return a_hi(s) + 2 * A_TILE + B_TILE; };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < STAGES_SINGLE; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
@@ -249,18 +257,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: the ring runs on across work units ----
-    int last_round[STAGES];
-    for (int s = 0; s < STAGES; ++s) last_round[s] = -1;
-    unsigned gk = 0;  // k blocks issued by this CTA
+    int last_round[STAGES_SINGLE];
+    for (int s = 0; s < STAGES_SINGLE; ++s) last_round[s] = -1;
+    int s = 0, r = 0;  // ring stage and round of the next k block
     bool stop = false;
     for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
       int m0, n0, z, kb0, nkb;
       coords(u, &m0, &n0, &z);
       if (n0 >= ncols) continue;
       krange(z, &kb0, &nkb);
-      for (int kb = 0; kb < nkb; ++kb, ++gk) {
-        const int s = gk % STAGES, r = gk / STAGES;
-        if (gk >= STAGES && !mbar_wait(empty0 + 8 * s, (r - 1) & 1)) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (r >= 1 && !mbar_wait(empty0 + 8 * s, (r - 1) & 1)) {
           atomicCAS(g.err, 0, ERR_WAIT_MMA);
           atomicExch(fail, 1);
           stop = true;
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         const int kc = (kb0 + kb) * BK;
-        mbar_expect_tx(full0 + 8 * s, three ? STAGE_BYTES : A_TILE + B_TILE);
+        mbar_expect_tx(full0 + 8 * s, st_bytes);
         tma_load_2d(a_hi(s), &tA_hi, full0 + 8 * s, kc, m0);
         tma_load_2d(b_hi(s), &tB_hi, full0 + 8 * s, kc, n0);
         if (three) {
@@ -279,16 +286,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_load_2d(b_lo(s), &tB_lo, full0 + 8 * s, kc, n0);
         }
         last_round[s] = r;
+        if (++s == nst) s = 0, ++r;
       }
     }
     // on an error path, let the copies already issued land before the CTA releases its memory
     if (*(volatile int*)fail)
-      for (int s = 0; s < STAGES; ++s)
-        if (last_round[s] >= 0) (void)mbar_wait(full0 + 8 * s, last_round[s] & 1);
+      for (int q = 0; q < nst; ++q)
+        if (last_round[q] >= 0) (void)mbar_wait(full0 + 8 * q, last_round[q] & 1);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: unit i accumulates into TMEM columns (i & 1) * BN ----
     constexpr uint32_t id = idesc<KIND>(BM, BN);
-    unsigned gk = 0;
+    int s = 0, r = 0;  // ring stage and round of the next k block
     int i = 0;
     bool stop = false;
     for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
@@ -305,8 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
       int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb, ++gk) {
-        const int s = gk % STAGES, r = gk / STAGES;
+      for (int kb = 0; kb < nkb; ++kb) {
         if (!mbar_wait(full0 + 8 * s, r & 1)) {
           atomicCAS(g.err, 0, ERR_WAIT_TMA);
           atomicExch(fail, 1);
@@ -326,6 +333,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           issued = 1;
         }
         umma_commit(empty0 + 8 * s);
+        if (++s == nst) s = 0, ++r;
       }
       if (stop) break;
       umma_commit(accf0 + 8 * b);  // fires once the unit's MMAs have completed
