@@ -425,6 +425,343 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---- two-SM variant (cta_group::2) of the same GEMM ---------------------------------------------
+// A cluster of two CTAs (an SM pair) computes a 256 x 128 output tile. Each CTA stages its own 128
+// rows of A and 64 of the tile's 128 B rows; the even CTA issues M = 256 MMAs that read both CTAs'
+// shared memory and accumulate into both CTAs' TMEM (each CTA's 128 rows x 128 columns). A CTA so
+// stages 24 KiB (hi) or 48 KiB (hi/lo) per k block for the same tensor work as the one-SM kernel's
+// 32 / 64 KiB, and its 192 KiB ring holds 8 or 4 stages: more of the operand latency is hidden.
+//   both CTAs, warp 0 lane 0: TMA producer into its own ring; the copies complete on the even CTA's
+//                             "full" barriers (which expect both CTAs' bytes)
+//   even CTA, warp 1 lane 0 : MMA issuer; its commits reach the "empty" and "accumulator full"
+//                             barriers of both CTAs
+//   both CTAs, warps 4..7   : epilogue of the CTA's own TMEM rows; the release of a TMEM buffer is
+//                             counted on the even CTA (4 warps x 2 CTAs)
+// Every mbarrier wait is bounded as in the one-SM kernel; the two cluster barriers (after set-up,
+// before TMEM is released) are reached by every thread of both CTAs on every path.
+constexpr int P_BM = 2 * BM;                                   // output rows per pair tile
+constexpr int P_BNH = BN / 2;                                  // B rows staged by each CTA
+constexpr int P_B_TILE = P_BNH * BK_BYTES;                     // 8 KiB
+constexpr int P_STAGE = 2 * A_TILE + 2 * P_B_TILE;             // 48 KiB: A hi, B hi, A lo, B lo
+constexpr int P_STAGES = STAGES * STAGE_BYTES / P_STAGE;       // 4
+constexpr int P_STAGES_SINGLE = STAGES * STAGE_BYTES / (A_TILE + P_B_TILE);  // 8
+constexpr int P_NBARS = 2 * P_STAGES_SINGLE + 5;
+constexpr int P_SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + P_NBARS * 8 + 16;
+static_assert(P_SMEM_BYTES <= 232448, "shared memory per CTA");
+static_assert(P_STAGE * P_STAGES <= STAGES * STAGE_BYTES && (A_TILE + P_B_TILE) * P_STAGES_SINGLE <= STAGES * STAGE_BYTES,
+              "ring");
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// The shared::cluster address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a barrier that arrivals from the other CTA of the cluster complete.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait_cluster(bar, parity))
+    if (global_ns() - t0 > WAIT_NS) return false;
+  return true;
+}
+// Tile load into this CTA's shared memory whose completion is counted on `bar` (a shared::cluster
+// address: here the even CTA's barrier).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t id,
+                                          uint32_t accumulate) {
+  if constexpr (KIND == KIND_BF16)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
+        : "memory");
+}
+// Arrive on the barrier at the same offset in both CTAs once the pair MMAs issued so far complete.
+__device__ __forceinline__ void umma_commit_pair_both(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(static_cast<uint16_t>(3))
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm3_pair_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                      const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+                      GemmArgs g) {
+  constexpr int BK = KindTraits<KIND>::BK;
+  extern __shared__ uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool even = rank == 0;
+  const int pair = static_cast<int>(blockIdx.x >> 1), npairs = static_cast<int>(gridDim.x >> 1);
+  const int ncols = g.n_cols ? *g.n_cols : g.N;
+  const bool three = !g.hilo || *g.hilo != 0;
+  const int nst = three ? P_STAGES : P_STAGES_SINGLE;
+  const uint32_t st_bytes = three ? P_STAGE : A_TILE + P_B_TILE;
+  const int mt = (g.M + P_BM - 1) / P_BM, nt = (g.N + BN - 1) / BN;
+  const int units = mt * nt;
+  const int nkb = (g.Kd + BK - 1) / BK;
+  auto coords = [&](int u, int* m0, int* n0) {  // pair tile u (m fastest)
+    *m0 = (u % mt) * P_BM;
+    *n0 = (u / mt) * BN;
+  };
+
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* const stage_out = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES + EPI_BYTES);
+  // full[8], empty[8], acc_full[2], acc_empty[2], drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + P_NBARS);
+  int* fail = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + P_STAGES_SINGLE);
+  const uint32_t accf0 = smem_u32(bars + 2 * P_STAGES_SINGLE), acce0 = smem_u32(bars + 2 * P_STAGES_SINGLE + 2);
+  const uint32_t drain = smem_u32(bars + 2 * P_STAGES_SINGLE + 4);
+  const uint32_t ring = smem_u32(base), stage_s = smem_u32(stage_out);
+  // stage s: A hi (16 KiB), B hi (8 KiB), then A lo, B lo; every tile on a 1 KiB (8-row atom) boundary,
+  // at the same offsets in both CTAs (the pair MMAs address the other CTA's tiles by this CTA's offsets)
+  auto a_hi = [&](int s) { return ring + static_cast<uint32_t>(s) * st_bytes; };
+  auto b_hi = [&](int s) { return a_hi(s) + A_TILE; };
+  auto a_lo = [&](int s) { return a_hi(s) + A_TILE + P_B_TILE; };
+  auto b_lo = [&](int s) { return a_hi(s) + 2 * A_TILE + P_B_TILE; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES_SINGLE; ++s) {
+      mbar_init(full0 + 8 * s, 1);   // the even CTA's producer; the bytes of both CTAs' copies
+      mbar_init(empty0 + 8 * s, 1);  // the pair MMAs' commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 8);  // one arrival per epilogue warp of either CTA
+    }
+    mbar_init(drain, 1);
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // the pair allocates together: the same columns in both CTAs' TMEM
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers are initialised before either CTA signals the other's
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer (both CTAs): this CTA's A rows and B rows of each pair tile ----
+    const uint32_t full_even = mapa_rank(full0, 0);
+    int last_round[P_STAGES_SINGLE];
+    for (int s = 0; s < P_STAGES_SINGLE; ++s) last_round[s] = -1;
+    int s = 0, r = 0;
+    bool stop = false;
+    for (int u = pair; u < units && !stop; u += npairs) {
+      int m0, n0;
+      coords(u, &m0, &n0);
+      if (n0 >= ncols) continue;
+      const int ma = m0 + static_cast<int>(rank) * BM, nb = n0 + static_cast<int>(rank) * P_BNH;
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (r >= 1 && !mbar_wait(empty0 + 8 * s, (r - 1) & 1)) {
+          atomicCAS(g.err, 0, ERR_WAIT_MMA);
+          atomicExch(fail, 1);
+          stop = true;
+          break;
+        }
+        if (*(volatile int*)fail) {
+          stop = true;
+          break;
+        }
+        const int kc = kb * BK;
+        const uint32_t fb = full_even + 8 * s;
+        if (even) mbar_expect_tx(full0 + 8 * s, 2 * st_bytes);
+        tma_load_2d_pair(a_hi(s), &tA_hi, fb, kc, ma);
+        tma_load_2d_pair(b_hi(s), &tB_hi, fb, kc, nb);
+        if (three) {
+          tma_load_2d_pair(a_lo(s), &tA_lo, fb, kc, ma);
+          tma_load_2d_pair(b_lo(s), &tB_lo, fb, kc, nb);
+        }
+        last_round[s] = r;
+        if (++s == nst) s = 0, ++r;
+      }
+    }
+    if (*(volatile int*)fail) {
+      if (even) {  // let the copies already issued land before the CTA releases its memory
+        for (int q = 0; q < nst; ++q)
+          if (last_round[q] >= 0) (void)mbar_wait(full0 + 8 * q, last_round[q] & 1);
+      } else {  // this CTA's copies complete on the even CTA's barriers: give them 100 us to land
+        const unsigned long long t0 = global_ns();
+        while (global_ns() - t0 < 100000ull) __nanosleep(1000);
+      }
+    }
+  } else if (warp == 1 && lane == 0 && even) {
+    // ---- MMA issuer (even CTA): pair tile i accumulates into TMEM columns (i & 1) * BN ----
+    constexpr uint32_t id = idesc<KIND>(P_BM, BN);
+    int s = 0, r = 0, i = 0;
+    bool stop = false;
+    for (int u = pair; u < units && !stop; u += npairs) {
+      int m0, n0;
+      coords(u, &m0, &n0);
+      if (n0 >= ncols) continue;
+      const int b = i & 1, use = i >> 1;
+      if (use >= 1 && !mbar_wait_cluster(acce0 + 8 * b, (use - 1) & 1)) {  // both epilogues drained buffer b
+        atomicCAS(g.err, 0, ERR_WAIT_ACC);
+        atomicExch(fail, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait(full0 + 8 * s, r & 1)) {
+          atomicCAS(g.err, 0, ERR_WAIT_TMA);
+          atomicExch(fail, 1);
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < BK_BYTES / 32; ++kk) {
+          const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
+          const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
+          umma_pair<KIND>(d, ah, bh, id, issued);
+          if (three) {
+            umma_pair<KIND>(d, ah, bl, id, 1);
+            umma_pair<KIND>(d, al, bh, id, 1);
+          }
+          issued = 1;
+        }
+        umma_commit_pair_both(empty0 + 8 * s);
+        if (++s == nst) s = 0, ++r;
+      }
+      if (stop) break;
+      umma_commit_pair_both(accf0 + 8 * b);
+      ++i;
+    }
+    umma_commit_pair(drain);  // every pair MMA issued above has completed: TMEM may be released
+    (void)mbar_wait(drain, 0);
+  } else if (warp >= 4) {
+    // ---- epilogue (both CTAs): this CTA's 128 rows of each pair tile, 64 columns at a time ----
+    const uint32_t acce_even = mapa_rank(acce0, 0);
+    const int q = warp & 3, et = threadIdx.x - 128;
+    int i = 0;
+    for (int u = pair; u < units; u += npairs) {
+      int m0, n0;
+      coords(u, &m0, &n0);
+      if (n0 >= ncols) continue;
+      const int b = i & 1, use = i >> 1;
+      const bool ok = mbar_wait(accf0 + 8 * b, use & 1);
+      if (!ok) atomicCAS(g.err, 0, ERR_WAIT_ACC);
+      if (bar_or_epi(!ok || *(volatile int*)fail)) {
+        atomicExch(fail, 1);
+        break;
+      }
+      tc_fence_after();
+      const int ma = m0 + static_cast<int>(rank) * BM;
+      const int row = ma + q * 32 + lane;
+      const int ncol_tile = min(BN, ncols - n0);
+      const int rows = min(BM, g.M - ma);  // <= 0: this CTA's half of the tile lies below the last row
+      for (int h = 0; h < BN / 64; ++h) {
+        if (g.bulk) {
+          if (et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        for (int c0 = h * 64; c0 < h * 64 + 64 && c0 < ncol_tile; c0 += 16) {
+          uint32_t v[16];
+          __syncwarp();
+          tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN + c0), v);
+          unsigned low = 0;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int col = n0 + c0 + c;
+            const bool in = col < ncols && row < g.M;
+            float val = __uint_as_float(v[c]);
+            low |= (in && !(val >= EXACT_BELOW)) ? (1u << c) : 0u;
+            if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;
+            if (g.bulk) {
+              stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;
+            } else if (in) {
+              const int o = g.col_map ? g.col_map[col] : col;
+              g.out[static_cast<size_t>(o) * g.ld_out + row] = val;
+            }
+          }
+          if (low && g.fix_list) {
+            for (; low; low &= low - 1) {
+              const int col = n0 + c0 + __ffs(low) - 1;
+              const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
+              if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
+            }
+          }
+        }
+        if (h == BN / 64 - 1) {  // every TMEM read of buffer b is done: count it on the even CTA
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_remote(acce_even + 8 * b);
+        }
+        if (g.bulk) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          const int c = h * 64 + et;
+          if (et < 64 && c < ncol_tile && rows > 0) {
+            const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
+            bulk_store(g.out + static_cast<size_t>(o) * g.ld_out + ma, stage_s + static_cast<uint32_t>(et) * (BM * 4),
+                       static_cast<uint32_t>(rows) * 4u);
+          }
+          if (et < 64) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      }
+      ++i;
+    }
+    if (g.bulk && et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // neither CTA releases TMEM or leaves while the other may still signal it
+  if (warp == 0) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 // ---- host side: tensor maps through the driver entry point (no -lcuda link needed) ----
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -499,6 +836,54 @@ static inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, int l
   const int grid = static_cast<int>(units < num_sms() ? units : num_sms());  // persistent: one CTA per SM
   gemm3_kernel<KIND><<<grid, THREADS, SMEM_BYTES, stream>>>(ta_hi, ta_lo, tb_hi, tb_lo, a);
   return cudaGetLastError();
+}
+
+// Launch the two-SM variant (same operands and arguments as launch_gemm3; no reduction split):
+// clusters of two CTAs, as many pairs as can be resident at once (one CTA per SM), each taking
+// 256 x 128 output tiles in turn.
+template <int KIND>
+static inline cudaError_t launch_gemm3_pair(const void* A_hi, const void* A_lo, int lda, const void* B_hi,
+                                            const void* B_lo, int ldb, int M, int N, int Kd, const GemmArgs& args,
+                                            cudaStream_t stream) {
+  static bool attr = false;
+  static int max_pairs = 0;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm3_pair_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (args.splits != 1) return cudaErrorInvalidValue;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = P_SMEM_BYTES;
+  cfg.stream = stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (!max_pairs) {
+    cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, gemm3_pair_kernel<KIND>, &cfg) != cudaSuccess || n < 1) {
+      (void)cudaGetLastError();
+      n = num_sms() / 2;
+    }
+    max_pairs = n < num_sms() / 2 ? n : num_sms() / 2;
+  }
+  GemmArgs a = args;
+  a.bulk = (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 && M % 4 == 0;
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  if (!make_map<KIND>(&ta_hi, A_hi, M, Kd, lda, BM) || !make_map<KIND>(&ta_lo, A_lo, M, Kd, lda, BM) ||
+      !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, P_BNH) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, P_BNH))
+    return cudaErrorInvalidValue;
+  const long long units = static_cast<long long>((M + P_BM - 1) / P_BM) * ((N + BN - 1) / BN);
+  const int pairs = static_cast<int>(units < max_pairs ? units : max_pairs);
+  cfg.gridDim = dim3(2 * pairs, 1, 1);
+  return cudaLaunchKernelEx(&cfg, gemm3_pair_kernel<KIND>, ta_hi, ta_lo, tb_hi, tb_lo, a);
 }
 
 // Splits of a reduction of `nkb` k blocks over `tiles` output tiles that minimise

@@ -770,6 +770,13 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   }
   const TcCost cost_src{ws.xt, C, float(1.0 / eps_ln2), 0}, cost_tgt{ws.xt, C, float(1.0 / eps_ln2), 1};
   const int red_grid = (int)(((size_t)batch * n + 255) / 256 < 1184 ? ((size_t)batch * n + 255) / 256 : 1184);
+  // the BF16 GEMM of an apply: the two-SM kernel (256 x 128 tiles over SM pairs) when the reduction
+  // is not split, else the one-SM kernel with its split partial sums
+  auto launch_apply = [&](const __nv_bfloat16* Ah, const __nv_bfloat16* Al, const __nv_bfloat16* Bh,
+                          const __nv_bfloat16* Bl, const tc::GemmArgs& a) -> cudaError_t {
+    if (a.splits == 1) return tc::launch_gemm3_pair<tc::KIND_BF16>(Ah, Al, tw.ld, Bh, Bl, tw.ld, n, batch, n, a, L.stream);
+    return tc::launch_gemm3<tc::KIND_BF16>(Ah, Al, tw.ld, Bh, Bl, tw.ld, n, batch, n, a, L.stream);
+  };
   // one apply into `acc` (counting underflows into `cnt`): split partial sums are added afterwards
   // the source apply reads K, the target apply K^T (the same matrix for the symmetric grid cost)
   auto apply = [&](float* acc, unsigned long long* cnt, bool target) -> cudaError_t {
@@ -777,8 +784,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     ga.fix_cnt = cnt;
     const bool kt = target && C;
     L.begin(KIND_APPLY);
-    cudaError_t r = tc::launch_gemm3<tc::KIND_BF16>(kt ? tw.Kthi : tw.Khi, kt ? tw.Ktlo : tw.Klo, tw.ld, tw.Vhi,
-                                                    tw.Vlo, tw.ld, n, batch, n, ga, L.stream);
+    cudaError_t r = launch_apply(kt ? tw.Kthi : tw.Khi, kt ? tw.Ktlo : tw.Klo, tw.Vhi, tw.Vlo, ga);
     if (r == cudaSuccess && ga.splits > 1) {
       tc_split_reduce_kernel<<<red_grid, 256, 0, L.stream>>>(tw.ACCP, ga.splits, ga.split_stride, ws.active,
                                                               ws.n_active, n, acc, tw.fix_list, cnt, ga.fix_cap);
@@ -814,8 +820,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     go.hilo = nullptr;  // the objective's apply always takes the three products
     go.out = go.splits > 1 ? tw.ACCP : ow->LB2;
     L.begin(KIND_APPLY);
-    r = tc::launch_gemm3<tc::KIND_BF16>(C ? tw.Kthi : tw.Khi, C ? tw.Ktlo : tw.Klo, tw.ld, tw.Vhi, tw.Vlo, tw.ld, n,
-                                        batch, n, go, L.stream);
+    r = launch_apply(C ? tw.Kthi : tw.Khi, C ? tw.Ktlo : tw.Klo, tw.Vhi, tw.Vlo, go);
     if (r == cudaSuccess && go.splits > 1) {
       tc_split_reduce_kernel<<<red_grid, 256, 0, L.stream>>>(tw.ACCP, go.splits, go.split_stride, list, count, n,
                                                               ow->LB2, tw.fix_list, tw.fix_cnt + 2, go.fix_cap);
