@@ -140,14 +140,26 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+
+// tcgen05.ld of 16 columns without the wait: several loads in flight, then one tmem_wait_ld.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
       "[%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+// Wait for the loads issued so far; the 64 destination registers pass through the waits so that no
+// use of them is scheduled before the loads have landed.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[64]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 64; j += 16)
+    asm volatile(""
+                 : "+r"(v[j]), "+r"(v[j + 1]), "+r"(v[j + 2]), "+r"(v[j + 3]), "+r"(v[j + 4]), "+r"(v[j + 5]),
+                   "+r"(v[j + 6]), "+r"(v[j + 7]), "+r"(v[j + 8]), "+r"(v[j + 9]), "+r"(v[j + 10]), "+r"(v[j + 11]),
+                   "+r"(v[j + 12]), "+r"(v[j + 13]), "+r"(v[j + 14]), "+r"(v[j + 15])::"memory");
 }
 
 struct GemmArgs {
@@ -185,6 +197,76 @@ __device__ __forceinline__ bool bar_or_epi(bool v) {
 __device__ __forceinline__ void bulk_store(float* gdst, uint32_t ssrc, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
                : "memory");
+}
+
+// Epilogue of one 128 x BN output tile in TMEM (the calling warp's lane quarter q: rows
+// m0 + 32 q + lane; columns n0 .. n0 + BN - 1 at TMEM column offsets tq + c), 64 columns at a time:
+// four loads and one wait per half, then either the 32 KiB staging buffer and one bulk copy per
+// column (g.bulk) or one 128-byte store per warp and column. release() runs once every TMEM read of
+// the tile is done. Sums below EXACT_BELOW are listed for the exact fix-up.
+template <class Release>
+__device__ __forceinline__ void epilogue_tile(const GemmArgs& g, float* out, uint32_t tq, float* stage_out,
+                                              uint32_t stage_s, int m0, int n0, int ncols, int q, int lane, int et,
+                                              Release release) {
+  const int row = m0 + q * 32 + lane;
+  const int ncol_tile = min(BN, ncols - n0);
+  const int rows = min(BM, g.M - m0);  // <= 0: the tile's rows all lie past the last row
+  for (int h = 0; h < BN / 64; ++h) {
+    if (g.bulk) {
+      if (et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging is free again
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+    // the half's 64 columns (columns past the last problem are read too: the buffer holds all BN)
+    uint32_t v[64];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tmem_ld16_nowait(tq + static_cast<uint32_t>(h * 64 + j * 16), v + 16 * j);
+    tmem_wait_ld(v);
+    if (h == BN / 64 - 1) {
+      tc_fence_before();
+      __syncwarp();
+      release();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c0 = h * 64 + j * 16;
+      unsigned low = 0;  // columns whose sum is below EXACT_BELOW (including an empty sum)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = n0 + c0 + c;
+        const bool in = col < ncols && row < g.M;
+        float val = __uint_as_float(v[16 * j + c]);
+        low |= (in && !(val >= EXACT_BELOW)) ? (1u << c) : 0u;
+        if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
+        if (g.bulk) {
+          stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;
+        } else if (in) {
+          const int o = g.col_map ? g.col_map[col] : col;
+          out[static_cast<size_t>(o) * g.ld_out + row] = val;
+        }
+      }
+      if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
+        for (; low; low &= low - 1) {
+          const int col = n0 + c0 + __ffs(low) - 1;
+          const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
+          if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
+        }
+      }
+    }
+    if (g.bulk) {
+      // the generic-proxy writes become visible to the bulk-copy (async) proxy, then one thread per
+      // column sends rows m0 .. m0 + rows - 1 of that column
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const int c = h * 64 + et;
+      if (et < 64 && c < ncol_tile && rows > 0) {
+        const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
+        bulk_store(out + static_cast<size_t>(o) * g.ld_out + m0, stage_s + static_cast<uint32_t>(et) * (BM * 4),
+                   static_cast<uint32_t>(rows) * 4u);
+      }
+      if (et < 64) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
 }
 
 template <int KIND>
@@ -357,61 +439,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       tc_fence_after();
-      float* const out = g.out + z * g.split_stride;
-      const int row = m0 + q * 32 + lane;
-      const int ncol_tile = min(BN, ncols - n0);
-      const int rows = min(BM, g.M - m0);
-      for (int h = 0; h < BN / 64; ++h) {
-        if (g.bulk) {
-          if (et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging is free again
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
-        for (int c0 = h * 64; c0 < h * 64 + 64 && c0 < ncol_tile; c0 += 16) {
-          uint32_t v[16];
-          __syncwarp();
-          tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN + c0), v);
-          unsigned low = 0;  // columns whose sum is below EXACT_BELOW (including an empty sum)
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int col = n0 + c0 + c;
-            const bool in = col < ncols && row < g.M;
-            float val = __uint_as_float(v[c]);
-            low |= (in && !(val >= EXACT_BELOW)) ? (1u << c) : 0u;
-            if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
-            if (g.bulk) {
-              stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;
-            } else if (in) {
-              const int o = g.col_map ? g.col_map[col] : col;
-              out[static_cast<size_t>(o) * g.ld_out + row] = val;
-            }
-          }
-          if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
-            for (; low; low &= low - 1) {
-              const int col = n0 + c0 + __ffs(low) - 1;
-              const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
-              if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
-            }
-          }
-        }
-        if (h == BN / 64 - 1) {  // every TMEM read of buffer b is done: hand it back to the MMA warp
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(acce0 + 8 * b);
-        }
-        if (g.bulk) {
-          // the generic-proxy writes become visible to the bulk-copy (async) proxy, then one thread
-          // per column sends rows m0 .. m0 + rows - 1 of that column
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-          const int c = h * 64 + et;
-          if (et < 64 && c < ncol_tile) {
-            const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
-            bulk_store(out + static_cast<size_t>(o) * g.ld_out + m0, stage_s + static_cast<uint32_t>(et) * (BM * 4),
-                       static_cast<uint32_t>(rows) * 4u);
-          }
-          if (et < 64) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
-      }
+      const uint32_t tq = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN);
+      // once every TMEM read of buffer b is done, hand it back to the MMA warp
+      epilogue_tile(g, g.out + z * g.split_stride, tq, stage_out, stage_s, m0, n0, ncols, q, lane, et,
+                    [&] { if (lane == 0) mbar_arrive(acce0 + 8 * b); });
       ++i;
     }
     if (g.bulk && et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -695,59 +726,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int ma = m0 + static_cast<int>(rank) * BM;
-      const int row = ma + q * 32 + lane;
-      const int ncol_tile = min(BN, ncols - n0);
-      const int rows = min(BM, g.M - ma);  // <= 0: this CTA's half of the tile lies below the last row
-      for (int h = 0; h < BN / 64; ++h) {
-        if (g.bulk) {
-          if (et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
-        for (int c0 = h * 64; c0 < h * 64 + 64 && c0 < ncol_tile; c0 += 16) {
-          uint32_t v[16];
-          __syncwarp();
-          tmem_ld16(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN + c0), v);
-          unsigned low = 0;
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int col = n0 + c0 + c;
-            const bool in = col < ncols && row < g.M;
-            float val = __uint_as_float(v[c]);
-            low |= (in && !(val >= EXACT_BELOW)) ? (1u << c) : 0u;
-            if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;
-            if (g.bulk) {
-              stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;
-            } else if (in) {
-              const int o = g.col_map ? g.col_map[col] : col;
-              g.out[static_cast<size_t>(o) * g.ld_out + row] = val;
-            }
-          }
-          if (low && g.fix_list) {
-            for (; low; low &= low - 1) {
-              const int col = n0 + c0 + __ffs(low) - 1;
-              const unsigned long long e = atomicAdd(g.fix_cnt, 1ull);
-              if (e < g.fix_cap) g.fix_list[e] = make_int2(g.col_map ? g.col_map[col] : col, row);
-            }
-          }
-        }
-        if (h == BN / 64 - 1) {  // every TMEM read of buffer b is done: count it on the even CTA
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive_remote(acce_even + 8 * b);
-        }
-        if (g.bulk) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-          const int c = h * 64 + et;
-          if (et < 64 && c < ncol_tile && rows > 0) {
-            const int o = g.col_map ? g.col_map[n0 + c] : n0 + c;
-            bulk_store(g.out + static_cast<size_t>(o) * g.ld_out + ma, stage_s + static_cast<uint32_t>(et) * (BM * 4),
-                       static_cast<uint32_t>(rows) * 4u);
-          }
-          if (et < 64) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
-      }
+      const int ma = m0 + static_cast<int>(rank) * BM;  // this CTA's rows of the pair tile
+      const uint32_t tq = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN);
+      // once every TMEM read of buffer b is done, count it on the even CTA
+      epilogue_tile(g, g.out, tq, stage_out, stage_s, ma, n0, ncols, q, lane, et,
+                    [&] { if (lane == 0) mbar_arrive_remote(acce_even + 8 * b); });
       ++i;
     }
     if (g.bulk && et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");

@@ -799,7 +799,8 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   gr.splits = tc::choose_splits(((k + tc::BM - 1) / tc::BM) * ((batch + tc::BN - 1) / tc::BN),
                                 (n + tc::KindTraits<tc::KIND_TF32>::BK - 1) / tc::KindTraits<tc::KIND_TF32>::BK);
   gr.split_stride = mb.plane;
-  // s = D w (TF32): M = bins, N = slots mapped to problems, reduction over dictionary columns
+  // s = D w (TF32, two-SM kernel): M = bins, N = slots mapped to problems, reduction over dictionary
+  // columns
   tc::GemmArgs gw{};
   gw.out = ws.S; gw.col_map = ws.active; gw.n_cols = ws.n_active; gw.M = n; gw.N = batch; gw.Kd = k;
   gw.ld_out = n; gw.err = tw.err; gw.flush_tiny = 1; gw.splits = 1;
@@ -849,7 +850,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, 0, 0, 0);
   L.end();
   L.begin(KIND_OTHER);
-  e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
+  e = tc::launch_gemm3_pair<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
   L.end();
   if (e != cudaSuccess) return e;
 
@@ -884,7 +885,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1, 1);
     L.end();
     L.begin(KIND_MM);
-    e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
+    e = tc::launch_gemm3_pair<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
     L.end();
     if (e != cudaSuccess) return e;
     // further MM steps with the same a: log ratios from the new s, D^T r, update, s = D w
@@ -900,7 +901,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
       tc_wupd_kernel<<<(int)(((long long)batch * k + 255) / 256), 256, 0, L.stream>>>(ta, mb, gr.splits, 1, 0);
       L.end();
       L.begin(KIND_MM);
-      e = tc::launch_gemm3<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
+      e = tc::launch_gemm3_pair<tc::KIND_TF32>(tw.Dhi, tw.Dlo, tw.kp, tw.Whi, tw.Wlo, tw.kp, n, batch, k, gw, L.stream);
       L.end();
       if (e != cudaSuccess) return e;
     }

@@ -83,6 +83,31 @@ def test_tensorcore_matches_fp32_path_with_tolerance_stop():
         assert rel_l1(a["t"][p], b["t"][p]) <= 2 * TOL
 
 
+@pytest.mark.parametrize("n", [100, 300])
+def test_two_sm_apply_ragged_tiles_and_compaction(n):
+    """130 problems (above the split-reduction batch size, so every apply runs on the two-SM kernel:
+    256 x 128 tiles over SM pairs) with a column tile of 2 problems; n = 100 leaves the odd CTA of
+    each pair no rows at all, n = 300 a partial row tile on the even CTA and none on the odd one.
+    Stopped at tol = 1e-5 under L2 + l2sq, so the problems leave the batch at different iterations
+    and the applies run over a compacted column list.  Sampled problems match the oracle at their own
+    iteration count (or, where the two stops differ by one, where the oracle's violation sits at
+    the tolerance)."""
+    d = spectra.batch(37, 130, n, 12, 3)
+    args = (1e-2, 1.0, 1e-3, "l2", "l2sq")
+    r = _solve(d, *args, 400, tol=1e-5)
+    assert np.all(r["status"] == api.CONVERGED)
+    assert len(np.unique(r["iters"])) > 1  # the batch did compact
+    for p in (0, 1, 63, 127, 128, 129):
+        o = _oracle(d, p, *args, 400, tol=1e-5)
+        gi = int(r["iters"][p])
+        if gi != o["iters"]:
+            e = o["err_hist"]
+            assert abs(gi - o["iters"]) == 1 and abs(e[min(gi, o["iters"]) - 1] / 1e-5 - 1) < 1e-2, (p, gi, o["iters"])
+            o = _oracle(d, p, *args, gi)
+        assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
+        assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
+
+
 @pytest.mark.parametrize("single_until", [0.0, 1e-2])
 def test_tensorcore_full_workload_sampled_against_oracle(single_until):
     """4096 problems at n = 4096, k = 128 (the measured workload) solved to tol in one call, with and
