@@ -386,9 +386,11 @@ class ClockSampler:
 
 # DRAM bytes per launch of the tensor-core apply (gemm3_pair_kernel<KIND_BF16>) at n = 4096, 4096
 # problems, averaged over the applies of one solve under the precision schedule, from a one-pass
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); None until taken for this kernel.
-TC_APPLY_TRAFFIC = None
-TC_APPLY_TRAFFIC_NOTE = "not yet captured for the two-SM kernel"
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands.
+TC_APPLY_TRAFFIC = 245.7e6
+TC_APPLY_TRAFFIC_NOTE = ("mean DRAM bytes per apply over the 40 applies of one solve (15 single-product: "
+                         "132 MB, 24 hi/lo: 327 MB, against 134 / 201 MB algorithmic), one-pass ncu capture: "
+                         "profiles/gemm3_pair_apply_n4096_b4096.md")
 
 # Precision schedule of the tensor-core applies (otlm_config.bf16_single_until) by workload: used
 # where the tests show the 1e-5 bar holds with it (the squared-error datafit); 0 = hi/lo throughout.

@@ -477,6 +477,7 @@ constexpr int P_STAGE = 2 * A_TILE + 2 * P_B_TILE;             // 48 KiB: A hi, 
 constexpr int P_STAGES = STAGES * STAGE_BYTES / P_STAGE;       // 4
 constexpr int P_STAGES_SINGLE = STAGES * STAGE_BYTES / (A_TILE + P_B_TILE);  // 8
 constexpr int P_NBARS = 2 * P_STAGES_SINGLE + 5;
+constexpr int P_GROUP_M = 8;                                   // row tiles per raster group
 constexpr int P_SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + P_NBARS * 8 + 16;
 static_assert(P_SMEM_BYTES <= 232448, "shared memory per CTA");
 static_assert(P_STAGE * P_STAGES <= STAGES * STAGE_BYTES && (A_TILE + P_B_TILE) * P_STAGES_SINGLE <= STAGES * STAGE_BYTES,
@@ -571,9 +572,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int mt = (g.M + P_BM - 1) / P_BM, nt = (g.N + BN - 1) / BN;
   const int units = mt * nt;
   const int nkb = (g.Kd + BK - 1) / BK;
-  auto coords = [&](int u, int* m0, int* n0) {  // pair tile u (m fastest)
-    *m0 = (u % mt) * P_BM;
-    *n0 = (u / mt) * BN;
+  // pair tile u: groups of P_GROUP_M row tiles, m fastest within a group, so that the pairs at work
+  // at one time share a band of A rows (2048 rows = 32 MiB of hi/lo BF16 at n = 4096) that stays in
+  // L2 while the B tiles stream, instead of all of A (which L2 does not hold across waves)
+  auto coords = [&](int u, int* m0, int* n0) {
+    const int per = P_GROUP_M * nt, grp = u / per, r = u - grp * per;
+    const int first = grp * P_GROUP_M, gsz = min(mt - first, P_GROUP_M);
+    *m0 = (first + r % gsz) * P_BM;
+    *n0 = (r / gsz) * BN;
   };
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
