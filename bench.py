@@ -387,6 +387,7 @@ class ClockSampler:
 # DRAM bytes per launch of the tensor-core apply (gemm3_pair_kernel<KIND_BF16>) at n = 4096, 4096
 # problems, averaged over the applies of one solve under the precision schedule, from a one-pass
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands.
+TC_APPLY_TRAFFIC_WORKLOAD = "batch4096_n4096_l2_l2sq"
 TC_APPLY_TRAFFIC = 245.7e6
 TC_APPLY_TRAFFIC_NOTE = ("mean DRAM bytes per apply over the 40 applies of one solve (15 single-product: "
                          "132 MB, 24 hi/lo: 327 MB, against 134 / 201 MB algorithmic), one-pass ncu capture: "
@@ -516,10 +517,12 @@ def run_ours(args, rank, world, local_rank, pool=None):
     roofline = {"bound": "tensor",
                 "kernel": "gemm3_pair_kernel<KIND_BF16> (two-SM tcgen05 K V^T, BF16 hi/lo, FP32 accumulate)",
                 "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": TC_APPLY_TRAFFIC, "launch_ms_avg": g_ms / max(g_cnt, 1),
+                "traffic": TC_APPLY_TRAFFIC if args.workload == TC_APPLY_TRAFFIC_WORKLOAD else None,
+                "launch_ms_avg": g_ms / max(g_cnt, 1),
                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained",
-                "traffic_note": TC_APPLY_TRAFFIC_NOTE}
+                "traffic_note": TC_APPLY_TRAFFIC_NOTE if args.workload == TC_APPLY_TRAFFIC_WORKLOAD else
+                "no DRAM capture of this workload"}
     if tc3 is not None:
         it3 = tc3["iters"].astype(np.float64)
         a3_ms, _ = tc3["timing"]["apply"]
