@@ -998,7 +998,7 @@ def run_single_hbm(args, rank, world, local_rank):
                    "l2": "the stored kernel (1 GiB) is larger than L2", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "gemm3_kernel<KIND_BF16> + tc_split_reduce_kernel (one apply)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": 1082.8e6, "traffic_note": "GEMM 1081.2 MB read + 0.8 MB written, split reduce "
+                     "traffic": 1081.2e6, "traffic_note": "GEMM 1079.4 MB read + 0.9 MB written, split reduce "
                                                           "0.9 MB read (ncu, profiles/hbm_single_n16384.md)",
                      "launch_ms_avg": launch_ms, "bytes_per_launch": 4.0 * n * n,
                      "peak_basis": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in _peaks() else "fallback 6.8 TB/s"},
