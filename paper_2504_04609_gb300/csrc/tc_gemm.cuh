@@ -34,6 +34,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace otlm {
 namespace tc {
 
@@ -179,6 +181,8 @@ struct GemmArgs {
                        // one bulk copy per column
   const int* hilo;     // null: the three products; otherwise, while *hilo == 0 (read at launch),
                        // the single product hi x hi: only the hi tiles are loaded
+  int store_direct;    // 1: the epilogue stores from registers, one 128-byte segment per warp and
+                       // column, instead of staging and one bulk copy per column
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -227,6 +231,13 @@ __device__ __forceinline__ void epilogue_tile(const GemmArgs& g, float* out, uin
       __syncwarp();
       release();
     }
+    // direct stores: the output rows of the half's 64 columns, two per lane, read once
+    int orow0 = 0, orow1 = 0;
+    if (!g.bulk) {
+      const int c0 = n0 + h * 64 + lane, c1 = c0 + 32;
+      orow0 = c0 < ncols ? (g.col_map ? g.col_map[c0] : c0) : 0;
+      orow1 = c1 < ncols ? (g.col_map ? g.col_map[c1] : c1) : 0;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c0 = h * 64 + j * 16;
@@ -240,9 +251,10 @@ __device__ __forceinline__ void epilogue_tile(const GemmArgs& g, float* out, uin
         if (g.flush_tiny && val < 1.17549435e-38f) val = 0.f;  // a NaN stays visible
         if (g.bulk) {
           stage_out[(c0 - h * 64 + c) * BM + q * 32 + lane] = val;
-        } else if (in) {
-          const int o = g.col_map ? g.col_map[col] : col;
-          out[static_cast<size_t>(o) * g.ld_out + row] = val;
+        } else {  // one 128-byte segment per warp and column
+          const int cc = j * 16 + c;  // column within the half (compile-time)
+          const int o = __shfl_sync(0xffffffffu, cc < 32 ? orow0 : orow1, cc & 31);
+          if (in) out[static_cast<size_t>(o) * g.ld_out + row] = val;
         }
       }
       if (low && g.fix_list) {  // rare: list each underflowed sum for the exact fix-up
@@ -377,50 +389,65 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (last_round[q] >= 0) (void)mbar_wait(full0 + 8 * q, last_round[q] & 1);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: unit i accumulates into TMEM columns (i & 1) * BN ----
-    constexpr uint32_t id = idesc<KIND>(BM, BN);
-    int s = 0, r = 0;  // ring stage and round of the next k block
-    int i = 0;
-    bool stop = false;
-    for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
-      int m0, n0, z, kb0, nkb;
-      coords(u, &m0, &n0, &z);
-      if (n0 >= ncols) continue;
-      krange(z, &kb0, &nkb);
-      const int b = i & 1, use = i >> 1;
-      if (use >= 1 && !mbar_wait(acce0 + 8 * b, (use - 1) & 1)) {  // the epilogue has drained buffer b
-        atomicCAS(g.err, 0, ERR_WAIT_ACC);
-        atomicExch(fail, 1);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        if (!mbar_wait(full0 + 8 * s, r & 1)) {
-          atomicCAS(g.err, 0, ERR_WAIT_TMA);
+    // One loop per product count, descriptors advanced by tile offsets (as in the two-SM kernel).
+    auto mma_role = [&](auto three_c) {
+      constexpr bool THREE = decltype(three_c)::value;
+      constexpr uint32_t id = idesc<KIND>(BM, BN);
+      constexpr uint32_t ST16 = (THREE ? STAGE_BYTES : A_TILE + B_TILE) >> 4;
+      constexpr int NST = THREE ? STAGES : STAGES_SINGLE;
+      constexpr uint32_t O_BH = A_TILE >> 4, O_AL = (A_TILE + B_TILE) >> 4, O_BL = (2 * A_TILE + B_TILE) >> 4;
+      const uint64_t d_ring = sw128_desc(ring);
+      uint64_t sd = d_ring;  // stage s
+      int s = 0, r = 0;      // ring stage and round of the next k block
+      int i = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+        int m0, n0, z, kb0, nkb;
+        coords(u, &m0, &n0, &z);
+        if (n0 >= ncols) continue;
+        krange(z, &kb0, &nkb);
+        const int b = i & 1, use = i >> 1;
+        if (use >= 1 && !mbar_wait(acce0 + 8 * b, (use - 1) & 1)) {  // the epilogue has drained buffer b
+          atomicCAS(g.err, 0, ERR_WAIT_ACC);
           atomicExch(fail, 1);
-          stop = true;
           break;
         }
         tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < BK_BYTES / 32; ++kk) {
-          const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
-          const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
-          umma<KIND>(d, ah, bh, id, issued);
-          if (three) {
-            umma<KIND>(d, ah, bl, id, 1);
-            umma<KIND>(d, al, bh, id, 1);
+        const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
+        int issued = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(full0 + 8 * s, r & 1)) {
+            atomicCAS(g.err, 0, ERR_WAIT_TMA);
+            atomicExch(fail, 1);
+            stop = true;
+            break;
           }
-          issued = 1;
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < BK_BYTES / 32; ++kk) {  // 32 bytes of k per MMA: +2 in the address field
+            const uint64_t ah = sd + 2 * kk, bh = sd + O_BH + 2 * kk;
+            umma<KIND>(d, ah, bh, id, issued);
+            if constexpr (THREE) {
+              umma<KIND>(d, ah, sd + O_BL + 2 * kk, id, 1);
+              umma<KIND>(d, sd + O_AL + 2 * kk, bh, id, 1);
+            }
+            issued = 1;
+          }
+          umma_commit(empty0 + 8 * s);
+          if (++s == NST) {
+            s = 0, ++r;
+            sd = d_ring;
+          } else {
+            sd += ST16;
+          }
         }
-        umma_commit(empty0 + 8 * s);
-        if (++s == nst) s = 0, ++r;
+        if (stop) break;
+        umma_commit(accf0 + 8 * b);  // fires once the unit's MMAs have completed
+        ++i;
       }
-      if (stop) break;
-      umma_commit(accf0 + 8 * b);  // fires once the unit's MMAs have completed
-      ++i;
-    }
+    };
+    if (three) mma_role(std::true_type{});
+    else mma_role(std::false_type{});
     umma_commit(drain);  // fires once every MMA issued above has completed: TMEM may be released
     (void)mbar_wait(drain, 0);
   } else if (warp >= 4) {
@@ -671,48 +698,65 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1 && lane == 0 && even) {
     // ---- MMA issuer (even CTA): pair tile i accumulates into TMEM columns (i & 1) * BN ----
-    constexpr uint32_t id = idesc<KIND>(P_BM, BN);
-    int s = 0, r = 0, i = 0;
-    bool stop = false;
-    for (int u = pair; u < units && !stop; u += npairs) {
-      int m0, n0;
-      coords(u, &m0, &n0);
-      if (n0 >= ncols) continue;
-      const int b = i & 1, use = i >> 1;
-      if (use >= 1 && !mbar_wait_cluster(acce0 + 8 * b, (use - 1) & 1)) {  // both epilogues drained buffer b
-        atomicCAS(g.err, 0, ERR_WAIT_ACC);
-        atomicExch(fail, 1);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        if (!mbar_wait(full0 + 8 * s, r & 1)) {
-          atomicCAS(g.err, 0, ERR_WAIT_TMA);
+    // One loop per product count (a compile-time constant in each), with the smem descriptors
+    // advanced by adding tile offsets in 16-byte units (the start-address field holds address / 16
+    // of shared memory below 256 KiB, so the offsets add without carry).
+    auto mma_role = [&](auto three_c) {
+      constexpr bool THREE = decltype(three_c)::value;
+      constexpr uint32_t id = idesc<KIND>(P_BM, BN);
+      constexpr uint32_t ST16 = (THREE ? P_STAGE : A_TILE + P_B_TILE) >> 4;
+      constexpr int NST = THREE ? P_STAGES : P_STAGES_SINGLE;
+      constexpr uint32_t O_BH = A_TILE >> 4, O_AL = (A_TILE + P_B_TILE) >> 4, O_BL = (2 * A_TILE + P_B_TILE) >> 4;
+      const uint64_t d_ring = sw128_desc(ring);
+      uint64_t sd = d_ring;  // stage s
+      int s = 0, r = 0, i = 0;
+      bool stop = false;
+      for (int u = pair; u < units && !stop; u += npairs) {
+        int m0, n0;
+        coords(u, &m0, &n0);
+        if (n0 >= ncols) continue;
+        const int b = i & 1, use = i >> 1;
+        if (use >= 1 && !mbar_wait_cluster(acce0 + 8 * b, (use - 1) & 1)) {  // both epilogues drained buffer b
+          atomicCAS(g.err, 0, ERR_WAIT_ACC);
           atomicExch(fail, 1);
-          stop = true;
           break;
         }
         tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < BK_BYTES / 32; ++kk) {
-          const uint64_t ah = sw128_desc(a_hi(s) + kk * 32), al = sw128_desc(a_lo(s) + kk * 32);
-          const uint64_t bh = sw128_desc(b_hi(s) + kk * 32), bl = sw128_desc(b_lo(s) + kk * 32);
-          umma_pair<KIND>(d, ah, bh, id, issued);
-          if (three) {
-            umma_pair<KIND>(d, ah, bl, id, 1);
-            umma_pair<KIND>(d, al, bh, id, 1);
+        const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
+        int issued = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(full0 + 8 * s, r & 1)) {
+            atomicCAS(g.err, 0, ERR_WAIT_TMA);
+            atomicExch(fail, 1);
+            stop = true;
+            break;
           }
-          issued = 1;
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < BK_BYTES / 32; ++kk) {  // 32 bytes of k per MMA: +2 in the address field
+            const uint64_t ah = sd + 2 * kk, bh = sd + O_BH + 2 * kk;
+            umma_pair<KIND>(d, ah, bh, id, issued);
+            if constexpr (THREE) {
+              umma_pair<KIND>(d, ah, sd + O_BL + 2 * kk, id, 1);
+              umma_pair<KIND>(d, sd + O_AL + 2 * kk, bh, id, 1);
+            }
+            issued = 1;
+          }
+          umma_commit_pair_both(empty0 + 8 * s);
+          if (++s == NST) {
+            s = 0, ++r;
+            sd = d_ring;
+          } else {
+            sd += ST16;
+          }
         }
-        umma_commit_pair_both(empty0 + 8 * s);
-        if (++s == nst) s = 0, ++r;
+        if (stop) break;
+        umma_commit_pair_both(accf0 + 8 * b);
+        ++i;
       }
-      if (stop) break;
-      umma_commit_pair_both(accf0 + 8 * b);
-      ++i;
-    }
+    };
+    if (three) mma_role(std::true_type{});
+    else mma_role(std::false_type{});
     umma_commit_pair(drain);  // every pair MMA issued above has completed: TMEM may be released
     (void)mbar_wait(drain, 0);
   } else if (warp >= 4) {
@@ -815,8 +859,8 @@ static inline cudaError_t launch_gemm3(const void* A_hi, const void* A_lo, int l
   if (args.splits < 1 || args.splits > nkb) return cudaErrorInvalidValue;
   GemmArgs a = args;
   // column segments out + o * ld_out + m0 of M - m0 (<= 128) floats: 16-byte aligned and sized
-  a.bulk = (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 && M % 4 == 0 &&
-           (a.splits == 1 || a.split_stride % 4 == 0);
+  a.bulk = !a.store_direct && (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 &&
+           M % 4 == 0 && (a.splits == 1 || a.split_stride % 4 == 0);
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
   if (!make_map<KIND>(&ta_hi, A_hi, M, Kd, lda, BM) || !make_map<KIND>(&ta_lo, A_lo, M, Kd, lda, BM) ||
       !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, BN) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, BN))
@@ -864,7 +908,7 @@ static inline cudaError_t launch_gemm3_pair(const void* A_hi, const void* A_lo, 
     max_pairs = n < num_sms() / 2 ? n : num_sms() / 2;
   }
   GemmArgs a = args;
-  a.bulk = (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 && M % 4 == 0;
+  a.bulk = !a.store_direct && (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 && M % 4 == 0;
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
   if (!make_map<KIND>(&ta_hi, A_hi, M, Kd, lda, BM) || !make_map<KIND>(&ta_lo, A_lo, M, Kd, lda, BM) ||
       !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, P_BNH) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, P_BNH))

@@ -803,7 +803,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   // columns
   tc::GemmArgs gw{};
   gw.out = ws.S; gw.col_map = ws.active; gw.n_cols = ws.n_active; gw.M = n; gw.N = batch; gw.Kd = k;
-  gw.ld_out = n; gw.err = tw.err; gw.flush_tiny = 1; gw.splits = 1;
+  gw.ld_out = n; gw.err = tw.err; gw.flush_tiny = 1; gw.splits = 1; gw.store_direct = 1;
   const int row_cfg = tc_row_cfg(n);
 
   // FP64 objective of the listed problems' states (w, g) on the tensor-core applies: the state's
