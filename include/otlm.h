@@ -6,7 +6,8 @@
  * per iteration a Gibbs-kernel apply a = K u1, one majorisation-minimisation (MM) step on the
  * dictionary weights w (Table 2), the source scaling u2 = X w / a, a second apply b = K^T u2,
  * and the datafit proximal step u1 = prox_L(b | y) / b (Table 1).  K = exp(-C/eps) with the
- * squared-distance cost C_ij = (x_i - x_j)^2 on a 1-D grid x (Sec. 2.2, Gibbs kernel).
+ * squared-distance cost C_ij = (x_i - x_j)^2 on a 1-D grid x (Sec. 2.2, Gibbs kernel), or the
+ * absolute distance |x_i - x_j| (otlm_config.cost).
  *
  * Conventions shared by every entry point
  *  - Every array argument is a DEVICE pointer owned by the caller, except where a function
@@ -74,6 +75,12 @@ typedef enum {            /* weight penalty R(w), Table 2 */
                                  (App. A's stationarity condition; Table 2 prints alpha/beta)   */
 } otlm_penalty;
 
+typedef enum {            /* grid cost of otlm_solve / otlm_solve_host / otlm_objective (Sec. 2.2) */
+  OTLM_COST_GRID_SQ  = 0,     /* C_ij = (x_i - x_j)^2 (the default)                              */
+  OTLM_COST_GRID_ABS = 1      /* C_ij = |x_i - x_j|: the cost of the paper's demonstrations and
+                                 scalability tests, C = rho |x_i - x_j| (pass x scaled by rho)    */
+} otlm_cost_kind;
+
 typedef enum {
   OTLM_PREC_FP32_LOG = 0,     /* FP32, scalings carried as log2 potentials (stable at small eps) */
   OTLM_PREC_FP64     = 1,     /* FP64 throughout, same log-domain arithmetic                   */
@@ -130,6 +137,10 @@ typedef struct otlm_config {
                           datafit (the measured workload stays at the 1e-5 bar: tests), but persist
                           in w where the weights converge slowly (e.g. KL + l1 at eps = 5e-3: ~2e-5),
                           so it is off by default.                                              */
+  int    cost;         /* otlm_cost_kind of the grid solves (0 = squared distance).  otlm_solve_cost
+                          (dense C) and otlm_solve_banded (cost diagonals) take their cost as given
+                          and ignore it; otlm_solve_ragged and otlm_tune_ragged support the squared
+                          distance only (OTLM_EUNSUPPORTED otherwise).                          */
 } otlm_config;
 
 typedef struct otlm_ctx* otlm_handle;
@@ -150,7 +161,7 @@ void otlm_destroy(otlm_handle h);
 
 /* Solve `batch` independent OTLM problems sharing one grid and one dictionary
  * (Algorithm 1; cfg.mm_steps MM steps per iteration, one by default as in Sec. 4.2).
- *   x      [n]          grid; cost C_ij = (x_i - x_j)^2
+ *   x      [n]          grid; cost C_ij = (x_i - x_j)^2, or |x_i - x_j| with OTLM_COST_GRID_ABS
  *   D      [n][k]       dictionary X of the paper; entries >= 0, every column sum > 0
  *   y      [batch][n]   targets, >= 0
  *   eps, lam, alpha     entropic weight (> 0), datafit weight (> 0; ignored for BALANCED),

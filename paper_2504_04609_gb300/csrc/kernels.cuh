@@ -4,6 +4,8 @@
 //   LA2 = log2 (K u1),  LB2 = log2 (K^T u2),  S = X w  (the paper's X is the dictionary D).
 // With the scaled grid xt = x / sqrt(eps ln2), C_ij / (eps ln2) = (xt_i - xt_j)^2, so
 //   LA2_i = log2 sum_j 2^(G2_j - (xt_i - xt_j)^2),   LB2_j = log2 sum_i 2^(F2_i - (xt_i - xt_j)^2).
+// The absolute-distance grid cost C_ij = |x_i - x_j| (the cost of the paper's demonstrations and
+// scalability tests, there scaled by rho: pass rho x) takes xt = x / (eps ln2) and |xt_i - xt_j|.
 #pragma once
 
 #include "common.cuh"
@@ -11,6 +13,13 @@
 namespace otlm {
 
 enum { EPI_SOURCE = 0, EPI_TARGET = 1 };
+enum { COST_SQ = 0, COST_ABS = 1 };  // grid cost in log2 units: (xt_i - xt_j)^2 or |xt_i - xt_j|
+
+template <int COST, typename T>
+__device__ __forceinline__ T grid_cost(T d) {
+  if constexpr (COST == COST_ABS) return fabs(d);
+  else return d * d;
+}
 enum { DF_BALANCED = 0, DF_KL = 1, DF_TV = 2, DF_L2 = 3, DF_POISSON = 4 };
 enum { PEN_NONE = 0, PEN_L1 = 1, PEN_L2SQ = 2, PEN_ELASTIC = 3 };
 enum { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_NONFINITE = 2, ST_INVALID = 3 };
@@ -109,8 +118,8 @@ __device__ __forceinline__ void stage_chunk(const ApplyArgs<T>& A, const int* pr
   __syncthreads();
 }
 
-// Exact shift: m = max_j (in_bj - c_ij), c_ij = (xt_i - xt_j)^2 (scalar; the rare path).
-template <typename T, class Cfg>
+// Exact shift: m = max_j (in_bj - c_ij), c_ij the grid cost (scalar; the rare path).
+template <typename T, class Cfg, int COST>
 __device__ __forceinline__ void sweep_max(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
                                           const T (&xi)[Cfg::RI], int wb, T (&m)[Cfg::RB][Cfg::RI]) {
   constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
@@ -125,14 +134,14 @@ __device__ __forceinline__ void sweep_max(const ApplyArgs<T>& A, const int* prob
       for (int r = 0; r < RI; ++r) {
         const T d = xi[r] - xj;
 #pragma unroll
-        for (int q = 0; q < RB; ++q) m[q][r] = fmax(m[q][r], v[q] - d * d);
+        for (int q = 0; q < RB; ++q) m[q][r] = fmax(m[q][r], v[q] - grid_cost<COST>(d));
       }
     }
   }
 }
 
 // Sum with a known shift: acc = sum_j 2^(in_bj - m_bi - c_ij).  Generic (double) version.
-template <typename T, class Cfg>
+template <typename T, class Cfg, int COST>
 __device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
                                           const T (&xi)[Cfg::RI], int wb, const T (&m)[Cfg::RB][Cfg::RI],
                                           T (&acc)[Cfg::RB][Cfg::RI]) {
@@ -149,7 +158,10 @@ __device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob
       for (int r = 0; r < RI; ++r) {
         const T d = xi[r] - xj;
 #pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q][r] += P::exp2(fma(-d, d, v[q] - m[q][r]));
+        for (int q = 0; q < RB; ++q) {
+          if constexpr (COST == COST_ABS) acc[q][r] += P::exp2((v[q] - m[q][r]) - fabs(d));
+          else acc[q][r] += P::exp2(fma(-d, d, v[q] - m[q][r]));
+        }
       }
     }
   }
@@ -162,7 +174,10 @@ __device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob
 // element against one exponent-unit op, and the exponent unit (32 results / SM / clock) is the
 // bound.  The centre keeps di small (a tile spans TI rows) and dj is small for every column that
 // matters, so no large squares are added and cancelled.
-template <class Cfg>
+// Absolute-distance cost (COST_ABS): no expansion; the staged values are the inputs themselves and
+// the grid values xt_j, and an element costs the difference xt_i - xt_j (shared by a packed pair of
+// problems) and two packed adds.
+template <class Cfg, int COST>
 __device__ __forceinline__ void stage_chunk_f32(const ApplyArgs<float>& A, const int* prob_s, float* h_s, float* dj_s,
                                                 float xc, int j0) {
   using P = Prec<float>;
@@ -170,7 +185,7 @@ __device__ __forceinline__ void stage_chunk_f32(const ApplyArgs<float>& A, const
   const int n = A.n;
   __syncthreads();
   for (int jj = threadIdx.x; jj < TJ; jj += NT) {
-    const float d = (j0 + jj < n) ? A.xt[j0 + jj] - xc : 0.f;
+    const float d = (j0 + jj < n) ? (COST == COST_ABS ? A.xt[j0 + jj] : A.xt[j0 + jj] - xc) : 0.f;
     dj_s[2 * jj] = d;
     dj_s[2 * jj + 1] = d;
   }
@@ -178,21 +193,25 @@ __device__ __forceinline__ void stage_chunk_f32(const ApplyArgs<float>& A, const
     const int bb = e / TJ, jj = e - bb * TJ, j = j0 + jj, p = prob_s[bb];
     float h = P::ninf();
     if (p >= 0 && j < n) {
-      const float d = A.xt[j] - xc;
-      h = fmaf(-d, d, A.in[(size_t)p * n + j]);
+      if constexpr (COST == COST_ABS) {
+        h = A.in[(size_t)p * n + j];
+      } else {
+        const float d = A.xt[j] - xc;
+        h = fmaf(-d, d, A.in[(size_t)p * n + j]);
+      }
     }
     h_s[jj * TB + bb] = h;
   }
   __syncthreads();
 }
 
-template <class Cfg>
+template <class Cfg, int COST>
 __device__ __forceinline__ void sweep_max_f32(const ApplyArgs<float>& A, const int* prob_s, float* h_s, float* dj_s,
-                                              float xc, const float (&di)[Cfg::RI], int wb,
-                                              float (&m)[Cfg::RB][Cfg::RI]) {
+                                              float xc, const float (&xi)[Cfg::RI], const float (&di)[Cfg::RI],
+                                              int wb, float (&m)[Cfg::RB][Cfg::RI]) {
   constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
   for (int j0 = 0; j0 < A.n; j0 += TJ) {
-    stage_chunk_f32<Cfg>(A, prob_s, h_s, dj_s, xc, j0);
+    stage_chunk_f32<Cfg, COST>(A, prob_s, h_s, dj_s, xc, j0);
 #pragma unroll 4
     for (int jj = 0; jj < TJ; ++jj) {
       const float dj = dj_s[2 * jj];
@@ -201,19 +220,25 @@ __device__ __forceinline__ void sweep_max_f32(const ApplyArgs<float>& A, const i
 #pragma unroll
       for (int r = 0; r < RI; ++r)
 #pragma unroll
-        for (int q = 0; q < RB; ++q) m[q][r] = fmaxf(m[q][r], fmaf(2.f * di[r], dj, h[q]));
+        for (int q = 0; q < RB; ++q) {
+          if constexpr (COST == COST_ABS) m[q][r] = fmaxf(m[q][r], h[q] - fabsf(xi[r] - dj));
+          else m[q][r] = fmaxf(m[q][r], fmaf(2.f * di[r], dj, h[q]));
+        }
     }
   }
+  if constexpr (COST == COST_SQ) {
 #pragma unroll
-  for (int r = 0; r < RI; ++r)
+    for (int r = 0; r < RI; ++r)
 #pragma unroll
-    for (int q = 0; q < RB; ++q) m[q][r] -= di[r] * di[r];
+      for (int q = 0; q < RB; ++q) m[q][r] -= di[r] * di[r];
+  }
 }
 
-template <class Cfg>
+template <class Cfg, int COST>
 __device__ __forceinline__ void sweep_sum_f32(const ApplyArgs<float>& A, const int* prob_s, float* h_s, float* dj_s,
-                                              float xc, const float (&di)[Cfg::RI], int wb,
-                                              const float (&m)[Cfg::RB][Cfg::RI], float (&acc)[Cfg::RB][Cfg::RI]) {
+                                              float xc, const float (&xi)[Cfg::RI], const float (&di)[Cfg::RI],
+                                              int wb, const float (&m)[Cfg::RB][Cfg::RI],
+                                              float (&acc)[Cfg::RB][Cfg::RI]) {
   using P = Prec<float>;
   constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ, QP = RB / 2;
   static_assert(RB == 4, "packed sweep expects 4 problems per thread");
@@ -221,7 +246,7 @@ __device__ __forceinline__ void sweep_sum_f32(const ApplyArgs<float>& A, const i
 #pragma unroll
   for (int r = 0; r < RI; ++r) {
     tdi[r] = f2_pack(2.f * di[r], 2.f * di[r]);
-    const float d2 = di[r] * di[r];
+    const float d2 = COST == COST_ABS ? 0.f : di[r] * di[r];
 #pragma unroll
     for (int p = 0; p < QP; ++p) {
       nq[p][r] = f2_pack(-(m[2 * p][r] + d2), -(m[2 * p + 1][r] + d2));
@@ -229,7 +254,7 @@ __device__ __forceinline__ void sweep_sum_f32(const ApplyArgs<float>& A, const i
     }
   }
   for (int j0 = 0; j0 < A.n; j0 += TJ) {
-    stage_chunk_f32<Cfg>(A, prob_s, h_s, dj_s, xc, j0);
+    stage_chunk_f32<Cfg, COST>(A, prob_s, h_s, dj_s, xc, j0);
 #pragma unroll 4
     for (int jj = 0; jj < TJ; ++jj) {
       const float2 dq = *reinterpret_cast<const float2*>(dj_s + 2 * jj);
@@ -237,14 +262,21 @@ __device__ __forceinline__ void sweep_sum_f32(const ApplyArgs<float>& A, const i
       const uint64_t dj2 = f2_pack(dq.x, dq.y);
       const uint64_t h2[QP] = {f2_pack(hq.x, hq.y), f2_pack(hq.z, hq.w)};
 #pragma unroll
-      for (int r = 0; r < RI; ++r)
+      for (int r = 0; r < RI; ++r) {
+        uint64_t nad = 0;  // -|xt_i - xt_j| on both lanes (absolute-distance cost)
+        if constexpr (COST == COST_ABS) {
+          const float ad = -fabsf(xi[r] - dq.x);
+          nad = f2_pack(ad, ad);
+        }
 #pragma unroll
         for (int p = 0; p < QP; ++p) {
-          const uint64_t u2 = f2_add(f2_fma(tdi[r], dj2, h2[p]), nq[p][r]);
+          const uint64_t u2 = COST == COST_ABS ? f2_add(f2_add(h2[p], nq[p][r]), nad)
+                                               : f2_add(f2_fma(tdi[r], dj2, h2[p]), nq[p][r]);
           float u0, u1;
           f2_unpack(u2, u0, u1);
           acc2[p][r] = f2_add(acc2[p][r], f2_pack(P::exp2(u0), P::exp2(u1)));
         }
+      }
     }
   }
 #pragma unroll
@@ -259,7 +291,7 @@ __device__ __forceinline__ void sweep_sum_f32(const ApplyArgs<float>& A, const i
 //   SHIFT_EXACT: an exact max pass first.
 // A fast shift is checked afterwards: if any sum of the tile leaves [2^-60, 2^60] (or a shift is
 // not finite) the CTA redoes its tile with the exact shift.
-template <typename T, class Cfg, int EPI, int SHIFT>
+template <typename T, class Cfg, int EPI, int SHIFT, int COST>
 __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
   using P = Prec<T>;
   constexpr int RB = Cfg::RB, RI = Cfg::RI, WB = Cfg::WB, TB = Cfg::TB, TI = Cfg::TI, TJ = Cfg::TJ;
@@ -305,8 +337,8 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
       }
     safe = __syncthreads_or(bad);
     if (!safe) {
-      if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg>(A, prob_s, in_s, xj_s, xc, di, wb, m, acc);
-      else sweep_sum<T, Cfg>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+      if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m, acc);
+      else sweep_sum<T, Cfg, COST>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
       bad = false;
 #pragma unroll
       for (int q = 0; q < RB; ++q)
@@ -323,15 +355,15 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r) { m[q][r] = P::ninf(); acc[q][r] = T(0); }
-    if constexpr (sizeof(T) == 4) sweep_max_f32<Cfg>(A, prob_s, in_s, xj_s, xc, di, wb, m);
-    else sweep_max<T, Cfg>(A, prob_s, in_s, xj_s, xi, wb, m);
+    if constexpr (sizeof(T) == 4) sweep_max_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m);
+    else sweep_max<T, Cfg, COST>(A, prob_s, in_s, xj_s, xi, wb, m);
 #pragma unroll
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r)
         if (!(m[q][r] > P::ninf())) m[q][r] = T(0);  // every term vanishes: the sum stays 0
-    if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg>(A, prob_s, in_s, xj_s, xc, di, wb, m, acc);
-      else sweep_sum<T, Cfg>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+    if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m, acc);
+      else sweep_sum<T, Cfg, COST>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
   }
   const bool prev_shift = SHIFT == SHIFT_PREV && !safe;  // then acc = a_new / a_old exactly
 

@@ -19,7 +19,7 @@ cudaError_t objective_device(const Launch& L, const Workspace<T>& ws, const Solv
   pa.iters = ws.iters; pa.status = ws.status; pa.err = ws.err;
   pa.dw = ws.dw; pa.all = ws.all; pa.all_count = ws.all_count;
   pa.batch = batch; pa.n = n; pa.k = k;
-  pa.xscale = T(1.0 / sqrt(eps_ln2));
+  pa.xscale = T(grid_scale(sp.cost, eps_ln2));
   pa.gscale = T(1.0 / eps_ln2);
   L.begin(KIND_OTHER);
   prep_kernel<T><<<1184, 256, 0, L.stream>>>(pa);
@@ -32,7 +32,7 @@ cudaError_t objective_device(const Launch& L, const Workspace<T>& ws, const Solv
   ApplyArgs<T> src{};
   src.in = ws.G2; src.out = ws.LA2; src.xt = ws.xt; src.active = ws.active; src.n_active = ws.n_active;
   src.n = n; src.S = ws.S; src.err_acc = ws.err_acc; src.check = 0;
-  launch_apply<T, EPI_SOURCE>(L, src, true, batch, n);
+  launch_apply<T, EPI_SOURCE>(L, src, true, batch, n, sp.cost);
   L.begin(KIND_OTHER);
   objective_source_kernel<T><<<batch, 256, 0, L.stream>>>(ws.Dt, ws.W, ws.LA2, ws.S, ws.F2, ws.mass, n, k);
   L.end();
@@ -44,14 +44,14 @@ cudaError_t objective_device(const Launch& L, const Workspace<T>& ws, const Solv
   tgt.tv_bound = T(sp.lam / eps_ln2);
   tgt.lam_over_eps = T(sp.lam / sp.eps);
   tgt.log_lam_over_eps = T(log(sp.lam / sp.eps));
-  launch_apply<T, EPI_TARGET>(L, tgt, true, batch, n);
+  launch_apply<T, EPI_TARGET>(L, tgt, true, batch, n, sp.cost);
 
   // sum(K) in FP64
   double* kmass = ws.kmass;
   cudaError_t e = cudaMemsetAsync(kmass, 0, sizeof(double), L.stream);
   if (e != cudaSuccess) return e;
   L.begin(KIND_OTHER);
-  kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, kmass);
+  kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, kmass, sp.cost == COST_ABS);
   L.end();
 
   ObjArgs<T> oa{};

@@ -24,16 +24,17 @@
 
 namespace otlm {
 
-// sum_ij exp(-(x_i - x_j)^2 / eps) in FP64, accumulated into *out (zeroed by the caller).
+// sum_ij exp(-C_ij / eps) of the grid cost ((x_i - x_j)^2, or |x_i - x_j| when abs_cost) in FP64,
+// accumulated into *out (zeroed by the caller).
 template <typename T>
-__global__ void kernel_mass_kernel(const T* x, int n, double inv_eps, double* out) {
+__global__ void kernel_mass_kernel(const T* x, int n, double inv_eps, double* out, int abs_cost) {
   __shared__ double red[32];
   double acc = 0.0;
   const size_t nn = (size_t)n * n;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
     const size_t i = e / n, j = e - i * n;
     const double d = (double)x[i] - (double)x[j];
-    acc += ::exp(-d * d * inv_eps);
+    acc += ::exp(-(abs_cost ? ::fabs(d) : d * d) * inv_eps);
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) atomicAdd(out, acc);

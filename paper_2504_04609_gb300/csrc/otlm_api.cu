@@ -59,7 +59,8 @@ bool valid_enum(const otlm_config& c) {
          (c.ragged_cta == 0 || c.ragged_cta == 128 || c.ragged_cta == 256 || c.ragged_cta == 512) &&
          std::all_of(c.ragged_rows_log2, c.ragged_rows_log2 + 16, [](int v) { return v >= 0 && v <= 5; }) &&
          c.bf16_single_until >= 0 && c.bf16_single_until < 1 &&
-         (c.bf16_single_until == 0 || c.precision == OTLM_PREC_BF16_TC);
+         (c.bf16_single_until == 0 || c.precision == OTLM_PREC_BF16_TC) &&
+         (c.cost == OTLM_COST_GRID_SQ || c.cost == OTLM_COST_GRID_ABS);
 }
 
 // Byte offsets of the workspace parts: the solver state, then (tensor-core handles) the GEMM
@@ -103,6 +104,7 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
   sp.beta = h->cfg.beta; sp.mm_steps = h->cfg.mm_steps > 1 ? h->cfg.mm_steps : 1;
   sp.check_every = h->cfg.check_every; sp.gap_tol = h->cfg.gap_tol; sp.dw_tol = h->cfg.dw_tol;
   sp.single_until = h->cfg.bf16_single_until;
+  sp.cost = h->cfg.cost == OTLM_COST_GRID_ABS ? otlm::COST_ABS : otlm::COST_SQ;
   return sp;
 }
 
@@ -156,7 +158,8 @@ int ragged_setup(otlm_ctx* h, int batch, const int* n, const int* k, const float
                  const long long* off_D, const long long* off_k, std::vector<int>* order,
                  std::vector<int>* n_host = nullptr) {
   const otlm_config& c = h->cfg;
-  if (c.precision != OTLM_PREC_FP32_LOG || c.check_every > 0 || c.dw_tol > 0) return OTLM_EUNSUPPORTED;
+  if (c.precision != OTLM_PREC_FP32_LOG || c.check_every > 0 || c.dw_tol > 0 || c.cost != OTLM_COST_GRID_SQ)
+    return OTLM_EUNSUPPORTED;
   if (batch < 1 || batch > c.batch_max || c.n_max > 4096) return OTLM_EINVAL;
   std::vector<int> hn(batch), hk(batch);
   std::vector<float> he(batch);

@@ -170,7 +170,14 @@ struct SolveParams {
   double gap_tol = 0.0;  // stop also requires (primal - dual) <= gap_tol |primal| at a check
   double dw_tol = 0.0;   // stop also requires ||dw||_1 / ||w||_1 <= dw_tol
   double single_until = 0.0;  // tensor cores: single BF16 product until a violation is <= this
+  int cost = COST_SQ;         // grid cost: COST_SQ (x_i - x_j)^2 or COST_ABS |x_i - x_j|
 };
+
+// Scale of the grid that turns the cost into log2 units: (xt_i - xt_j)^2 = (x_i - x_j)^2 / (eps ln2)
+// or |xt_i - xt_j| = |x_i - x_j| / (eps ln2).
+inline double grid_scale(int cost, double eps_ln2) {
+  return cost == COST_ABS ? 1.0 / eps_ln2 : 1.0 / sqrt(eps_ln2);
+}
 
 // Argument block of the FP64 reduction for a state held in the workspaces (S, G2, the weights)
 // with its source potential, target sums and datafit step in the objective scratch.
@@ -220,11 +227,16 @@ inline int sm_count() {
 }
 
 template <typename T, typename Cfg, int EPI>
-void launch_apply_cfg(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n) {
+void launch_apply_cfg(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n, int cost) {
   const dim3 grid((n + Cfg::TI - 1) / Cfg::TI, (batch + Cfg::TB - 1) / Cfg::TB);
   L.begin(KIND_APPLY);
-  if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG><<<grid, Cfg::NT, 0, L.stream>>>(a);
-  else apply_kernel<T, Cfg, EPI, SHIFT_PREV><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  if (cost == COST_ABS) {
+    if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG, COST_ABS><<<grid, Cfg::NT, 0, L.stream>>>(a);
+    else apply_kernel<T, Cfg, EPI, SHIFT_PREV, COST_ABS><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  } else {
+    if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG, COST_SQ><<<grid, Cfg::NT, 0, L.stream>>>(a);
+    else apply_kernel<T, Cfg, EPI, SHIFT_PREV, COST_SQ><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  }
   L.end();
 }
 
@@ -232,16 +244,16 @@ void launch_apply_cfg(const Launch& L, const ApplyArgs<T>& a, bool first, int ba
 // per SM (at n = 1024 x 1024 problems it gives 512 CTAs, 3.4 per SM at four resident: a quarter of
 // the warps the exponent unit needs to stay busy).
 template <typename T, int EPI>
-void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n) {
+void launch_apply(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n, int cost) {
   using Cfg = typename TileFor<T>::type;
   if constexpr (sizeof(T) == 4) {
     const long long ctas = (long long)((n + Cfg::TI - 1) / Cfg::TI) * ((batch + Cfg::TB - 1) / Cfg::TB);
     if (ctas < 8LL * sm_count()) {
-      launch_apply_cfg<T, typename TileFor<T>::small, EPI>(L, a, first, batch, n);
+      launch_apply_cfg<T, typename TileFor<T>::small, EPI>(L, a, first, batch, n, cost);
       return;
     }
   }
-  launch_apply_cfg<T, Cfg, EPI>(L, a, first, batch, n);
+  launch_apply_cfg<T, Cfg, EPI>(L, a, first, batch, n, cost);
 }
 
 template <typename T>
@@ -266,7 +278,7 @@ void objective_eval(const Launch& L, const Workspace<T>& ws, const ObjWorkspace<
   L.end();
   ApplyArgs<T> t = tgt;
   t.in = ow.F2; t.out = ow.LB2; t.G2 = ow.G2n; t.active = list; t.n_active = count; t.check = 0;
-  launch_apply<T, EPI_TARGET>(L, t, true, sp.batch, sp.n);
+  launch_apply<T, EPI_TARGET>(L, t, true, sp.batch, sp.n, sp.cost);
   ObjArgs<T> oa = obj_args<T>(sp, D, ws.xcol, ws.W, y, ws.S, ws.G2, ow);
   oa.list = list; oa.count = count; oa.gap_ok = gap ? ow.gap_ok : nullptr;
   L.begin(KIND_OTHER);
@@ -291,7 +303,7 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorks
   pa.iters = ws.iters; pa.status = ws.status; pa.err = ws.err;
   pa.dw = ws.dw; pa.all = ws.all; pa.all_count = ws.all_count;
   pa.batch = batch; pa.n = n; pa.k = k;
-  pa.xscale = T(1.0 / sqrt(eps_ln2));
+  pa.xscale = T(grid_scale(sp.cost, eps_ln2));
   pa.gscale = T(1.0 / eps_ln2);
   L.begin(KIND_OTHER);
   prep_kernel<T><<<1184, 256, 0, L.stream>>>(pa);
@@ -306,7 +318,7 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorks
     cudaError_t e = cudaMemsetAsync(ow->kmass, 0, sizeof(double), L.stream);
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
-    kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass);
+    kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass, sp.cost == COST_ABS);
     L.end();
   }
 
@@ -331,7 +343,7 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorks
 
   for (int it = 0;; ++it) {
     src.check = it > 0;
-    launch_apply<T, EPI_SOURCE>(L, src, it == 0, batch, n);
+    launch_apply<T, EPI_SOURCE>(L, src, it == 0, batch, n, sp.cost);
     // a check: the state (w, g) whose a = K u1 was just computed is the one this iteration returns
     // if it stops here; its FP64 objective and gap come before the stopping decision
     const bool check = checks && it > 0 && it % sp.check_every == 0;
@@ -343,7 +355,7 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorks
     compact_kernel<<<1, 1024, 0, L.stream>>>(ws.active, ws.n_active, ws.done);
     L.end();
     if (it >= sp.max_iter) break;
-    launch_apply<T, EPI_TARGET>(L, tgt, it == 0, batch, n);
+    launch_apply<T, EPI_TARGET>(L, tgt, it == 0, batch, n, sp.cost);
     if ((it + 1) % sp.poll_every == 0) {
       cudaError_t e = cudaMemcpyAsync(L.host_flag, ws.n_active, sizeof(int), cudaMemcpyDeviceToHost, L.stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);

@@ -143,14 +143,14 @@ __global__ void tc_dsplit_kernel(const float* D, int n, int k, int kp, int ld, f
   }
 }
 
-// K = 2^{-(xt_i - xt_j)^2} as a BF16 hi/lo pair, [n][ld] (columns >= n left untouched: the
-// tensor maps stop at column n).
-__global__ void kbuild_kernel(const float* xt, int n, int ld, __nv_bfloat16* Khi, __nv_bfloat16* Klo) {
+// K = 2^{-(xt_i - xt_j)^2} (or 2^{-|xt_i - xt_j|} for the absolute-distance cost) as a BF16 hi/lo
+// pair, [n][ld] (columns >= n left untouched: the tensor maps stop at column n).
+__global__ void kbuild_kernel(const float* xt, int n, int ld, __nv_bfloat16* Khi, __nv_bfloat16* Klo, int abs_cost) {
   const size_t nn = (size_t)n * n;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
     const float d = xt[i] - xt[j];
-    const float k = Prec<float>::exp2(-d * d);
+    const float k = Prec<float>::exp2(abs_cost ? -fabsf(d) : -d * d);
     const __nv_bfloat16 hi = __float2bfloat16_rn(k);
     Khi[(size_t)i * ld + j] = hi;
     Klo[(size_t)i * ld + j] = __float2bfloat16_rn(k - __bfloat162float(hi));
@@ -222,17 +222,19 @@ __global__ void __launch_bounds__(256) kdense_kernel(const float* C, int n, int 
 // other, which the next GEMM appends to.  With nothing listed every CTA leaves after one load.
 constexpr int TC_FIX_GRID = 4 * 152;
 
-// The exponent of term j of row i in log2 units: the grid cost (xt_i - xt_j)^2, or a dense cost
-// C c read along row i (trans = 0) or column i (trans = 1: a target sum of the transposed kernel).
+// The exponent of term j of row i in log2 units: the grid cost (xt_i - xt_j)^2 or |xt_i - xt_j|,
+// or a dense cost C c read along row i (trans = 0) or column i (trans = 1: a target sum of the
+// transposed kernel).
 struct TcCost {
   const float* xt;  // scaled grid, when C is NULL
   const float* C;   // dense cost [n][n] or NULL
   float c;          // 1 / (eps ln2)
   int trans;
+  int abs_cost;     // grid cost |xt_i - xt_j|
   __device__ __forceinline__ float operator()(int i, int j, int n) const {
     if (!C) {
       const float d = xt[i] - xt[j];
-      return d * d;
+      return abs_cost ? fabsf(d) : d * d;
     }
     return (trans ? C[(size_t)j * n + i] : C[(size_t)i * n + j]) * c;
   }
@@ -713,7 +715,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   pa.iters = ws.iters; pa.status = ws.status; pa.err = ws.err;
   pa.dw = ws.dw; pa.all = ws.all; pa.all_count = ws.all_count;
   pa.batch = batch; pa.n = n; pa.k = k;
-  pa.xscale = float(1.0 / sqrt(eps_ln2));
+  pa.xscale = float(grid_scale(sp.cost, eps_ln2));
   pa.gscale = float(1.0 / eps_ln2);
   L.begin(KIND_OTHER);
   prep_kernel<float><<<1184, 256, 0, L.stream>>>(pa);
@@ -725,7 +727,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   if (C)
     kdense_kernel<<<2048, 256, 0, L.stream>>>(C, n, tw.ld, float(1.0 / eps_ln2), tw.Khi, tw.Klo, tw.Kthi, tw.Ktlo);
   else
-    kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo);
+    kbuild_kernel<<<2048, 256, 0, L.stream>>>(ws.xt, n, tw.ld, tw.Khi, tw.Klo, sp.cost == COST_ABS);
   L.end();
   L.begin(KIND_OTHER);
   tc_dsplit_kernel<<<1184, 256, 0, L.stream>>>(D, n, k, tw.kp, tw.ld, tw.Dhi, tw.Dlo, tw.Dthi, tw.Dtlo);
@@ -738,7 +740,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   if (checks) {  // sum_ij K_ij in FP64, once per solve
     L.begin(KIND_OTHER);
     if (C) kernel_mass_dense_kernel<<<592, 256, 0, L.stream>>>(C, n, 1.0 / sp.eps, ow->kmass);
-    else kernel_mass_kernel<float><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass);
+    else kernel_mass_kernel<float><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass, sp.cost == COST_ABS);
     L.end();
   }
 
@@ -768,7 +770,8 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
     ga.split_stride = (size_t)batch * n;
     if (ga.splits > 1) ga.fix_list = nullptr;  // listed by tc_split_reduce_kernel instead
   }
-  const TcCost cost_src{ws.xt, C, float(1.0 / eps_ln2), 0}, cost_tgt{ws.xt, C, float(1.0 / eps_ln2), 1};
+  const int abs_cost = sp.cost == COST_ABS;
+  const TcCost cost_src{ws.xt, C, float(1.0 / eps_ln2), 0, abs_cost}, cost_tgt{ws.xt, C, float(1.0 / eps_ln2), 1, abs_cost};
   const int red_grid = (int)(((size_t)batch * n + 255) / 256 < 1184 ? ((size_t)batch * n + 255) / 256 : 1184);
   // the BF16 GEMM of an apply: the two-SM kernel (256 x 128 tiles over SM pairs) when the reduction
   // is not split, else the one-SM kernel with its split partial sums

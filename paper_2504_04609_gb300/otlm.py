@@ -28,6 +28,7 @@ EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm
            "otlm_ws_make_targets", "otlm_ws_fit_normalization", "otlm_initial_weights", "otlm_solve_stats",
            "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
+COST = {"sq": 0, "abs": 1}  # grid cost (x_i - x_j)^2 or |x_i - x_j| (otlm_cost_kind)
 
 
 class otlm_config(ctypes.Structure):
@@ -36,7 +37,8 @@ class otlm_config(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("poll_every", ctypes.c_int),
                 ("beta", ctypes.c_double), ("mm_steps", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("gap_tol", ctypes.c_double), ("dw_tol", ctypes.c_double), ("ragged_cta", ctypes.c_int),
-                ("ragged_rows_log2", ctypes.c_int * 16), ("bf16_single_until", ctypes.c_double)]
+                ("ragged_rows_log2", ctypes.c_int * 16), ("bf16_single_until", ctypes.c_double),
+                ("cost", ctypes.c_int)]
 
 
 _LIB = None
@@ -146,15 +148,17 @@ class Handle:
     beta: squared-l2 weight of the "elastic" penalty (alpha sum w + (beta/2) ||w||^2);
     mm_steps: MM steps of the weight update per iteration (1 in Algorithm 1);
     check_every, gap_tol, dw_tol: the FP64 objective / gap checks and the further stopping
-    criteria of otlm_config."""
+    criteria of otlm_config; cost: "sq" (squared distance, default) or "abs" (absolute distance)
+    for the grid solves."""
 
     def __init__(self, n_max, k_max, batch_max, precision="fp32", datafit="kl", penalty="l2sq",
                  max_iter=1000, tol=0.0, poll_every=8, stream=None, beta=0.0, mm_steps=1, check_every=0,
-                 gap_tol=0.0, dw_tol=0.0, ragged_cta=0, ragged_rows_log2=None, bf16_single_until=0.0):
+                 gap_tol=0.0, dw_tol=0.0, ragged_cta=0, ragged_rows_log2=None, bf16_single_until=0.0, cost="sq"):
         rows = (ctypes.c_int * 16)(*(list(ragged_rows_log2) if ragged_rows_log2 is not None else [0] * 16))
         self.cfg = otlm_config(n_max, k_max, batch_max, PRECISION[precision], DATAFIT[datafit], PENALTY[penalty],
                                max_iter, float(tol), poll_every, float(beta), mm_steps, check_every, float(gap_tol),
-                               float(dw_tol), ragged_cta, rows, float(bf16_single_until))
+                               float(dw_tol), ragged_cta, rows, float(bf16_single_until),
+                               COST[cost] if isinstance(cost, str) else int(cost))
         self.precision = precision
         self._h = ctypes.c_void_p()
         _check(lib().otlm_create(ctypes.byref(self._h), ctypes.byref(self.cfg), stream), "otlm_create")
@@ -272,7 +276,7 @@ def solve_noalloc(x, D, y, eps, lam, alpha, datafit, penalty, max_iter, tol, w, 
 
 
 def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000, tol=0.0,
-          precision="fp32", poll_every=8, beta=0.0, mm_steps=1, bf16_single_until=0.0):
+          precision="fp32", poll_every=8, beta=0.0, mm_steps=1, bf16_single_until=0.0, cost="sq"):
     """One-shot convenience: allocate a handle sized for this problem and solve on the GPU.
 
     Inputs are torch CUDA tensors of the handle's dtype.  Returns SolveResult of CUDA tensors.
@@ -282,7 +286,7 @@ def solve(x, D, y, eps, lam, alpha, datafit, penalty, w0, g0=None, max_iter=1000
     k = D.shape[1]
     h = Handle(n, k, B, precision, datafit, penalty, max_iter, tol, poll_every,
                stream=torch.cuda.current_stream().cuda_stream, beta=beta, mm_steps=mm_steps,
-               bf16_single_until=bf16_single_until)
+               bf16_single_until=bf16_single_until, cost=cost)
     dt = torch.float64 if precision == "fp64" else torch.float32
     w = w0.clone()
     g = torch.zeros_like(y) if g0 is None else g0.clone()

@@ -45,6 +45,11 @@ def squared_cost(x: np.ndarray) -> np.ndarray:
     return (x[:, None] - x[None, :]) ** 2
 
 
+def abs_cost(x: np.ndarray) -> np.ndarray:
+    """Dense C_ij = |x_i - x_j| (the absolute-distance grid cost; pass rho x for rho |x_i - x_j|)."""
+    return np.abs(x[:, None] - x[None, :])
+
+
 def _unit_peaks(x: np.ndarray, mu: np.ndarray, sigma: np.ndarray) -> np.ndarray:
     g = np.exp(-0.5 * ((x[:, None] - mu[None, :]) / sigma[None, :]) ** 2)
     return g / g.sum(axis=0, keepdims=True)

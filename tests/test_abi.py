@@ -49,7 +49,7 @@ def test_strerror_names_every_code():
                                          ("gap_tol", 1e-4),  # a gap tolerance with no checks
                                          ("ragged_cta", 64), ("ragged_cta", 384),
                                          ("bf16_single_until", 1e-2),  # the schedule on an FP32 handle
-                                         ("bf16_single_until", -1.0)])
+                                         ("bf16_single_until", -1.0), ("cost", 2), ("cost", -1)])
 def test_create_rejects_bad_config_without_gpu(field, value):
     _ensure_built()
     cfg = api.otlm_config(64, 8, 4, 0, 1, 2, 10, 0.0, 4)
@@ -120,3 +120,17 @@ def test_precision_schedule_needs_a_tensor_core_handle_and_a_value_below_one():
                 api.lib().otlm_destroy(h)
         else:
             assert got == rc
+
+
+def test_absolute_distance_cost_passes_validation():
+    """cost = 1 (|x_i - x_j|) is a valid grid cost on every precision: without a GPU creation fails
+    only after validation."""
+    _ensure_built()
+    for prec in (0, 1, 2):
+        cfg = api.otlm_config(64, 8, 4, prec, 1, 2, 10, 0.0, 4)
+        cfg.cost = api.COST["abs"]
+        h = ctypes.c_void_p()
+        got = api.lib().otlm_create(ctypes.byref(h), ctypes.byref(cfg), None)
+        assert got != api.OTLM_EINVAL
+        if got == api.OTLM_OK:
+            api.lib().otlm_destroy(h)
