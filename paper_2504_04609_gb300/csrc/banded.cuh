@@ -109,17 +109,30 @@ __device__ __forceinline__ float2 pot_from_pair(float hi, float lo) {
   return pot_norm(a, __fadd_rn(__fsub_rn(hi, a), lo));
 }
 
-// Stage PB split potential rows: dst[pp][c] = src[p0 + pp][t0 - h + c] (-inf outside [0, n) or past
-// the batch).
+// Staged split potentials of PB problems (PB even) in pair layout: column c of problems 2q and 2q+1
+// is the float4 {a_2q, a_2q+1, b_2q, b_2q+1} at dst[q * L + c] (a: integer parts, b: fractions), so
+// one 16-byte load feeds the packed (f32x2) arithmetic of both problems and a warp's load of 32
+// consecutive columns is contiguous.
+__device__ __forceinline__ float4 pair_put(float2 u, float2 v) { return make_float4(u.x, v.x, u.y, v.y); }
+__device__ __forceinline__ float2 pair_get(const float4& q, int which) {
+  return which ? make_float2(q.y, q.w) : make_float2(q.x, q.z);
+}
+
+// Stage PB split potential rows: problem p0 + pp, column c = src[p0 + pp][t0 - h + c] (-inf outside
+// [0, n) or past the batch), in pair layout.
 template <int PB>
-__device__ __forceinline__ void band_stage_rows(const BandArgs& A, const float2* src, float2* dst, int p0, int t0,
+__device__ __forceinline__ void band_stage_rows(const BandArgs& A, const float2* src, float4* dst, int p0, int t0,
                                                 int L) {
+  const float2 none = make_float2(-CUDART_INF_F, 0.f);
 #pragma unroll
-  for (int pp = 0; pp < PB; ++pp)
+  for (int q = 0; q < PB / 2; ++q)
     for (int c = threadIdx.x; c < L; c += BAND_NT) {
       const int j = t0 - A.h + c;
-      dst[pp * L + c] = (p0 + pp < A.batch && j >= 0 && j < A.n) ? src[(size_t)(p0 + pp) * A.n + j]
-                                                                  : make_float2(-CUDART_INF_F, 0.f);
+      const bool in = j >= 0 && j < A.n;
+      const int pa = p0 + 2 * q, pb = pa + 1;
+      const float2 u = (in && pa < A.batch) ? src[(size_t)pa * A.n + j] : none;
+      const float2 v = (in && pb < A.batch) ? src[(size_t)pb * A.n + j] : none;
+      dst[q * L + c] = pair_put(u, v);
     }
 }
 
@@ -136,63 +149,108 @@ struct BandRow {
   }
 };
 
-// sum_t 2^(v_t - c_t - s) with split potentials: ((v_t.a - s.a) - c_t) + (v_t.b - s.b), where the
+// sum_t 2^(v_t - c_t - s) with split potentials, ((v_t.a - s.a) - c_t) + (v_t.b - s.b), where the
 // first difference is exact and a term that matters has an exponent near 0 (so its rounding is
-// relative to a small number).
+// relative to a small number), for the two problems of a pair at once (the pair at v, stride `st`
+// float4 between columns): packed FP32 pairs (f32x2), two chains of additions in flight.
 template <int WR>
-__device__ __forceinline__ float band_sum(const float2* v, const BandRow<WR>& row, int T, float2 s) {
+__device__ __forceinline__ void band_sum2(const float4* v, int st, const BandRow<WR>& row, int T, float2 s0, float2 s1,
+                                          float* sum0, float* sum1) {
   using P = Prec<float>;
-  float sum0 = 0.f, sum1 = 0.f;  // two chains of additions in flight
+  const uint64_t nsa = f2_pack(-s0.x, -s1.x), nsb = f2_pack(-s0.y, -s1.y);
+  uint64_t acc0 = f2_pack(0.f, 0.f), acc1 = acc0;  // two chains of additions in flight
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const float e = P::exp2(((v[t].x - s.x) - row.c(t)) + (v[t].y - s.y));
-    if (t & 1) sum1 += e;
-    else sum0 += e;
+    const float4 q = v[t * st];
+    const float nc = -row.c(t);
+    const uint64_t e = f2_add(f2_add(f2_add(f2_pack(q.x, q.y), nsa), f2_pack(nc, nc)), f2_add(f2_pack(q.z, q.w), nsb));
+    float e0, e1;
+    f2_unpack(e, e0, e1);
+    const uint64_t x = f2_pack(P::exp2(e0), P::exp2(e1));
+    if (t & 1) acc1 = f2_add(acc1, x);
+    else acc0 = f2_add(acc0, x);
   }
-  return sum0 + sum1;
+  f2_unpack(f2_add(acc0, acc1), *sum0, *sum1);
 }
 
-// log2 sum_t 2^(v_t - c_t) over the row's band (v: split potentials in shared memory at stride 1).
-// One pass around `shift`, the previous iteration's log-sum, so the sum is the ratio new / old;
-// when that sum leaves [2^-60, 2^60], or the shift is not finite, the exact two passes (the
-// largest term as the shift, then the sum around it).  Returns the split log-sum and writes the
-// ratio 2^(new - shift).
-template <int WR>
-__device__ __forceinline__ float2 band_lse(const float2* v, const BandRow<WR>& row, int W, float2 shift,
-                                           float* ratio) {
+struct BandLse {
+  float2 la;    // split log-sum
+  float ratio;  // 2^(la - shift)
+};
+// The exact two passes for problem `which` of the pair at v (stride st): the largest term's exponent
+// as the shift (a split value), then the sum around it; the band costs cg[t * cgstride], t < W.
+// Out of line: rare, and it keeps the packed path's registers free.
+__device__ __noinline__ BandLse band_lse_exact(const float4* v, int st, const float* cg, long cgstride, int W,
+                                               int which, float2 sh) {
   using P = Prec<float>;
-  constexpr bool REG = WR > 0;
-  const int T = REG ? WR : W;
-  if (isfinite(shift.x)) {
-    const float sum = band_sum<WR>(v, row, T, shift);
-    if (sum >= 0x1p-60f && sum <= 0x1p60f) {
-      *ratio = sum;
-      return pot_norm(shift.x, shift.y + P::log2(sum));
-    }
-  }
-  float m = -CUDART_INF_F;
+  float m = -CUDART_INF_F, ctm = 0.f;
   int tm = 0;
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const float e = (v[t].x - row.c(t)) + v[t].y;
+  for (int t = 0; t < W; ++t) {
+    const float2 vt = pair_get(v[t * st], which);
+    const float c = cg[t * cgstride];
+    const float e = (vt.x - c) + vt.y;
     if (e > m) {
       m = e;
       tm = t;
+      ctm = c;
     }
   }
+  BandLse r;
   if (!(m > -CUDART_INF_F)) {
-    *ratio = P::exp2(-CUDART_INF_F - shift.x);
-    return make_float2(-CUDART_INF_F, 0.f);
+    r.la = make_float2(-CUDART_INF_F, 0.f);
+    r.ratio = P::exp2(-CUDART_INF_F - sh.x);
+    return r;
   }
-  // the shift: the largest term's exponent as a split value (any shift is exact in real arithmetic)
-  float ctm = 0.f;
-#pragma unroll
-  for (int t = 0; t < T; ++t) ctm = t == tm ? row.c(t) : ctm;
-  const float2 s2 = pot_norm(v[tm].x, v[tm].y - ctm);
-  const float sum = band_sum<WR>(v, row, T, s2);
-  const float2 la = pot_norm(s2.x, s2.y + P::log2(sum));
-  *ratio = P::exp2((la.x - shift.x) + (la.y - shift.y));
-  return la;
+  const float2 vm = pair_get(v[tm * st], which);
+  const float2 s2 = pot_norm(vm.x, vm.y - ctm);
+  float sa = 0.f, sb = 0.f;  // two chains, as the packed path
+  for (int t = 0; t < W; ++t) {
+    const float2 vt = pair_get(v[t * st], which);
+    const float e = P::exp2(((vt.x - s2.x) - cg[t * cgstride]) + (vt.y - s2.y));
+    if (t & 1) sb += e;
+    else sa += e;
+  }
+  r.la = pot_norm(s2.x, s2.y + P::log2(sa + sb));
+  r.ratio = P::exp2((r.la.x - sh.x) + (r.la.y - sh.y));
+  return r;
+}
+
+// log2 sum_t 2^(v_t - c_t) over the row's band for the two problems of a pair: one pass around each
+// problem's shift, the previous iteration's log-sum, so the sum is the ratio new / old; a problem
+// whose shift is not finite or whose sum leaves [2^-60, 2^60] takes the exact two passes alone (the
+// largest term as the shift, then the sum around it).  Returns the split log-sums and the ratios
+// 2^(new - shift).
+template <int WR>
+__device__ __forceinline__ void band_lse2(const float4* v, int st, const BandRow<WR>& row, int W, float2 sh0,
+                                          float2 sh1, float2* la0, float2* la1, float* ratio0, float* ratio1) {
+  using P = Prec<float>;
+  constexpr bool REG = WR > 0;
+  const int T = REG ? WR : W;
+  float sum0 = 0.f, sum1 = 0.f;
+  const bool f0 = isfinite(sh0.x), f1 = isfinite(sh1.x);
+  if (f0 || f1)
+    band_sum2<WR>(v, st, row, T, f0 ? sh0 : make_float2(0.f, 0.f), f1 ? sh1 : make_float2(0.f, 0.f), &sum0, &sum1);
+  const bool ok0 = f0 && sum0 >= 0x1p-60f && sum0 <= 0x1p60f, ok1 = f1 && sum1 >= 0x1p-60f && sum1 <= 0x1p60f;
+  if (ok0) {
+    *ratio0 = sum0;
+    *la0 = pot_norm(sh0.x, sh0.y + P::log2(sum0));
+  }
+  if (ok1) {
+    *ratio1 = sum1;
+    *la1 = pot_norm(sh1.x, sh1.y + P::log2(sum1));
+  }
+  if (!ok0 || !ok1) {  // rare: the exact path, one problem at a time, with the band read from memory
+    if (!ok0) {
+      const BandLse r = band_lse_exact(v, st, row.cg, row.cgstride, W, 0, sh0);
+      *la0 = r.la;
+      *ratio0 = r.ratio;
+    }
+    if (!ok1) {
+      const BandLse r = band_lse_exact(v, st, row.cg, row.cgstride, W, 1, sh1);
+      *la1 = r.la;
+      *ratio1 = r.ratio;
+    }
+  }
 }
 
 // Fixed-order block sum of PB per-thread values; thread pp < PB gets the total of value pp.
@@ -244,7 +302,8 @@ __global__ void __launch_bounds__(BAND_NT, 3) band_source_kernel(BandArgs A) {
   const int n = A.n, h = A.h, W = 2 * h + 1, L = BAND_TN + 2 * h, t0 = tile * BAND_TN;
   bool live[PB];
   if (!band_live<PB>(A, p0, live)) return;
-  float2* gs = reinterpret_cast<float2*>(smem);
+  static_assert(PB % 2 == 0, "problems go in pairs");
+  float4* gs = reinterpret_cast<float4*>(smem);
   float* red = smem + 2 * (size_t)PB * L;
   band_stage_rows<PB>(A, A.G2, gs, p0, t0, L);
   const int i = t0 + threadIdx.x;
@@ -269,14 +328,20 @@ __global__ void __launch_bounds__(BAND_NT, 3) band_source_kernel(BandArgs A) {
   const bool check = A.it > 0;
   float part[PB];
 #pragma unroll
-  for (int pp = 0; pp < PB; ++pp) {
-    part[pp] = 0.f;
-    if (!live[pp] || !valid) continue;
-    const size_t o = (size_t)(p0 + pp) * n + i;
-    float ratio;
-    const float2 la = band_lse<WR>(gs + pp * L + threadIdx.x, row, W, old[pp], &ratio);
-    if (check && sv[pp] > 0.f) part[pp] = sv[pp] * fabsf(ratio - 1.f);
-    A.LA2[o] = la;
+  for (int q = 0; q < PB / 2; ++q) {
+    const int pa = 2 * q, pb = pa + 1;
+    part[pa] = part[pb] = 0.f;
+    if (!valid || !(live[pa] || live[pb])) continue;
+    float2 la[2];
+    float ratio[2];
+    band_lse2<WR>(gs + q * L + threadIdx.x, 1, row, W, old[pa], old[pb], &la[0], &la[1], &ratio[0], &ratio[1]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int pp = pa + u;
+      if (!live[pp]) continue;
+      if (check && sv[pp] > 0.f) part[pp] = sv[pp] * fabsf(ratio[u] - 1.f);
+      A.LA2[(size_t)(p0 + pp) * n + i] = la[u];
+    }
   }
   if (!check) return;
   const float tot = band_block_sums<PB>(part, red);
@@ -436,7 +501,8 @@ __global__ void __launch_bounds__(BAND_NT, 3) band_target_kernel(BandArgs A) {
   const int n = A.n, h = A.h, W = 2 * h + 1, L = BAND_TN + 2 * h, t0 = tile * BAND_TN;
   bool live[PB];
   if (!band_live<PB>(A, p0, live)) return;
-  float2* fs = reinterpret_cast<float2*>(smem);
+  static_assert(PB % 2 == 0, "problems go in pairs");
+  float4* fs = reinterpret_cast<float4*>(smem);
   float* red = smem + 2 * (size_t)PB * L;
   float mass[PB];
 #pragma unroll
@@ -457,6 +523,7 @@ __global__ void __launch_bounds__(BAND_NT, 3) band_target_kernel(BandArgs A) {
       }
     }
     const bool own = c >= h && c < h + BAND_TN && i < n;
+    float2 f2s[PB];
 #pragma unroll
     for (int pp = 0; pp < PB; ++pp) {
       float2 f2 = make_float2(-CUDART_INF_F, 0.f);
@@ -473,8 +540,10 @@ __global__ void __launch_bounds__(BAND_NT, 3) band_target_kernel(BandArgs A) {
           mass[pp] += sv;
         }
       }
-      fs[pp * L + c] = f2;
+      f2s[pp] = f2;
     }
+#pragma unroll
+    for (int q = 0; q < PB / 2; ++q) fs[q * L + c] = pair_put(f2s[2 * q], f2s[2 * q + 1]);
   }
   const int j = t0 + threadIdx.x;
   const bool valid = j < n;
@@ -500,13 +569,20 @@ __global__ void __launch_bounds__(BAND_NT, 3) band_target_kernel(BandArgs A) {
   }
   __syncthreads();
 #pragma unroll
-  for (int pp = 0; pp < PB; ++pp) {
-    if (!live[pp] || !valid) continue;
-    const size_t o = (size_t)(p0 + pp) * n + j;
-    float ratio;
-    const float2 lb = band_lse<WR>(fs + pp * L + threadIdx.x, col, W, old[pp], &ratio);
-    A.LB2[o] = lb;
-    A.G2[o] = band_datafit(A, lb, yv[pp]);
+  for (int q = 0; q < PB / 2; ++q) {
+    const int pa = 2 * q, pb = pa + 1;
+    if (!valid || !(live[pa] || live[pb])) continue;
+    float2 lb[2];
+    float ratio[2];
+    band_lse2<WR>(fs + q * L + threadIdx.x, 1, col, W, old[pa], old[pb], &lb[0], &lb[1], &ratio[0], &ratio[1]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int pp = pa + u;
+      if (!live[pp]) continue;
+      const size_t o = (size_t)(p0 + pp) * n + j;
+      A.LB2[o] = lb[u];
+      A.G2[o] = band_datafit(A, lb[u], yv[pp]);
+    }
   }
   const float tot = band_block_sums<PB>(mass, red);
   if (threadIdx.x < PB && band_live_one(A, p0 + threadIdx.x))
@@ -808,7 +884,7 @@ inline cudaError_t solve_device_band(const Launch& L, const BandWorkspace& ws, c
   band_init_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, 1.0 / eps_ln2);
   L.end();
 
-  e = c.batch >= 4 ? band_iterate_pb<4>(L, A, ws, sp) : band_iterate_pb<1>(L, A, ws, sp);
+  e = c.batch >= 4 ? band_iterate_pb<4>(L, A, ws, sp) : band_iterate_pb<2>(L, A, ws, sp);
   if (e != cudaSuccess) return e;
   L.begin(KIND_OTHER);
   band_finalize_kernel<<<1184, 256, 0, L.stream>>>(A, c.w, c.g, c.t_out, c.iters_out, c.err_out, c.status_out,
