@@ -187,18 +187,20 @@ int otlm_solve(otlm_handle h, int batch, int n, int k,
                int* iters_out, void* err_out, int* status_out);
 
 /* Same as otlm_solve for a cost given as a dense matrix instead of a grid: C [n][n] (device,
- * row-major, FP32) is the cost of moving mass from source bin i (row) to target bin j (column),
- * shared by the batch; it need not be symmetric (e.g. the non-stationary cost rho (x_i - x_j)^2 /
- * x_i^2 of the muonic X-ray spectra appendix), and +inf forbids a pair (a truncated cost).  Both
- * kernel applies of Algorithm 1 follow Q_ij = u2_i K_ij u1_j with K = exp(-C / eps): the source
- * apply uses K, the target apply K^T, built once per call (BF16 hi/lo) in the workspace.
- * Tensor-core handles only (OTLM_PREC_BF16_TC; otherwise OTLM_EUNSUPPORTED); errors as
- * otlm_solve.  otlm_objective covers the grid cost only. */
+ * row-major, the handle's element type) is the cost of moving mass from source bin i (row) to
+ * target bin j (column), shared by the batch; it need not be symmetric (e.g. the non-stationary
+ * cost rho (x_i - x_j)^2 / x_i^2 of the muonic X-ray spectra appendix), and +inf forbids a pair (a
+ * truncated cost; NaN and -inf are not allowed).  Both kernel applies of Algorithm 1 follow
+ * Q_ij = u2_i K_ij u1_j with K = exp(-C / eps): the source apply sums row i of K, the target apply
+ * column j.  Tensor-core handles build K and K^T once per call (BF16 hi/lo) in the workspace; FP32
+ * and FP64 handles read C in tiles through shared memory in every apply (log domain, as the grid
+ * solves; check_every and the stopping criteria as otlm_solve).  Errors as otlm_solve.
+ * otlm_objective covers the grid costs only. */
 int otlm_solve_cost(otlm_handle h, int batch, int n, int k,
-                    const float* C, const float* D, const float* y,
+                    const void* C, const void* D, const void* y,
                     double eps, double lam, double alpha,
-                    float* w, float* g, float* t_out,
-                    int* iters_out, float* err_out, int* status_out);
+                    void* w, void* g, void* t_out,
+                    int* iters_out, void* err_out, int* status_out);
 
 /* Same as otlm_solve, with x, D, y, w (in/out), g (in/out, may be NULL) and t_out (may be
  * NULL) in HOST memory (pageable or pinned), and iters_out / status_out / err_out as host

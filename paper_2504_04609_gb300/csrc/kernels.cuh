@@ -6,6 +6,8 @@
 //   LA2_i = log2 sum_j 2^(G2_j - (xt_i - xt_j)^2),   LB2_j = log2 sum_i 2^(F2_i - (xt_i - xt_j)^2).
 // The absolute-distance grid cost C_ij = |x_i - x_j| (the cost of the paper's demonstrations and
 // scalability tests, there scaled by rho: pass rho x) takes xt = x / (eps ln2) and |xt_i - xt_j|.
+// A dense cost C [n][n] (any, e.g. non-symmetric or truncated with +inf) is read in tiles: the
+// source apply sums along row i of C, the target apply along column j, in units C / (eps ln2).
 #pragma once
 
 #include "common.cuh"
@@ -13,7 +15,7 @@
 namespace otlm {
 
 enum { EPI_SOURCE = 0, EPI_TARGET = 1 };
-enum { COST_SQ = 0, COST_ABS = 1 };  // grid cost in log2 units: (xt_i - xt_j)^2 or |xt_i - xt_j|
+enum { COST_SQ = 0, COST_ABS = 1, COST_DENSE = 2 };  // (xt_i - xt_j)^2, |xt_i - xt_j|, or C_ij / (eps ln2)
 
 template <int COST, typename T>
 __device__ __forceinline__ T grid_cost(T d) {
@@ -55,6 +57,11 @@ struct ApplyArgs {
   T tv_bound;           // lam / (eps ln2)
   T lam_over_eps;       // lam / eps
   T log_lam_over_eps;   // ln(lam / eps)
+  // dense cost (the COST_DENSE kernels): C [n][n] row-major, the source apply reading row i (the
+  // output row) and the target apply (c_trans = 1) column j; scaled by c_scale = 1 / (eps ln2)
+  const T* C;
+  T c_scale;
+  int c_trans;
 };
 
 // Tile of the kernel apply: TB = RB*WB problems x TI = 32*RI*WI rows; warp (wb, wi) owns RB
@@ -103,9 +110,30 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   return r;
 }
 
-// Stage one chunk of TJ columns: the CTA's TB input rows into in_s[j][b] and the grid values.
+// Dense-cost tile of a chunk, c_s[jj][il] (row pitch TI + 1) = C2 of output row i0 + il and summed
+// index j0 + jj: C[i][j] for the source apply (read along j, transposed into shared memory), C[j][i]
+// for the target apply (read along i); +inf outside [0, n), so that the term vanishes.
 template <typename T, class Cfg>
-__device__ __forceinline__ void stage_chunk(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s, int j0) {
+__device__ __forceinline__ void stage_cost_tile(const ApplyArgs<T>& A, T* c_s, int i0, int j0) {
+  constexpr int TI = Cfg::TI, TJ = Cfg::TJ, NT = Cfg::NT, TIP = TI + 1;
+  const int n = A.n;
+  const T inf = -Prec<T>::ninf();
+  for (int e = threadIdx.x; e < TI * TJ; e += NT) {
+    if (!A.c_trans) {  // consecutive threads: consecutive j of one row i
+      const int il = e / TJ, jj = e - il * TJ, i = i0 + il, j = j0 + jj;
+      c_s[jj * TIP + il] = (i < n && j < n) ? A.C[(size_t)i * n + j] * A.c_scale : inf;
+    } else {  // consecutive threads: consecutive i of one row j of C
+      const int jj = e / TI, il = e - jj * TI, i = i0 + il, j = j0 + jj;
+      c_s[jj * TIP + il] = (i < n && j < n) ? A.C[(size_t)j * n + i] * A.c_scale : inf;
+    }
+  }
+}
+
+// Stage one chunk of TJ columns: the CTA's TB input rows into in_s[j][b] and the grid values (or,
+// for a dense cost, the cost tile).
+template <typename T, class Cfg, int COST>
+__device__ __forceinline__ void stage_chunk(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s, T* c_s,
+                                            int i0, int j0) {
   using P = Prec<T>;
   constexpr int TB = Cfg::TB, TJ = Cfg::TJ, NT = Cfg::NT;
   const int n = A.n;
@@ -114,27 +142,37 @@ __device__ __forceinline__ void stage_chunk(const ApplyArgs<T>& A, const int* pr
     const int bb = e / TJ, jj = e - bb * TJ, j = j0 + jj, p = prob_s[bb];
     in_s[jj * TB + bb] = (p >= 0 && j < n) ? A.in[(size_t)p * n + j] : P::ninf();
   }
-  for (int jj = threadIdx.x; jj < TJ; jj += NT) xj_s[jj] = (j0 + jj < n) ? A.xt[j0 + jj] : T(0);
+  if constexpr (COST == COST_DENSE) stage_cost_tile<T, Cfg>(A, c_s, i0, j0);
+  else
+    for (int jj = threadIdx.x; jj < TJ; jj += NT) xj_s[jj] = (j0 + jj < n) ? A.xt[j0 + jj] : T(0);
   __syncthreads();
 }
 
 // Exact shift: m = max_j (in_bj - c_ij), c_ij the grid cost (scalar; the rare path).
+// The cost of term jj for row r: the grid cost of xi[r] - xj, or the dense tile's entry of the
+// thread's row il0 + 32 r.
 template <typename T, class Cfg, int COST>
-__device__ __forceinline__ void sweep_max(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
-                                          const T (&xi)[Cfg::RI], int wb, T (&m)[Cfg::RB][Cfg::RI]) {
+__device__ __forceinline__ T term_cost(const T (&xi)[Cfg::RI], T xj, const T* c_s, int il0, int jj, int r) {
+  if constexpr (COST == COST_DENSE) return c_s[jj * (Cfg::TI + 1) + il0 + 32 * r];
+  else return grid_cost<COST>(xi[r] - xj);
+}
+
+template <typename T, class Cfg, int COST>
+__device__ __forceinline__ void sweep_max(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s, T* c_s, int i0,
+                                          int il0, const T (&xi)[Cfg::RI], int wb, T (&m)[Cfg::RB][Cfg::RI]) {
   constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
   for (int j0 = 0; j0 < A.n; j0 += TJ) {
-    stage_chunk<T, Cfg>(A, prob_s, in_s, xj_s, j0);
+    stage_chunk<T, Cfg, COST>(A, prob_s, in_s, xj_s, c_s, i0, j0);
 #pragma unroll 4
     for (int jj = 0; jj < TJ; ++jj) {
-      const T xj = xj_s[jj];
+      const T xj = COST == COST_DENSE ? T(0) : xj_s[jj];
       T v[RB];
       VecLoad<T, RB>::ld(in_s + jj * TB + wb * RB, v);
 #pragma unroll
       for (int r = 0; r < RI; ++r) {
-        const T d = xi[r] - xj;
+        const T c = term_cost<T, Cfg, COST>(xi, xj, c_s, il0, jj, r);
 #pragma unroll
-        for (int q = 0; q < RB; ++q) m[q][r] = fmax(m[q][r], v[q] - grid_cost<COST>(d));
+        for (int q = 0; q < RB; ++q) m[q][r] = fmax(m[q][r], v[q] - c);
       }
     }
   }
@@ -142,16 +180,16 @@ __device__ __forceinline__ void sweep_max(const ApplyArgs<T>& A, const int* prob
 
 // Sum with a known shift: acc = sum_j 2^(in_bj - m_bi - c_ij).  Generic (double) version.
 template <typename T, class Cfg, int COST>
-__device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s,
-                                          const T (&xi)[Cfg::RI], int wb, const T (&m)[Cfg::RB][Cfg::RI],
+__device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob_s, T* in_s, T* xj_s, T* c_s, int i0,
+                                          int il0, const T (&xi)[Cfg::RI], int wb, const T (&m)[Cfg::RB][Cfg::RI],
                                           T (&acc)[Cfg::RB][Cfg::RI]) {
   using P = Prec<T>;
   constexpr int RB = Cfg::RB, RI = Cfg::RI, TB = Cfg::TB, TJ = Cfg::TJ;
   for (int j0 = 0; j0 < A.n; j0 += TJ) {
-    stage_chunk<T, Cfg>(A, prob_s, in_s, xj_s, j0);
+    stage_chunk<T, Cfg, COST>(A, prob_s, in_s, xj_s, c_s, i0, j0);
 #pragma unroll 4
     for (int jj = 0; jj < TJ; ++jj) {
-      const T xj = xj_s[jj];
+      const T xj = COST == COST_DENSE ? T(0) : xj_s[jj];
       T v[RB];
       VecLoad<T, RB>::ld(in_s + jj * TB + wb * RB, v);
 #pragma unroll
@@ -159,7 +197,8 @@ __device__ __forceinline__ void sweep_sum(const ApplyArgs<T>& A, const int* prob
         const T d = xi[r] - xj;
 #pragma unroll
         for (int q = 0; q < RB; ++q) {
-          if constexpr (COST == COST_ABS) acc[q][r] += P::exp2((v[q] - m[q][r]) - fabs(d));
+          if constexpr (COST == COST_DENSE) acc[q][r] += P::exp2((v[q] - m[q][r]) - c_s[jj * (Cfg::TI + 1) + il0 + 32 * r]);
+          else if constexpr (COST == COST_ABS) acc[q][r] += P::exp2((v[q] - m[q][r]) - fabs(d));
           else acc[q][r] += P::exp2(fma(-d, d, v[q] - m[q][r]));
         }
       }
@@ -297,6 +336,7 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
   constexpr int RB = Cfg::RB, RI = Cfg::RI, WB = Cfg::WB, TB = Cfg::TB, TI = Cfg::TI, TJ = Cfg::TJ;
   __shared__ __align__(16) T in_s[TJ * TB];
   __shared__ __align__(16) T xj_s[2 * TJ];
+  __shared__ T c_s[COST == COST_DENSE ? TJ * (TI + 1) : 1];
   __shared__ int prob_s[TB];
   const int na = *A.n_active;
   const int b0 = blockIdx.y * TB;
@@ -314,11 +354,12 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
   T xi[RI], di[RI];
   // tile centre for the FP32 expansion (any value is exact in real arithmetic; the middle of the
   // tile keeps the squares small)
-  const T xc = T(0.5) * (A.xt[min(i0, n - 1)] + A.xt[min(i0 + TI - 1, n - 1)]);
+  const T xc = COST == COST_DENSE ? T(0) : T(0.5) * (A.xt[min(i0, n - 1)] + A.xt[min(i0 + TI - 1, n - 1)]);
+  const int il0 = wi * 32 * RI + lane;  // the thread's first row within the tile (dense-cost tiles)
 #pragma unroll
   for (int r = 0; r < RI; ++r) {
-    row[r] = i0 + wi * 32 * RI + r * 32 + lane;
-    xi[r] = row[r] < n ? A.xt[row[r]] : xc;
+    row[r] = i0 + il0 + r * 32;
+    xi[r] = (COST != COST_DENSE && row[r] < n) ? A.xt[row[r]] : xc;
     di[r] = xi[r] - xc;
   }
   T m[RB][RI], acc[RB][RI];
@@ -337,8 +378,9 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
       }
     safe = __syncthreads_or(bad);
     if (!safe) {
-      if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m, acc);
-      else sweep_sum<T, Cfg, COST>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+      if constexpr (sizeof(T) == 4 && COST != COST_DENSE)
+        sweep_sum_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m, acc);
+      else sweep_sum<T, Cfg, COST>(A, prob_s, in_s, xj_s, c_s, i0, il0, xi, wb, m, acc);
       bad = false;
 #pragma unroll
       for (int q = 0; q < RB; ++q)
@@ -355,15 +397,16 @@ __global__ void __launch_bounds__(Cfg::NT) apply_kernel(ApplyArgs<T> A) {
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r) { m[q][r] = P::ninf(); acc[q][r] = T(0); }
-    if constexpr (sizeof(T) == 4) sweep_max_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m);
-    else sweep_max<T, Cfg, COST>(A, prob_s, in_s, xj_s, xi, wb, m);
+    if constexpr (sizeof(T) == 4 && COST != COST_DENSE) sweep_max_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m);
+    else sweep_max<T, Cfg, COST>(A, prob_s, in_s, xj_s, c_s, i0, il0, xi, wb, m);
 #pragma unroll
     for (int q = 0; q < RB; ++q)
 #pragma unroll
       for (int r = 0; r < RI; ++r)
         if (!(m[q][r] > P::ninf())) m[q][r] = T(0);  // every term vanishes: the sum stays 0
-    if constexpr (sizeof(T) == 4) sweep_sum_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m, acc);
-      else sweep_sum<T, Cfg, COST>(A, prob_s, in_s, xj_s, xi, wb, m, acc);
+    if constexpr (sizeof(T) == 4 && COST != COST_DENSE)
+      sweep_sum_f32<Cfg, COST>(A, prob_s, in_s, xj_s, xc, xi, di, wb, m, acc);
+    else sweep_sum<T, Cfg, COST>(A, prob_s, in_s, xj_s, c_s, i0, il0, xi, wb, m, acc);
   }
   const bool prev_shift = SHIFT == SHIFT_PREV && !safe;  // then acc = a_new / a_old exactly
 
@@ -657,7 +700,8 @@ __global__ void prep_kernel(PrepArgs<T> A) {
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nk = (size_t)A.n * A.k, bn = (size_t)A.batch * A.n, bk = (size_t)A.batch * A.k;
   if (A.x)  // NULL when the cost is given as a dense matrix
-    for (size_t e = tid; e < (size_t)A.n; e += stride) A.xt[e] = A.x[e] * A.xscale;
+    if (A.x)  // no grid with a dense cost
+      for (size_t e = tid; e < (size_t)A.n; e += stride) A.xt[e] = A.x[e] * A.xscale;
   for (size_t e = tid; e < nk; e += stride) {
     const size_t i = e / A.k, j = e - i * A.k;
     A.Dt[j * A.n + i] = A.D[e];

@@ -40,8 +40,9 @@ __global__ void kernel_mass_kernel(const T* x, int n, double inv_eps, double* ou
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
-// sum_ij exp(-C_ij / eps) for a dense cost C [n][n] (FP32, +inf allowed) in FP64.
-static __global__ void kernel_mass_dense_kernel(const float* C, int n, double inv_eps, double* out) {
+// sum_ij exp(-C_ij / eps) for a dense cost C [n][n] (+inf allowed) in FP64.
+template <typename T>
+__global__ void kernel_mass_dense_kernel(const T* C, int n, double inv_eps, double* out) {
   __shared__ double red[32];
   double acc = 0.0;
   const size_t nn = (size_t)n * n;

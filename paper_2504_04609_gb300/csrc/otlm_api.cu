@@ -108,7 +108,7 @@ SolveParams params(const otlm_ctx* h, int batch, int n, int k, double eps, doubl
   return sp;
 }
 
-// C: dense cost [n][n] (tensor-core handles only) or NULL for the grid cost from x
+// C: dense cost [n][n] or NULL for the grid cost from x
 template <typename T>
 int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* C, const void* D, const void* y, void* w,
               void* g, void* t_out, int* iters_out, void* err_out, int* status_out) {
@@ -132,7 +132,7 @@ int run_solve(otlm_ctx* h, const SolveParams& sp, const void* x, const void* C, 
                               (float*)g, (float*)t_out, iters_out, (float*)err_out, status_out);
   } else {
     e = otlm::solve_device<T>(L, ws, lay.obj ? &ow : nullptr, sp, (const T*)x, (const T*)D, (const T*)y, (T*)w,
-                              (T*)g, (T*)t_out, iters_out, (T*)err_out, status_out);
+                              (T*)g, (T*)t_out, iters_out, (T*)err_out, status_out, (const T*)C);
   }
   if (e == cudaErrorLaunchTimeout) return OTLM_ETIMEOUT;
   return e == cudaSuccess ? OTLM_OK : OTLM_ECUDA;
@@ -335,14 +335,15 @@ int otlm_solve(otlm_handle h, int batch, int n, int k, const void* x, const void
   return run_solve<float>(h, sp, x, nullptr, D, y, w, g, t_out, iters_out, err_out, status_out);
 }
 
-int otlm_solve_cost(otlm_handle h, int batch, int n, int k, const float* C, const float* D, const float* y,
-                    double eps, double lam, double alpha, float* w, float* g, float* t_out, int* iters_out,
-                    float* err_out, int* status_out) {
+int otlm_solve_cost(otlm_handle h, int batch, int n, int k, const void* C, const void* D, const void* y,
+                    double eps, double lam, double alpha, void* w, void* g, void* t_out, int* iters_out,
+                    void* err_out, int* status_out) {
   if (!h || !C || !D || !y || !w) return OTLM_EINVAL;
-  if (h->cfg.precision != OTLM_PREC_BF16_TC) return OTLM_EUNSUPPORTED;
   int rc = check_problem(h, batch, n, k, eps, lam, alpha);
   if (rc != OTLM_OK) return rc;
   const SolveParams sp = params(h, batch, n, k, eps, lam, alpha);
+  if (h->cfg.precision == OTLM_PREC_FP64)
+    return run_solve<double>(h, sp, nullptr, C, D, y, w, g, t_out, iters_out, err_out, status_out);
   return run_solve<float>(h, sp, nullptr, C, D, y, w, g, t_out, iters_out, err_out, status_out);
 }
 

@@ -230,7 +230,10 @@ template <typename T, typename Cfg, int EPI>
 void launch_apply_cfg(const Launch& L, const ApplyArgs<T>& a, bool first, int batch, int n, int cost) {
   const dim3 grid((n + Cfg::TI - 1) / Cfg::TI, (batch + Cfg::TB - 1) / Cfg::TB);
   L.begin(KIND_APPLY);
-  if (cost == COST_ABS) {
+  if (a.C) {
+    if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG, COST_DENSE><<<grid, Cfg::NT, 0, L.stream>>>(a);
+    else apply_kernel<T, Cfg, EPI, SHIFT_PREV, COST_DENSE><<<grid, Cfg::NT, 0, L.stream>>>(a);
+  } else if (cost == COST_ABS) {
     if (first) apply_kernel<T, Cfg, EPI, SHIFT_DIAG, COST_ABS><<<grid, Cfg::NT, 0, L.stream>>>(a);
     else apply_kernel<T, Cfg, EPI, SHIFT_PREV, COST_ABS><<<grid, Cfg::NT, 0, L.stream>>>(a);
   } else {
@@ -291,7 +294,7 @@ void objective_eval(const Launch& L, const Workspace<T>& ws, const ObjWorkspace<
 template <typename T>
 cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorkspace<T>* ow, const SolveParams& sp,
                          const T* x, const T* D, const T* y, T* w, T* g, T* t_out, int* iters_out, T* err_out,
-                         int* status_out) {
+                         int* status_out, const T* C = nullptr) {
   const int batch = sp.batch, n = sp.n, k = sp.k;
   const double eps_ln2 = sp.eps * kLn2;
   const bool checks = ow && sp.check_every > 0;
@@ -318,14 +321,17 @@ cudaError_t solve_device(const Launch& L, const Workspace<T>& ws, const ObjWorks
     cudaError_t e = cudaMemsetAsync(ow->kmass, 0, sizeof(double), L.stream);
     if (e != cudaSuccess) return e;
     L.begin(KIND_OTHER);
-    kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass, sp.cost == COST_ABS);
+    if (C) kernel_mass_dense_kernel<T><<<592, 256, 0, L.stream>>>(C, n, 1.0 / sp.eps, ow->kmass);
+    else kernel_mass_kernel<T><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass, sp.cost == COST_ABS);
     L.end();
   }
 
   ApplyArgs<T> src{};
   src.in = ws.G2; src.out = ws.LA2; src.xt = ws.xt; src.active = ws.active; src.n_active = ws.n_active;
   src.n = n; src.S = ws.S; src.err_acc = ws.err_acc;
+  src.C = C; src.c_scale = T(1.0 / eps_ln2); src.c_trans = 0;  // dense cost (or none: the grid)
   ApplyArgs<T> tgt = src;
+  tgt.c_trans = 1;
   tgt.in = ws.F2; tgt.out = ws.LB2; tgt.check = 0; tgt.y = y; tgt.G2 = ws.G2; tgt.datafit = sp.datafit;
   tgt.kl_coef = T(sp.lam / (sp.eps + sp.lam));
   tgt.tv_bound = T(sp.lam / eps_ln2);

@@ -739,7 +739,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   if (e != cudaSuccess) return e;
   if (checks) {  // sum_ij K_ij in FP64, once per solve
     L.begin(KIND_OTHER);
-    if (C) kernel_mass_dense_kernel<<<592, 256, 0, L.stream>>>(C, n, 1.0 / sp.eps, ow->kmass);
+    if (C) kernel_mass_dense_kernel<float><<<592, 256, 0, L.stream>>>(C, n, 1.0 / sp.eps, ow->kmass);
     else kernel_mass_kernel<float><<<592, 256, 0, L.stream>>>(x, n, 1.0 / sp.eps, ow->kmass, sp.cost == COST_ABS);
     L.end();
   }

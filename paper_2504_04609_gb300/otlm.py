@@ -199,7 +199,7 @@ class Handle:
 
     def solve_cost(self, C, D, y, eps, lam, alpha, w, g=None, t_out=None, iters=None, err=None, status=None):
         """otlm_solve_cost: a dense cost C [n][n] (torch CUDA tensor; row = source bin, column = target
-        bin, need not be symmetric, +inf forbids a pair) instead of a grid; tensor-core handles only."""
+        bin, need not be symmetric, +inf forbids a pair; the handle's element type) instead of a grid."""
         B, n = y.shape
         k = D.shape[1]
         rc = lib().otlm_solve_cost(self._h, B, n, k, _ptr(C), _ptr(D), _ptr(y), eps, lam, alpha, _ptr(w), _ptr(g),

@@ -177,28 +177,35 @@ def _dense_cost(kind, x):
     return (xs[:, None] - xs[None, :]) ** 2
 
 
+@pytest.mark.parametrize("prec", ["bf16tc", "fp32", "fp64"])
 @pytest.mark.parametrize("kind,datafit,penalty,eps", [
     ("nonstationary", "kl", "l2sq", 2e-2),
     ("nonstationary", "l2", "l1", 2e-2),
     ("truncated", "kl", "l2sq", 1e-2),
     ("muonic", "tv", "l1", 2e-2),
 ])
-def test_dense_cost_trajectory_parity(kind, datafit, penalty, eps):
-    """otlm_solve_cost with a cost matrix instead of a grid: the source apply uses K, the target
-    apply K^T (a non-symmetric cost makes them differ; +inf entries forbid pairs).  7 problems,
-    n = 300, k = 12, 25 iterations against the oracle's trajectory on the same FP64 cost.  Under
-    the truncated cost some KL targets leave a source bin with no reachable target bin (a_i = 0
-    while s_i > 0), where the MM step is undefined: the oracle returns NaN there and the solver
-    must report OTLM_NONFINITE for exactly those problems."""
-    d = spectra.batch(35, 7, 300, 12, 3)
+def test_dense_cost_trajectory_parity(prec, kind, datafit, penalty, eps):
+    """otlm_solve_cost with a cost matrix instead of a grid: the source apply sums rows of K, the
+    target apply columns (a non-symmetric cost makes them differ; +inf entries forbid pairs), on
+    the tensor-core path (K and K^T built once) and the FP32 / FP64 log-domain paths (C read in
+    tiles by every apply).  7 problems, n = 300 (ragged tiles), k = 12, 25 iterations against the
+    oracle's trajectory on the same cost (1e-5; FP64 1e-9).  Under the truncated cost some KL
+    targets leave a source bin with no reachable target bin (a_i = 0 while s_i > 0), where the MM
+    step is undefined: the oracle returns NaN there and the solver must report OTLM_NONFINITE for
+    exactly those problems."""
+    d = spectra.batch(35, 7, 300, 12, 3, dtype=np.float64 if prec == "fp64" else np.float32)
     C64 = _dense_cost(kind, d["x"])
+    if prec != "fp64":
+        C64 = C64.astype(np.float32).astype(np.float64)  # the oracle sees the cost the GPU gets
     lam, alpha, T = 1.0, 1e-3 if penalty == "l2sq" else 1e-2, 25
     dev = "cuda"
-    C = torch.tensor(C64.astype(np.float32), device=dev)
-    D, y = (torch.tensor(d[k], device=dev) for k in ("D", "y"))
-    w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=torch.float32, device=dev)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    bar = 1e-9 if prec == "fp64" else TOL
+    C = torch.tensor(C64, dtype=dt, device=dev)
+    D, y = (torch.tensor(d[k], dtype=dt, device=dev) for k in ("D", "y"))
+    w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=dt, device=dev)
     B, n = y.shape
-    h = api.Handle(n, 12, B, "bf16tc", datafit, penalty, T, 0.0, poll_every=4)
+    h = api.Handle(n, 12, B, prec, datafit, penalty, T, 0.0, poll_every=4)
     t = torch.empty_like(y)
     it = torch.empty(B, dtype=torch.int32, device=dev)
     st = torch.empty(B, dtype=torch.int32, device=dev)
@@ -215,15 +222,16 @@ def test_dense_cost_trajectory_parity(kind, datafit, penalty, eps):
             assert status[p] == api.NONFINITE, (p, status[p])
             continue
         assert status[p] == api.MAX_ITER, (p, status[p])
-        assert rel_l1(w[p].cpu().numpy(), o["w"]) <= TOL, (p, rel_l1(w[p].cpu().numpy(), o["w"]))
-        assert rel_l1(t[p].cpu().numpy(), o["t"]) <= TOL, (p, rel_l1(t[p].cpu().numpy(), o["t"]))
+        assert rel_l1(w[p].cpu().numpy(), o["w"]) <= bar, (p, rel_l1(w[p].cpu().numpy(), o["w"]))
+        assert rel_l1(t[p].cpu().numpy(), o["t"]) <= bar, (p, rel_l1(t[p].cpu().numpy(), o["t"]))
         compared += 1
     assert compared >= 5
 
 
 def test_dense_cost_of_the_grid_matches_the_grid_solve():
     """The squared-distance cost given as a matrix reproduces the grid solve (both within the 1e-5
-    bar of each other); a non-tensor-core handle refuses the dense cost."""
+    bar of each other) on the tensor-core and the FP32 paths, and the FP32 dense path with the
+    FP64 gap checks on reports the returned states' primal and dual."""
     d = spectra.batch(36, 5, 256, 8, 3)
     g = _solve(d, 1e-2, 1.0, 1e-3, "l2", "l2sq", 20)
     dev = "cuda"
@@ -238,10 +246,25 @@ def test_dense_cost_of_the_grid_matches_the_grid_solve():
     for p in range(5):
         assert rel_l1(w[p].cpu().numpy(), g["w"][p]) <= TOL
         assert rel_l1(t[p].cpu().numpy(), g["t"][p]) <= TOL
-    h32 = api.Handle(256, 8, 5, "fp32", "l2", "l2sq", 20, 0.0)
-    with pytest.raises(api.OTLMError):
-        h32.solve_cost(C, D, y, 1e-2, 1.0, 1e-3, w)
+    g32 = _solve(d, 1e-2, 1.0, 1e-3, "l2", "l2sq", 20, precision="fp32")
+    w = torch.tensor(spectra.initial_weights(d["y"], d["D"]), dtype=torch.float32, device=dev)
+    g = torch.zeros_like(y)
+    h32 = api.Handle(256, 8, 5, "fp32", "l2", "l2sq", 20, 0.0, check_every=10)
+    h32.solve_cost(C, D, y, 1e-2, 1.0, 1e-3, w, g, t)
+    P = torch.empty(5, dtype=torch.float64, device=dev)
+    Dv = torch.empty(5, dtype=torch.float64, device=dev)
+    h32.solve_stats(5, None, P, Dv)
+    torch.cuda.synchronize()
     h32.close()
+    C64 = _dense_cost("grid", d["x"]).astype(np.float32).astype(np.float64)
+    for p in range(5):
+        assert rel_l1(w[p].cpu().numpy(), g32["w"][p]) <= TOL
+        assert rel_l1(t[p].cpu().numpy(), g32["t"][p]) <= TOL
+        Po, Do, _ = oracle.objective_and_dual(w[p].cpu().numpy().astype(np.float64),
+                                              g[p].cpu().numpy().astype(np.float64), C64,
+                                              d["D"].astype(np.float64), d["y"][p].astype(np.float64), 1e-2, 1.0,
+                                              1e-3, "l2", "l2sq")
+        assert P[p].item() == pytest.approx(Po, rel=2e-6) and Dv[p].item() == pytest.approx(Do, rel=2e-6)
 
 
 def test_precision_schedule_on_the_squared_error_workload():
