@@ -406,6 +406,17 @@ int otlm_solve_noalloc(int batch, int n, int k, const float* x, const float* D, 
                        int* status_out, void* cuda_stream);
 
 /* Static description of a status code; never NULL. */
+/* Self-check of the tensor-core kernels' bounded waits (no fault and no hang: the waits are what is
+ * exercised).  Runs one small BF16 GEMM (256 x 256 x 256, zero operands) on the one-SM kernel
+ * (two_sm = 0) or the two-SM kernel (two_sm != 0) with a 20 ms wait limit, whose first CTA arms its
+ * first ring stage but never issues the copies: the waits on that stage and the ones behind it run
+ * out, the kernel records an error code and leaves after releasing its tensor memory, and the device
+ * stays usable.  Returns OTLM_ETIMEOUT with the first recorded code in *code_out (1: operand copies,
+ * 2: ring stage release, 3: accumulator), OTLM_OK if no expiry was detected (a defect),
+ * OTLM_ENOMEM / OTLM_ECUDA, OTLM_EINVAL for a null code_out.  Allocates and frees about 1 MB and
+ * a stream of its own. */
+int otlm_check_wait_expiry(int two_sm, int* code_out);
+
 const char* otlm_strerror(int code);
 
 #ifdef __cplusplus

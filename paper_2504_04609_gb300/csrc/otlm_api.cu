@@ -656,6 +656,39 @@ int otlm_get_timing(otlm_handle h, double* ms, long long* launches) {
   return OTLM_OK;
 }
 
+int otlm_check_wait_expiry(int two_sm, int* code_out) {
+  if (!code_out) return OTLM_EINVAL;
+  *code_out = 0;
+  constexpr int M = 256, N = 256, Kd = 256;
+  const size_t op = sizeof(__nv_bfloat16) * (size_t)M * Kd, outb = sizeof(float) * (size_t)M * N;
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, 4 * op + outb + 256) != cudaSuccess) return OTLM_ENOMEM;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 4 * op + outb + 256, st);
+  const __nv_bfloat16* a_hi = reinterpret_cast<const __nv_bfloat16*>(buf);
+  const __nv_bfloat16* a_lo = reinterpret_cast<const __nv_bfloat16*>(buf + op);
+  const __nv_bfloat16* b_hi = reinterpret_cast<const __nv_bfloat16*>(buf + 2 * op);
+  const __nv_bfloat16* b_lo = reinterpret_cast<const __nv_bfloat16*>(buf + 3 * op);
+  int* err = reinterpret_cast<int*>(buf + 4 * op + outb);
+  otlm::tc::GemmArgs g{};
+  g.out = reinterpret_cast<float*>(buf + 4 * op);
+  g.M = M; g.N = N; g.Kd = Kd; g.ld_out = M; g.err = err; g.splits = 1;
+  g.wait_ns = 20000000ull;  // 20 ms
+  g.withhold = 1;
+  if (e == cudaSuccess)
+    e = two_sm ? otlm::tc::launch_gemm3_pair<otlm::tc::KIND_BF16>(a_hi, a_lo, Kd, b_hi, b_lo, Kd, M, N, Kd, g, st)
+               : otlm::tc::launch_gemm3<otlm::tc::KIND_BF16>(a_hi, a_lo, Kd, b_hi, b_lo, Kd, M, N, Kd, g, st);
+  int code = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&code, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return OTLM_ECUDA;
+  *code_out = code;
+  return code ? OTLM_ETIMEOUT : OTLM_OK;
+}
+
 const char* otlm_strerror(int code) {
   switch (code) {
     case OTLM_OK: return "ok";

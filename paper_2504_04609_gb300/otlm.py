@@ -26,7 +26,7 @@ EXPORTS = ("otlm_create", "otlm_destroy", "otlm_solve", "otlm_solve_cost", "otlm
            "otlm_tune_ragged", "otlm_ws_create", "otlm_ws_destroy", "otlm_ws_num_params", "otlm_ws_set_normalization",
            "otlm_ws_get_params", "otlm_ws_set_params", "otlm_ws_gradients", "otlm_ws_train_step", "otlm_ws_predict",
            "otlm_ws_make_targets", "otlm_ws_fit_normalization", "otlm_initial_weights", "otlm_solve_stats",
-           "otlm_strerror")
+           "otlm_check_wait_expiry", "otlm_strerror")
 TIMING_KINDS = ("apply", "mm_source", "compact", "other")
 COST = {"sq": 0, "abs": 1}  # grid cost (x_i - x_j)^2 or |x_i - x_j| (otlm_cost_kind)
 
@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
         L.otlm_solve.restype = i
         L.otlm_solve_host.argtypes = solve_args
         L.otlm_solve_host.restype = i
+        L.otlm_check_wait_expiry.argtypes = [i, ctypes.POINTER(ctypes.c_int)]
+        L.otlm_check_wait_expiry.restype = i
         L.otlm_solve_cost.argtypes = solve_args
         L.otlm_solve_cost.restype = i
         L.otlm_objective.argtypes = [vp, i, i, i, vp, vp, vp, d, d, d, vp, vp, vp, vp]
@@ -379,3 +381,10 @@ class WarmStart:
     def predict(self, y, eps, cold_w, g0, w0):
         _check(lib().otlm_ws_predict(self._w, y.shape[0], _ptr(y), eps, _ptr(cold_w), _ptr(g0), _ptr(w0)),
                "otlm_ws_predict")
+
+
+def check_wait_expiry(two_sm: bool) -> tuple:
+    """otlm_check_wait_expiry: (return code, recorded error code) of the bounded-wait self-check."""
+    code = ctypes.c_int(0)
+    rc = lib().otlm_check_wait_expiry(int(bool(two_sm)), ctypes.byref(code))
+    return rc, code.value

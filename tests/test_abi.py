@@ -134,3 +134,8 @@ def test_absolute_distance_cost_passes_validation():
         assert got != api.OTLM_EINVAL
         if got == api.OTLM_OK:
             api.lib().otlm_destroy(h)
+
+
+def test_wait_expiry_check_rejects_a_null_code_pointer():
+    _ensure_built()
+    assert api.lib().otlm_check_wait_expiry(0, None) == api.OTLM_EINVAL
