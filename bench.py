@@ -394,8 +394,9 @@ TC_APPLY_TRAFFIC_NOTE = ("mean DRAM bytes per apply over the 40 applies of one s
                          "profiles/gemm3_pair_apply_n4096_b4096.md")
 
 # Precision schedule of the tensor-core applies (otlm_config.bf16_single_until) by workload: used
-# where the tests show the 1e-5 bar holds with it (the squared-error datafit); 0 = hi/lo throughout.
-SINGLE_UNTIL = {"batch4096_n4096_l2_l2sq": 1e-2}
+# where the tests show the 1e-5 bar holds with it (the squared-error datafit, up to three times the
+# tolerance); 0 = hi/lo throughout.
+SINGLE_UNTIL = {"batch4096_n4096_l2_l2sq": 3e-5}
 
 
 def run_ours(args, rank, world, local_rank, pool=None):

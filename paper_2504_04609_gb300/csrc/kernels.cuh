@@ -520,12 +520,16 @@ __device__ __forceinline__ T source_marginal(const T* __restrict__ Dt, const T* 
 // violation e <= tol, optionally together with the weight change ||dw||_1 / ||w||_1 <= dw_tol and a
 // relative FP64 duality gap <= gap_tol (taken at check iterations only).  Every enabled criterion
 // must hold; with none enabled the solve runs max_iter iterations.  Returns a status or -1.
+// may_converge = false holds a problem back from a converged stop at this iteration (the tensor-core
+// path while its applies still take the single BF16 product: a returned state always comes from
+// hi/lo applies).
 template <typename T>
 __device__ __forceinline__ int stop_decision(T e, T dw, T tol, T dw_tol, bool gap_on, bool gap_ok, int it,
-                                             int max_iter) {
+                                             int max_iter, bool may_converge = true) {
   if (e != e) return ST_NONFINITE;
   const bool any = tol > T(0) || dw_tol > T(0) || gap_on;
-  if (any && (!(tol > T(0)) || e <= tol) && (!(dw_tol > T(0)) || dw <= dw_tol) && (!gap_on || gap_ok))
+  if (may_converge && any && (!(tol > T(0)) || e <= tol) && (!(dw_tol > T(0)) || dw <= dw_tol) &&
+      (!gap_on || gap_ok))
     return ST_CONVERGED;
   if (it >= max_iter) return ST_MAX_ITER;
   return -1;

@@ -49,7 +49,8 @@ struct TcWorkspace {
   float* Msrc[2];            // [batch] source shifts, ping-pong
   float* Mtgt;               // [batch] target shifts
   int* err;                  // GEMM error flag
-  int* hilo;                 // 0: the applies use the single BF16 product, 1: hi/lo (three products)
+  int* hilo;                 // [0] 0: the applies use the single BF16 product, 1: hi/lo (three
+                             // products); [1] the value the iteration's source apply was launched with
   int2* fix_list;            // [batch x n] underflowed sums (problem, row) listed by a GEMM
   unsigned long long* fix_cnt;  // [2] list lengths: source GEMM, target GEMM
   unsigned long long fix_cap;
@@ -350,6 +351,9 @@ __global__ void __launch_bounds__(NT) tc_prep_src_kernel(TcIterArgs A) {
   using P = Prec<float>;
   __shared__ float red[32];
   const int slot = blockIdx.x;
+  // the product count the coming source apply takes (it reads hilo[0] at launch; nothing changes it
+  // before then), for the stopping decision after it
+  if (slot == 0 && threadIdx.x == 0) A.t.hilo[1] = A.t.hilo[0];
   if (slot >= *A.n_active) return;
   const int p = A.active[slot], n = A.n;
   float* G2 = A.G2 + (size_t)p * n;
@@ -482,8 +486,10 @@ __device__ __forceinline__ void tc_violation_body(const TcIterArgs& A) {
     // the precision schedule: the first problem whose violation reaches single_until switches every
     // later apply to the hi/lo products (a violation this large is far from any stop at tol)
     if (A.single_until > 0.f && e <= A.single_until) atomicExch(A.t.hilo, 1);
+    // a converged stop needs this iteration's source sums from the hi/lo products
+    const bool src_hilo = !(A.single_until > 0.f) || A.t.hilo[1] != 0;
     const int st = stop_decision<float>(e, dw, A.tol, A.dw_tol, A.gap_on != 0,
-                                        A.gap_check && A.gap_ok && A.gap_ok[p], A.it, A.max_iter);
+                                        A.gap_check && A.gap_ok && A.gap_ok[p], A.it, A.max_iter, src_hilo);
     if (st >= 0) {
       A.status[p] = st;
       A.iters[p] = A.it;
@@ -733,7 +739,7 @@ inline cudaError_t solve_device_tc(const Launch& L, const Workspace<float>& ws, 
   tc_dsplit_kernel<<<1184, 256, 0, L.stream>>>(D, n, k, tw.kp, tw.ld, tw.Dhi, tw.Dlo, tw.Dthi, tw.Dtlo);
   L.end();
   cudaError_t e = cudaMemsetAsync(tw.err, 0, sizeof(int), L.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(tw.hilo, sp.single_until > 0 ? 0 : 0xFF, sizeof(int), L.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tw.hilo, sp.single_until > 0 ? 0 : 0xFF, 2 * sizeof(int), L.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(tw.fix_cnt, 0, 2 * sizeof(unsigned long long), L.stream);
   if (e == cudaSuccess && checks) e = cudaMemsetAsync(ow->kmass, 0, sizeof(double), L.stream);
   if (e != cudaSuccess) return e;

@@ -109,10 +109,13 @@ def test_two_sm_apply_ragged_tiles_and_compaction(n):
         assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
 
 
-@pytest.mark.parametrize("single_until", [0.0, 1e-2])
+@pytest.mark.parametrize("single_until", [0.0, 3e-5])
 def test_tensorcore_full_workload_sampled_against_oracle(single_until):
     """4096 problems at n = 4096, k = 128 (the measured workload) solved to tol in one call, with and
-    without the precision schedule (the benchmark's form is 1e-2)."""
+    without the precision schedule (the benchmark's form is 3e-5).  Sampled problems match the
+    oracle run to the GPU's own iteration count: the state at the 1e-5 bar and the violation there
+    to 2.5e-6 (the bar of the two-SM test; the schedule may hold a problem one iteration past the
+    oracle's stop, where its source sums were still single-product)."""
     c = spectra.WORKLOADS["batch4096_n4096_l2_l2sq"]
     B, n, k = c["B"], c["n"], c["k"]
     d = spectra.batch(c["id"], B, n, k, c["nnz"])
@@ -121,13 +124,10 @@ def test_tensorcore_full_workload_sampled_against_oracle(single_until):
     assert np.all(r["status"] == api.CONVERGED)
     assert np.all(r["err"] <= c["tol"])
     assert np.all(r["w"] >= 0) and np.all(r["t"] >= 0)
-    for p in (0, 1777, 4095):
-        o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"], tol=c["tol"])
+    for p in (0, 1777, 3000, 4095):
         gi = int(r["iters"][p])
-        if gi != o["iters"]:
-            e = o["err_hist"]
-            assert abs(gi - o["iters"]) == 1 and abs(e[min(gi, o["iters"]) - 1] / c["tol"] - 1) < 1e-2
-            o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], gi)
+        o = _oracle(d, p, c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], gi)
+        assert abs(float(r["err"][p]) - o["err_hist"][gi - 1]) <= 2.5e-6, (p, r["err"][p], o["err_hist"][gi - 1])
         assert rel_l1(r["w"][p], o["w"]) <= TOL, (p, rel_l1(r["w"][p], o["w"]))
         assert rel_l1(r["t"][p], o["t"]) <= TOL, (p, rel_l1(r["t"][p], o["t"]))
 
@@ -267,16 +267,19 @@ def test_dense_cost_of_the_grid_matches_the_grid_solve():
         assert P[p].item() == pytest.approx(Po, rel=2e-6) and Dv[p].item() == pytest.approx(Do, rel=2e-6)
 
 
-def test_precision_schedule_on_the_squared_error_workload():
-    """bf16_single_until = 1e-2: the applies take the single BF16 product until some problem's
-    violation reaches 1e-2, then the hi/lo products.  On the measured workload's configuration (L2
-    datafit + squared l2, eps = 1e-2), n = 2048, 16 problems, solved to 1e-5: each problem matches
-    the oracle at its own iteration count at the 1e-5 bar, and the results differ from the all hi/lo
-    solve's (so the single product did run)."""
+@pytest.mark.parametrize("single_until", [1e-2, 3e-5])
+def test_precision_schedule_on_the_squared_error_workload(single_until):
+    """bf16_single_until: the applies take the single BF16 product until some problem's violation
+    reaches the value, then the hi/lo products, and no problem stops on the violation before its
+    source sums come from the hi/lo products.  On the measured workload's configuration (L2
+    datafit + squared l2, eps = 1e-2), n = 2048, 16 problems, solved to 1e-5, at 1e-2 and at the
+    benchmark's 3e-5 (three times the tolerance): each problem matches the oracle at its own
+    iteration count at the 1e-5 bar, and the results differ from the all hi/lo solve's (so the
+    single product did run)."""
     c = spectra.WORKLOADS["batch4096_n4096_l2_l2sq"]
     d = spectra.batch(c["id"], 16, 2048, 128, c["nnz"], first=500)
     args = (c["eps"], c["lam"], c["alpha"], c["datafit"], c["penalty"], c["iters"])
-    r = _solve(d, *args, tol=c["tol"], single_until=1e-2)
+    r = _solve(d, *args, tol=c["tol"], single_until=single_until)
     r3 = _solve(d, *args, tol=c["tol"])
     assert np.all(r["status"] == api.CONVERGED)
     assert not np.array_equal(r["w"], r3["w"])
