@@ -491,11 +491,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---- two-SM variant (cta_group::2) of the same GEMM ---------------------------------------------
-// A cluster of two CTAs (an SM pair) computes a 256 x 128 output tile. Each CTA stages its own 128
-// rows of A and 64 of the tile's 128 B rows; the even CTA issues M = 256 MMAs that read both CTAs'
-// shared memory and accumulate into both CTAs' TMEM (each CTA's 128 rows x 128 columns). A CTA so
-// stages 24 KiB (hi) or 48 KiB (hi/lo) per k block for the same tensor work as the one-SM kernel's
-// 32 / 64 KiB, and its 192 KiB ring holds 8 or 4 stages: more of the operand latency is hidden.
+// A cluster of two CTAs (an SM pair) computes a 256 x 128 output tile (hi/lo launches) or a 256 x 256
+// tile (single-product launches). Each CTA stages its own 128 rows of A and half of the tile's B
+// rows; the even CTA issues M = 256 MMAs that read both CTAs' shared memory and accumulate into both
+// CTAs' TMEM (each CTA's 128 rows x all the tile's columns). Per k block a CTA so stages 48 KiB
+// (hi/lo: A hi, 64 B rows hi, A lo, B lo) for 128 x 128 of tensor work, 4 stages in its 192 KiB ring,
+// or 32 KiB (A hi, 128 B rows hi) for 128 x 256 of work, 6 stages: twice the work per staged byte of
+// the one-SM kernel's single product, whose launches are bound by the latency of their ring.
 //   both CTAs, warp 0 lane 0: TMA producer into its own ring; the copies complete on the even CTA's
 //                             "full" barriers (which expect both CTAs' bytes)
 //   even CTA, warp 1 lane 0 : MMA issuer; its commits reach the "empty" and "accumulator full"
@@ -505,16 +507,20 @@ __global__ void __launch_bounds__(THREADS, 1)
 // Every mbarrier wait is bounded as in the one-SM kernel; the two cluster barriers (after set-up,
 // before TMEM is released) are reached by every thread of both CTAs on every path.
 constexpr int P_BM = 2 * BM;                                   // output rows per pair tile
-constexpr int P_BNH = BN / 2;                                  // B rows staged by each CTA
+constexpr int P_BNH = BN / 2;                                  // B rows staged by each CTA (hi/lo)
 constexpr int P_B_TILE = P_BNH * BK_BYTES;                     // 8 KiB
 constexpr int P_STAGE = 2 * A_TILE + 2 * P_B_TILE;             // 48 KiB: A hi, B hi, A lo, B lo
 constexpr int P_STAGES = STAGES * STAGE_BYTES / P_STAGE;       // 4
-constexpr int P_STAGES_SINGLE = STAGES * STAGE_BYTES / (A_TILE + P_B_TILE);  // 8
-constexpr int P_NBARS = 2 * P_STAGES_SINGLE + 5;
+constexpr int P_BN_SINGLE = 2 * BN;                            // pair tile columns, single product
+constexpr int P_STAGE_SINGLE = A_TILE + 2 * P_B_TILE;          // 32 KiB: A hi, 128 B rows hi
+constexpr int P_STAGES_SINGLE = STAGES * STAGE_BYTES / P_STAGE_SINGLE;  // 6
+constexpr int P_STAGES_MAX = P_STAGES > P_STAGES_SINGLE ? P_STAGES : P_STAGES_SINGLE;
+constexpr int P_NBARS = 2 * P_STAGES_MAX + 5;
+constexpr uint32_t P_TMEM_COLS = 2 * P_BN_SINGLE;              // two accumulators of up to 256 columns
 constexpr int P_GROUP_M = 8;                                   // row tiles per raster group
 constexpr int P_SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_BYTES + P_NBARS * 8 + 16;
 static_assert(P_SMEM_BYTES <= 232448, "shared memory per CTA");
-static_assert(P_STAGE * P_STAGES <= STAGES * STAGE_BYTES && (A_TILE + P_B_TILE) * P_STAGES_SINGLE <= STAGES * STAGE_BYTES,
+static_assert(P_STAGE * P_STAGES <= STAGES * STAGE_BYTES && P_STAGE_SINGLE * P_STAGES_SINGLE <= STAGES * STAGE_BYTES,
               "ring");
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -592,7 +598,7 @@ template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm3_pair_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                       const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
-                      GemmArgs g) {
+                      const __grid_constant__ CUtensorMap tB_hi2, GemmArgs g) {
   constexpr int BK = KindTraits<KIND>::BK;
   extern __shared__ uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -602,9 +608,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int ncols = g.n_cols ? *g.n_cols : g.N;
   const bool three = !g.hilo || *g.hilo != 0;
   const int nst = three ? P_STAGES : P_STAGES_SINGLE;
+  const int bnp = three ? BN : P_BN_SINGLE, bnh = bnp / 2;  // pair tile columns, B rows per CTA
   const unsigned long long lim = g.wait_ns ? g.wait_ns : WAIT_NS;
-  const uint32_t st_bytes = three ? P_STAGE : A_TILE + P_B_TILE;
-  const int mt = (g.M + P_BM - 1) / P_BM, nt = (g.N + BN - 1) / BN;
+  const uint32_t st_bytes = three ? P_STAGE : P_STAGE_SINGLE;
+  const int mt = (g.M + P_BM - 1) / P_BM, nt = (g.N + bnp - 1) / bnp;
   const int units = mt * nt;
   const int nkb = (g.Kd + BK - 1) / BK;
   // pair tile u: groups of P_GROUP_M row tiles, m fastest within a group, so that the pairs at work
@@ -614,28 +621,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int per = P_GROUP_M * nt, grp = u / per, r = u - grp * per;
     const int first = grp * P_GROUP_M, gsz = min(mt - first, P_GROUP_M);
     *m0 = (first + r % gsz) * P_BM;
-    *n0 = (r / gsz) * BN;
+    *n0 = (r / gsz) * bnp;
   };
 
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* const stage_out = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES + EPI_BYTES);
-  // full[8], empty[8], acc_full[2], acc_empty[2], drain
+  // full[P_STAGES_MAX], empty[P_STAGES_MAX], acc_full[2], acc_empty[2], drain
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + P_NBARS);
   int* fail = reinterpret_cast<int*>(tmem_slot + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + P_STAGES_SINGLE);
-  const uint32_t accf0 = smem_u32(bars + 2 * P_STAGES_SINGLE), acce0 = smem_u32(bars + 2 * P_STAGES_SINGLE + 2);
-  const uint32_t drain = smem_u32(bars + 2 * P_STAGES_SINGLE + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + P_STAGES_MAX);
+  const uint32_t accf0 = smem_u32(bars + 2 * P_STAGES_MAX), acce0 = smem_u32(bars + 2 * P_STAGES_MAX + 2);
+  const uint32_t drain = smem_u32(bars + 2 * P_STAGES_MAX + 4);
   const uint32_t ring = smem_u32(base), stage_s = smem_u32(stage_out);
-  // stage s: A hi (16 KiB), B hi (8 KiB), then A lo, B lo; every tile on a 1 KiB (8-row atom) boundary,
-  // at the same offsets in both CTAs (the pair MMAs address the other CTA's tiles by this CTA's offsets)
+  // stage s: A hi (16 KiB), B hi (8 KiB; 16 KiB for the single product's 128 rows), then (hi/lo) A lo,
+  // B lo; every tile on a 1 KiB (8-row atom) boundary, at the same offsets in both CTAs (the pair MMAs
+  // address the other CTA's tiles by this CTA's offsets)
   auto a_hi = [&](int s) { return ring + static_cast<uint32_t>(s) * st_bytes; };
   auto b_hi = [&](int s) { return a_hi(s) + A_TILE; };
   auto a_lo = [&](int s) { return a_hi(s) + A_TILE + P_B_TILE; };
   auto b_lo = [&](int s) { return a_hi(s) + 2 * A_TILE + P_B_TILE; };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < P_STAGES_SINGLE; ++s) {
+    for (int s = 0; s < P_STAGES_MAX; ++s) {
       mbar_init(full0 + 8 * s, 1);   // the even CTA's producer; the bytes of both CTAs' copies
       mbar_init(empty0 + 8 * s, 1);  // the pair MMAs' commit
     }
@@ -649,7 +657,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 0) {  // the pair allocates together: the same columns in both CTAs' TMEM
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(P_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
   }
@@ -662,15 +670,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0 && lane == 0) {
     // ---- TMA producer (both CTAs): this CTA's A rows and B rows of each pair tile ----
     const uint32_t full_even = mapa_rank(full0, 0);
-    int last_round[P_STAGES_SINGLE];
-    for (int s = 0; s < P_STAGES_SINGLE; ++s) last_round[s] = -1;
+    int last_round[P_STAGES_MAX];
+    for (int s = 0; s < P_STAGES_MAX; ++s) last_round[s] = -1;
+    const CUtensorMap* mb_hi = three ? &tB_hi : &tB_hi2;  // boxes of 64 or 128 B rows
     int s = 0, r = 0;
     bool stop = false;
     for (int u = pair; u < units && !stop; u += npairs) {
       int m0, n0;
       coords(u, &m0, &n0);
       if (n0 >= ncols) continue;
-      const int ma = m0 + static_cast<int>(rank) * BM, nb = n0 + static_cast<int>(rank) * P_BNH;
+      const int ma = m0 + static_cast<int>(rank) * BM, nb = n0 + static_cast<int>(rank) * bnh;
       for (int kb = 0; kb < nkb; ++kb) {
         if (r >= 1 && !mbar_wait(empty0 + 8 * s, (r - 1) & 1, lim)) {
           atomicCAS(g.err, 0, ERR_WAIT_MMA);
@@ -687,7 +696,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (even) mbar_expect_tx(full0 + 8 * s, 2 * st_bytes);
         if (!(g.withhold && blockIdx.x == 0 && r == 0 && s == 0)) {  // (self-check: the first copies withheld)
           tma_load_2d_pair(a_hi(s), &tA_hi, fb, kc, ma);
-          tma_load_2d_pair(b_hi(s), &tB_hi, fb, kc, nb);
+          tma_load_2d_pair(b_hi(s), mb_hi, fb, kc, nb);
           if (three) {
             tma_load_2d_pair(a_lo(s), &tA_lo, fb, kc, ma);
             tma_load_2d_pair(b_lo(s), &tB_lo, fb, kc, nb);
@@ -713,8 +722,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     // of shared memory below 256 KiB, so the offsets add without carry).
     auto mma_role = [&](auto three_c) {
       constexpr bool THREE = decltype(three_c)::value;
-      constexpr uint32_t id = idesc<KIND>(P_BM, BN);
-      constexpr uint32_t ST16 = (THREE ? P_STAGE : A_TILE + P_B_TILE) >> 4;
+      constexpr int NPT = THREE ? BN : P_BN_SINGLE;  // pair tile columns
+      constexpr uint32_t id = idesc<KIND>(P_BM, NPT);
+      constexpr uint32_t ST16 = (THREE ? P_STAGE : P_STAGE_SINGLE) >> 4;
       constexpr int NST = THREE ? P_STAGES : P_STAGES_SINGLE;
       constexpr uint32_t O_BH = A_TILE >> 4, O_AL = (A_TILE + P_B_TILE) >> 4, O_BL = (2 * A_TILE + P_B_TILE) >> 4;
       const uint64_t d_ring = sw128_desc(ring);
@@ -732,7 +742,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
+        const uint32_t d = tmem + static_cast<uint32_t>(b * NPT);
         int issued = 0;
         for (int kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait(full0 + 8 * s, r & 1, lim)) {
@@ -787,10 +797,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       tc_fence_after();
       const int ma = m0 + static_cast<int>(rank) * BM;  // this CTA's rows of the pair tile
-      const uint32_t tq = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * BN);
-      // once every TMEM read of buffer b is done, count it on the even CTA
-      epilogue_tile(g, g.out, tq, stage_out, stage_s, ma, n0, ncols, q, lane, et,
-                    [&] { if (lane == 0) mbar_arrive_remote(acce_even + 8 * b); });
+      const uint32_t tq = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(b * bnp);
+      // once every TMEM read of buffer b is done, count it on the even CTA; a 256-column tile
+      // leaves as two 128-column halves
+      auto release = [&] { if (lane == 0) mbar_arrive_remote(acce_even + 8 * b); };
+      if (three) {
+        epilogue_tile(g, g.out, tq, stage_out, stage_s, ma, n0, ncols, q, lane, et, release);
+      } else {
+        epilogue_tile(g, g.out, tq, stage_out, stage_s, ma, n0, ncols, q, lane, et, [] {});
+        epilogue_tile(g, g.out, tq + BN, stage_out, stage_s, ma, n0 + BN, ncols, q, lane, et, release);
+      }
       ++i;
     }
     if (g.bulk && et < 64) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -801,7 +817,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P_TMEM_COLS) : "memory");
   }
 }
 
@@ -919,14 +935,15 @@ static inline cudaError_t launch_gemm3_pair(const void* A_hi, const void* A_lo, 
   }
   GemmArgs a = args;
   a.bulk = !a.store_direct && (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && a.ld_out % 4 == 0 && M % 4 == 0;
-  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo, tb_hi2;
   if (!make_map<KIND>(&ta_hi, A_hi, M, Kd, lda, BM) || !make_map<KIND>(&ta_lo, A_lo, M, Kd, lda, BM) ||
-      !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, P_BNH) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, P_BNH))
+      !make_map<KIND>(&tb_hi, B_hi, N, Kd, ldb, P_BNH) || !make_map<KIND>(&tb_lo, B_lo, N, Kd, ldb, P_BNH) ||
+      !make_map<KIND>(&tb_hi2, B_hi, N, Kd, ldb, P_BN_SINGLE / 2))
     return cudaErrorInvalidValue;
   const long long units = static_cast<long long>((M + P_BM - 1) / P_BM) * ((N + BN - 1) / BN);
   const int pairs = static_cast<int>(units < max_pairs ? units : max_pairs);
   cfg.gridDim = dim3(2 * pairs, 1, 1);
-  return cudaLaunchKernelEx(&cfg, gemm3_pair_kernel<KIND>, ta_hi, ta_lo, tb_hi, tb_lo, a);
+  return cudaLaunchKernelEx(&cfg, gemm3_pair_kernel<KIND>, ta_hi, ta_lo, tb_hi, tb_lo, tb_hi2, a);
 }
 
 // Splits of a reduction of `nkb` k blocks over `tiles` output tiles that minimise
