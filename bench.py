@@ -388,10 +388,10 @@ class ClockSampler:
 # problems, averaged over the applies of one solve under the precision schedule, from a one-pass
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands.
 TC_APPLY_TRAFFIC_WORKLOAD = "batch4096_n4096_l2_l2sq"
-TC_APPLY_TRAFFIC = 197.3e6
+TC_APPLY_TRAFFIC = 189.7e6
 TC_APPLY_TRAFFIC_NOTE = ("mean DRAM bytes per apply over the 40 applies of one solve under the schedule at 3e-5 "
-                         "(25 single-product: 131 MB, 14 hi/lo: 331 MB, against 134 / 201 MB algorithmic), "
-                         "one-pass ncu capture: profiles/gemm3_pair_apply_n4096_b4096.md")
+                         "(25 single-product on 256 x 256 pair tiles: 119 MB, 14 hi/lo: 329 MB, against 134 / 201 MB "
+                         "algorithmic), one-pass ncu capture: profiles/gemm3_pair_apply_n4096_b4096.md")
 
 # Precision schedule of the tensor-core applies (otlm_config.bf16_single_until) by workload: used
 # where the tests show the 1e-5 bar holds with it (the squared-error datafit, up to three times the
