@@ -15,8 +15,11 @@
 // column map, with an optional split of the reduction (each split stores its own partial sums,
 // added later in a fixed order).
 //
-// Persistent kernel, one CTA per SM; work units (128 x 128 output tile, reduction split) are dealt
-// round-robin over the CTAs:
+// Two kernels: gemm3_pair_kernel (below; SM pairs, cta_group::2) for every GEMM whose reduction is
+// not split (the applies of larger batches, D w), and gemm3_kernel for split reductions (small batches,
+// D^T r) and the warm-start network.  gemm3_kernel is a persistent
+// kernel, one CTA per SM; work units (128 x 128 output tile, reduction split) are dealt round-robin
+// over the CTAs:
 //   warp 0 lane 0: TMA producer (cp.async.bulk.tensor, 128B-swizzled tiles, a 192 KiB ring that runs
 //                  on across units: 3 stages of the four hi/lo tiles, or 6 stages of the two hi
 //                  tiles when the single product is requested, so that twice as many k blocks are
@@ -24,10 +27,11 @@
 //   warp 1 lane 0: MMA issuer  (3 x 4 tcgen05.mma per 128-byte k block) into one of two TMEM
 //                  accumulators, so the epilogue of unit i overlaps the MMAs of unit i + 1
 //   warps 4..7   : epilogue    (tcgen05.ld 32x32b, one TMEM lane quarter per warp; 64 columns at a
-//                  time through a 32 KiB staging buffer and one bulk copy per output column)
-// Every wait on an mbarrier is bounded (about 2 s of %globaltimer); on expiry the CTA records an
-// error in *err, stops issuing work, lets its issued copies land, waits boundedly for its
-// committed MMAs and frees its TMEM.
+//                  time, four loads per wait, through a 32 KiB staging buffer and one bulk copy per
+//                  output column, or stored from registers on request)
+// Every wait on an mbarrier is bounded (about 2 s of %globaltimer, or GemmArgs.wait_ns); on expiry
+// the CTA records an error in *err, stops issuing work, lets its issued copies land, waits boundedly
+// for its committed MMAs and frees its TMEM.
 #pragma once
 
 #include <cuda.h>
