@@ -399,6 +399,38 @@ TC_APPLY_TRAFFIC_NOTE = ("mean DRAM bytes per apply over the 40 applies of one s
 SINGLE_UNTIL = {"batch4096_n4096_l2_l2sq": 3e-5}
 
 
+def tc_apply_roofline(workload, n, iters, apply_timing, peaks, iters_hilo=None, apply_timing_hilo=None):
+    """Roofline of the tensor-core apply (gemm3_pair_kernel<KIND_BF16>) from one timed solve.
+
+    Algorithmic work is 2 n^2 flops per problem per apply (one multiply-add per kernel entry); a
+    problem stopping after T iterations sees T + 1 source and T target applies.  apply_timing =
+    (ms, launches) of the solve's applies (CUDA events).  Under the precision schedule the first
+    applies issue one tensor product per algorithmic one and the rest three (the hi/lo split); the
+    solve with the split throughout (iters_hilo, apply_timing_hilo) gives the issued rate of the
+    three-product launches.  DRAM traffic is reported for the workload it was captured on only."""
+    it = np.asarray(iters, dtype=np.float64)
+    flops = 2.0 * n * n * float(np.sum(2 * it + 1))
+    g_ms, g_cnt = apply_timing
+    achieved = flops / (g_ms / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    captured = workload == TC_APPLY_TRAFFIC_WORKLOAD
+    r = {"bound": "tensor",
+         "kernel": "gemm3_pair_kernel<KIND_BF16> (two-SM tcgen05 K V^T, BF16 hi/lo, FP32 accumulate)",
+         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+         "traffic": TC_APPLY_TRAFFIC if captured else None, "launch_ms_avg": g_ms / max(g_cnt, 1),
+         "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
+         if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained",
+         "traffic_note": TC_APPLY_TRAFFIC_NOTE if captured else "no DRAM capture of this workload"}
+    if iters_hilo is not None:
+        it3 = np.asarray(iters_hilo, dtype=np.float64)
+        issued = 3 * 2.0 * n * n * float(np.sum(2 * it3 + 1)) / (apply_timing_hilo[0] / 1e3) / 1e12
+    else:
+        issued = 3 * achieved
+    r["issued_tensor_tflops_hilo"] = issued
+    r["issued_frac_hilo"] = issued / peak
+    return r
+
+
 def run_ours(args, rank, world, local_rank, pool=None):
     import torch
     import torch.distributed as dist
@@ -505,34 +537,10 @@ def run_ours(args, rank, world, local_rank, pool=None):
     fp_value = whole_job_rate(B, world, fp_steps, fp_ms / 1e3)
     peaks = _peaks()
 
-    # tensor-core path: the GEMM apply; algorithmic work is 2 n^2 flops per problem per apply
-    # (one multiply-add per kernel entry); a problem stopping after T iterations sees T + 1 source
-    # and T target applies.  Under the precision schedule the first applies issue one tensor product
-    # per algorithmic one and the rest three (the hi/lo split); the run with the split throughout
-    # gives the issued rate of the three-product launches.
     it_tc = tc["iters"].astype(np.float64)
-    flops_step = 2.0 * n * n * float(np.sum(2 * it_tc + 1))
-    g_ms, g_cnt = tc["timing"]["apply"]
-    achieved_tf = flops_step / (g_ms / 1e3) / 1e12  # the timing solve is one step
-    peak_tf = float(peaks.get("bf16_tflops_sustained", 1700.0))
-    roofline = {"bound": "tensor",
-                "kernel": "gemm3_pair_kernel<KIND_BF16> (two-SM tcgen05 K V^T, BF16 hi/lo, FP32 accumulate)",
-                "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": TC_APPLY_TRAFFIC if args.workload == TC_APPLY_TRAFFIC_WORKLOAD else None,
-                "launch_ms_avg": g_ms / max(g_cnt, 1),
-                "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)"
-                if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained",
-                "traffic_note": TC_APPLY_TRAFFIC_NOTE if args.workload == TC_APPLY_TRAFFIC_WORKLOAD else
-                "no DRAM capture of this workload"}
-    if tc3 is not None:
-        it3 = tc3["iters"].astype(np.float64)
-        a3_ms, _ = tc3["timing"]["apply"]
-        issued = 3 * 2.0 * n * n * float(np.sum(2 * it3 + 1)) / (a3_ms / 1e3) / 1e12
-        roofline["issued_tensor_tflops_hilo"] = issued
-        roofline["issued_frac_hilo"] = issued / peak_tf
-    else:
-        roofline["issued_tensor_tflops_hilo"] = 3 * achieved_tf
-        roofline["issued_frac_hilo"] = 3 * achieved_tf / peak_tf
+    roofline = tc_apply_roofline(args.workload, n, tc["iters"], tc["timing"]["apply"], peaks,
+                                 tc3["iters"] if tc3 is not None else None,
+                                 tc3["timing"]["apply"] if tc3 is not None else None)
 
     # plain FP32 path: the log-sum-exp apply against the exponent unit
     it_fp = fp["iters"].astype(np.float64)
