@@ -4,7 +4,7 @@ Orchestration only: every numerical step runs in libotlm.so (the solver through 
 network through otlm_ws_*).  Labels are the solver's own results: each training target is solved
 from the cold start (u1 = 1, w0_j = sum(y) / (k x_j)) to the stopping tolerance, and the network
 learns (g / eps, log w) of that solution.  At inference the prediction replaces the cold start; the
-same solver then runs to the same tolerance, so the plain iteration stays the judge: a poor
+same solver then runs to the same tolerance, so the plain iteration decides convergence: a poor
 prediction can only cost iterations, never accuracy (non-finite predictions fall back to the cold
 start inside otlm_ws_predict).
 """
