@@ -64,6 +64,9 @@ def test_null_handle_is_rejected():
     _ensure_built()
     rc = api.lib().otlm_solve(None, 1, 8, 2, 1, 1, 1, 0.1, 1.0, 0.1, 1, None, None, None, None, None)
     assert rc == api.OTLM_EINVAL
+    # the dense-cost entry point (every precision takes a cost matrix of the handle's element type)
+    rc = api.lib().otlm_solve_cost(None, 1, 8, 2, 1, 1, 1, 0.1, 1.0, 0.1, 1, None, None, None, None, None)
+    assert rc == api.OTLM_EINVAL
     assert api.lib().otlm_launch_count(None) == -1
 
 
